@@ -1,0 +1,158 @@
+"""CPU oracle for the Relay-BP hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline / reference
+legs may import this package.  It wraps ``relaybp_oracle.c`` (plain C, FP64)
+through ctypes; that file cites the passages of arXiv 2607.27644 it follows.
+
+Pins (tests/test_oracle_*.py) tie it to things other than itself: published
+Philox known-answer vectors, brute-force min-marginals on cycle-free graphs,
+a closed-form memory recurrence, brute-force minimum-weight decoding of the
+[[60,12,6]] code, and invariants (H e^ = s on every claimed success).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "relaybp_oracle.c")
+_LIB = os.path.join(_HERE, "librelaybp_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over shots)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OracleParams(ctypes.Structure):
+    _fields_ = [("gamma0", ctypes.c_double), ("pre_iter", ctypes.c_int32), ("num_sets", ctypes.c_int32),
+                ("max_iterations", ctypes.c_int32), ("stop_nconv", ctypes.c_int32),
+                ("gamma_min", ctypes.c_double), ("gamma_max", ctypes.c_double),
+                ("stop_all", ctypes.c_int32), ("carry_messages", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        _lib.oracle_philox4x32_10.argtypes = [P, P, P]
+        _lib.oracle_philox4x32_10.restype = None
+        _lib.oracle_sample.argtypes = [ctypes.c_int32] * 3 + [P] * 5 + [ctypes.c_uint64, ctypes.c_uint64,
+                                                                         ctypes.c_int64, P, P, P]
+        _lib.oracle_sample.restype = ctypes.c_int
+        _lib.oracle_relaybp_decode.argtypes = ([ctypes.c_int32] * 3 + [P] * 5 + [ctypes.POINTER(OracleParams), P,
+                                               ctypes.c_uint64, ctypes.c_int64, P, P, P, P, ctypes.c_int32, P,
+                                               ctypes.c_int32])
+        _lib.oracle_relaybp_decode.restype = ctypes.c_int
+        _lib.oracle_max_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def _dem_arrays(dem):
+    return (np.ascontiguousarray(dem.H_indptr, dtype=np.int32), np.ascontiguousarray(dem.H_indices, dtype=np.int32),
+            np.ascontiguousarray(dem.O_indptr, dtype=np.int32), np.ascontiguousarray(dem.O_indices, dtype=np.int32),
+            np.ascontiguousarray(dem.priors, dtype=np.float64))
+
+
+def sample(dem, seed: int, shot0: int, shots: int, want_errors: bool = False):
+    """(syndromes [shots, ceil(C/32)] u32, obs [shots, ceil(k/32)] u32, errors or None)."""
+    lib = _load()
+    Hp, Hi, Op, Oi, pr = _dem_arrays(dem)
+    syn = np.zeros((shots, (dem.n_det + 31) // 32), dtype=np.uint32)
+    obs = np.zeros((shots, max(1, (dem.n_obs + 31) // 32)), dtype=np.uint32)
+    err = np.zeros((shots, (dem.n_loc + 31) // 32), dtype=np.uint32) if want_errors else None
+    rc = lib.oracle_sample(dem.n_det, dem.n_loc, dem.n_obs, _ptr(Hp), _ptr(Hi), _ptr(Op), _ptr(Oi), _ptr(pr),
+                           seed, shot0, shots, _ptr(syn), _ptr(obs), _ptr(err))
+    if rc != 0:
+        raise ValueError("oracle_sample rejected its input")
+    return syn, obs, err
+
+
+@dataclass
+class DecodeParams:
+    """Relay-BP parameters (Sec. 6.1 decoder configuration list)."""
+    gamma0: float = 0.125
+    pre_iter: int = 80
+    num_sets: int = 1000
+    max_iterations: int = 60
+    stop_nconv: int = 5
+    gamma_min: float = -0.24
+    gamma_max: float = 0.66
+    stop_all: bool = False
+    carry_messages: bool = False
+    seed: int = 0
+
+    def c(self) -> OracleParams:
+        return OracleParams(self.gamma0, self.pre_iter, self.num_sets, self.max_iterations, self.stop_nconv,
+                            self.gamma_min, self.gamma_max, int(self.stop_all), int(self.carry_messages),
+                            self.seed)
+
+
+def decode(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0, trace_iters: int = 0,
+           n_threads: int = 0):
+    """Relay-BP on every syndrome row.
+
+    Returns dict(corrections, pred_obs, stats[shots,4], weights, trace or None).
+    stats columns: converged, #solutions, legs run, total iterations.
+    """
+    lib = _load()
+    Hp, Hi, Op, Oi, pr = _dem_arrays(dem)
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint32)
+    shots = syn.shape[0]
+    corr = np.zeros((shots, (dem.n_loc + 31) // 32), dtype=np.uint32)
+    pobs = np.zeros((shots, max(1, (dem.n_obs + 31) // 32)), dtype=np.uint32)
+    stats = np.zeros((shots, 4), dtype=np.int32)
+    w = np.zeros(shots, dtype=np.float64)
+    trace = np.zeros((shots, trace_iters, dem.n_loc), dtype=np.float64) if trace_iters > 0 else None
+    cp = params.c()
+    rc = lib.oracle_relaybp_decode(dem.n_det, dem.n_loc, dem.n_obs, _ptr(Hp), _ptr(Hi), _ptr(Op), _ptr(Oi), _ptr(pr),
+                                   ctypes.byref(cp), _ptr(syn), shot0, shots, _ptr(corr), _ptr(pobs), _ptr(stats),
+                                   _ptr(w), trace_iters, _ptr(trace), n_threads)
+    if rc != 0:
+        raise ValueError("oracle_relaybp_decode rejected its input")
+    return dict(corrections=corr, pred_obs=pobs, stats=stats, weights=w, trace=trace)
+
+
+def unpack_bits(words: np.ndarray, nbits: int) -> np.ndarray:
+    """[..., W] u32 -> [..., nbits] uint8 (bit b in word b/32, position b%32)."""
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    b = np.unpackbits(w.view(np.uint8), axis=-1, bitorder="little")
+    return b[..., :nbits]
+
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """[..., nbits] {0,1} -> [..., ceil(nbits/32)] u32."""
+    bits = np.asarray(bits, dtype=np.uint8)
+    nb = bits.shape[-1]
+    pad = (-nb) % 32
+    if pad:
+        bits = np.concatenate([bits, np.zeros(bits.shape[:-1] + (pad,), dtype=np.uint8)], axis=-1)
+    by = np.packbits(bits, axis=-1, bitorder="little")
+    return np.ascontiguousarray(by).view(np.uint32)

@@ -1,0 +1,359 @@
+/*
+ * relaybp_oracle.c -- plain, slow, FP64 CPU oracle for the Relay-BP hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or call
+ * this file: it exists so that tests, the smoke check and the CPU-baseline leg
+ * of the benchmark can check the CUDA path against a direct transcription of
+ * the method.  It shares no code, header or table with the CUDA library.
+ *
+ * What it computes (arXiv 2607.27644, Sec. 6.1 "Quantum circuit-level memory",
+ * decoder configuration list; the update rule of Relay-BP itself is cited, not
+ * printed, by the paper, so the reading below is the one stated in the design
+ * notes):
+ *
+ *   a1  prior LLRs            L0_j = log((1 - p_j) / p_j)                (FP64)
+ *   a2  fault sampler         e_j = [philox word_j < floor(p_j 2^32)],
+ *                             s = H e, obs = O e                        (exact)
+ *   a3  check update          nu_{i->j} = (-1)^{s_i} prod_{j' != j} sgn(mu_{j'->i})
+ *                                                 * min_{j' != j} |mu_{j'->i}|
+ *   a4  variable update       L_j(t)  = (1 - g_j) L0_j + g_j M_j(t-1)
+ *       (memory strength g)   mu_{j->i} = L_j(t) + sum_{i' != i} nu_{i'->j}(t-1)
+ *                             M_j(t)  = L_j(t) + sum_i nu_{i->j}(t)
+ *                             e^_j    = [M_j(t) < 0]
+ *   a5  residual              converged iff H e^ = s
+ *   a6  relay legs            leg 0: pre_iter iterations at g_j = gamma0;
+ *                             legs 1..num_sets: max_iterations iterations with
+ *                             g_j ~ U[gamma_min, gamma_max] per variable per leg;
+ *                             M carries across legs, messages reset (unless
+ *                             carry_messages); a leg stops at its first
+ *                             convergence; stop after stop_nconv solutions
+ *   a7  select                weight w(e^) = sum_j e^_j L0_j in FP64; keep the
+ *                             minimum, earliest on ties
+ *   a9  accounting            predicted observables O e^
+ *
+ * Philox4x32-10 follows Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
+ * as easy as 1, 2, 3" (SC'11): two 32x32->64 multiplies per round with the
+ * published multipliers and Weyl key increments, ten rounds.
+ *
+ * Bit layouts: bit b of a packed vector lives in word b/32 at position b%32.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (SC'11)                                                      */
+/* ------------------------------------------------------------------------- */
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Word j of the counter stream (stream id, shot) for a 64-bit seed. */
+static uint32_t stream_word(uint64_t seed, uint64_t shot, uint32_t stream, uint64_t j)
+{
+    uint32_t ctr[4], key[2], out[4];
+    ctr[0] = (uint32_t)(j / 4);
+    ctr[1] = (uint32_t)(shot & 0xffffffffu);
+    ctr[2] = (uint32_t)(shot >> 32);
+    ctr[3] = stream;
+    key[0] = (uint32_t)(seed & 0xffffffffu);
+    key[1] = (uint32_t)(seed >> 32);
+    oracle_philox4x32_10(ctr, key, out);
+    return out[j % 4];
+}
+
+static int get_bit(const uint32_t *v, int64_t b) { return (int)((v[b >> 5] >> (b & 31)) & 1u); }
+static void flip_bit(uint32_t *v, int64_t b) { v[b >> 5] ^= (1u << (b & 31)); }
+
+/* ------------------------------------------------------------------------- */
+/* a2: Bernoulli fault sampler                                               */
+/* ------------------------------------------------------------------------- */
+/* Fault j of shot s fires iff word j of stream 0 is below floor(p_j * 2^32).
+ * Returns 0, or -1 on a probability outside [0, 1]. */
+int oracle_sample(int32_t n_det, int32_t n_loc, int32_t n_obs,
+                  const int32_t *H_indptr, const int32_t *H_indices,
+                  const int32_t *O_indptr, const int32_t *O_indices,
+                  const double *priors, uint64_t seed, uint64_t shot0, int64_t shots,
+                  uint32_t *syndromes, uint32_t *obs, uint32_t *errors)
+{
+    int64_t wd = (n_det + 31) / 32, wo = (n_obs + 31) / 32, wv = (n_loc + 31) / 32;
+    /* columns of H and O as lists: plain transposes of the CSR inputs */
+    int32_t *hc_ptr = calloc((size_t)n_loc + 1, sizeof(int32_t));
+    int32_t *oc_ptr = calloc((size_t)n_loc + 1, sizeof(int32_t));
+    int32_t nnz_h = H_indptr[n_det], nnz_o = n_obs ? O_indptr[n_obs] : 0;
+    int32_t *hc_rows = malloc(sizeof(int32_t) * (size_t)(nnz_h + 1));
+    int32_t *oc_rows = malloc(sizeof(int32_t) * (size_t)(nnz_o + 1));
+    uint32_t *thr = malloc(sizeof(uint32_t) * (size_t)(n_loc + 1));
+    for (int32_t j = 0; j < n_loc; ++j) {
+        double p = priors[j];
+        if (!(p >= 0.0 && p <= 1.0)) { free(hc_ptr); free(oc_ptr); free(hc_rows); free(oc_rows); free(thr); return -1; }
+        double t = floor(p * 4294967296.0);
+        thr[j] = t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
+    }
+    for (int32_t i = 0; i < n_det; ++i)
+        for (int32_t e = H_indptr[i]; e < H_indptr[i + 1]; ++e) hc_ptr[H_indices[e] + 1]++;
+    for (int32_t i = 0; i < n_obs; ++i)
+        for (int32_t e = O_indptr[i]; e < O_indptr[i + 1]; ++e) oc_ptr[O_indices[e] + 1]++;
+    for (int32_t j = 0; j < n_loc; ++j) { hc_ptr[j + 1] += hc_ptr[j]; oc_ptr[j + 1] += oc_ptr[j]; }
+    {
+        int32_t *fh = calloc((size_t)n_loc + 1, sizeof(int32_t));
+        int32_t *fo = calloc((size_t)n_loc + 1, sizeof(int32_t));
+        for (int32_t i = 0; i < n_det; ++i)
+            for (int32_t e = H_indptr[i]; e < H_indptr[i + 1]; ++e) {
+                int32_t j = H_indices[e];
+                hc_rows[hc_ptr[j] + fh[j]++] = i;
+            }
+        for (int32_t i = 0; i < n_obs; ++i)
+            for (int32_t e = O_indptr[i]; e < O_indptr[i + 1]; ++e) {
+                int32_t j = O_indices[e];
+                oc_rows[oc_ptr[j] + fo[j]++] = i;
+            }
+        free(fh); free(fo);
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t s = 0; s < shots; ++s) {
+        uint32_t *syn = syndromes + s * wd;
+        uint32_t *ob = obs ? obs + s * wo : NULL;
+        uint32_t *er = errors ? errors + s * wv : NULL;
+        memset(syn, 0, sizeof(uint32_t) * (size_t)wd);
+        if (ob) memset(ob, 0, sizeof(uint32_t) * (size_t)wo);
+        if (er) memset(er, 0, sizeof(uint32_t) * (size_t)wv);
+        for (int32_t j = 0; j < n_loc; ++j) {
+            uint32_t w = stream_word(seed, shot0 + (uint64_t)s, 0u, (uint64_t)j);
+            if (w < thr[j]) {
+                if (er) flip_bit(er, j);
+                for (int32_t e = hc_ptr[j]; e < hc_ptr[j + 1]; ++e) flip_bit(syn, hc_rows[e]);
+                if (ob)
+                    for (int32_t e = oc_ptr[j]; e < oc_ptr[j + 1]; ++e) flip_bit(ob, oc_rows[e]);
+            }
+        }
+    }
+    free(hc_ptr); free(oc_ptr); free(hc_rows); free(oc_rows); free(thr);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* a1, a3-a7, a9: Relay-BP                                                    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double gamma0;
+    int32_t pre_iter, num_sets, max_iterations, stop_nconv;
+    double gamma_min, gamma_max;
+    int32_t stop_all;          /* 1: run every leg regardless of solutions */
+    int32_t carry_messages;    /* 1: keep check->variable messages across legs */
+    uint64_t seed;             /* key of the memory-strength stream */
+} oracle_params;
+
+typedef struct {
+    int32_t n_det, n_loc;
+    const int32_t *rptr, *rcol;   /* CSR of H: edge e = (row i, column rcol[e]) */
+    int32_t *cptr, *cedge;        /* per column: the edge ids that touch it */
+    const double *L0;
+} graph_t;
+
+/* g_j for leg r >= 1: gamma_min + (gamma_max - gamma_min) * u, u = top 24 bits
+ * of word (r * ceil(n_loc / 4) * 4 + j) of stream 1, scaled by 2^-24. */
+static double draw_gamma(const oracle_params *P, uint64_t shot, int32_t leg, int32_t j, int32_t n_loc)
+{
+    uint64_t nblk = ((uint64_t)n_loc + 3) / 4;
+    uint64_t word_index = (uint64_t)leg * nblk * 4 + (uint64_t)j;
+    uint32_t w = stream_word(P->seed, shot, 1u, word_index);
+    double u = (double)(w >> 8) * (1.0 / 16777216.0);
+    return P->gamma_min + (P->gamma_max - P->gamma_min) * u;
+}
+
+static double sgn(double v) { return v < 0.0 ? -1.0 : 1.0; }   /* sgn(0) = +1 */
+
+static void decode_one(const graph_t *g, const oracle_params *P, const uint32_t *syn, uint64_t shot,
+                       uint32_t *corr, int32_t *stats, double *weight, int trace_iters, double *trace,
+                       double *nu, double *mu, double *M, double *Lam, double *gam, uint8_t *ehat,
+                       uint8_t *best)
+{
+    const int32_t V = g->n_loc, C = g->n_det, E = g->rptr[C];
+    const double *L0 = g->L0;
+    int32_t nsol = 0, legs = 0, iters = 0, have_best = 0;
+    double best_w = 0.0;
+    for (int32_t j = 0; j < V; ++j) M[j] = L0[j];
+    for (int32_t e = 0; e < E; ++e) nu[e] = 0.0;
+    memset(ehat, 0, (size_t)V);
+    for (int32_t leg = 0; leg <= P->num_sets; ++leg) {
+        legs++;
+        for (int32_t j = 0; j < V; ++j) gam[j] = (leg == 0) ? P->gamma0 : draw_gamma(P, shot, leg, j, V);
+        if (leg > 0 && !P->carry_messages)
+            for (int32_t e = 0; e < E; ++e) nu[e] = 0.0;
+        int32_t T = (leg == 0) ? P->pre_iter : P->max_iterations;
+        int converged = 0;
+        for (int32_t t = 1; t <= T && !converged; ++t) {
+            /* a4 (first half): memory-biased prior */
+            for (int32_t j = 0; j < V; ++j) Lam[j] = (1.0 - gam[j]) * L0[j] + gam[j] * M[j];
+            /* variable-to-check messages: prior plus every other incoming message */
+            for (int32_t j = 0; j < V; ++j)
+                for (int32_t a = g->cptr[j]; a < g->cptr[j + 1]; ++a) {
+                    int32_t e = g->cedge[a];
+                    double s = Lam[j];
+                    for (int32_t b = g->cptr[j]; b < g->cptr[j + 1]; ++b)
+                        if (b != a) s += nu[g->cedge[b]];
+                    mu[e] = s;
+                }
+            /* a3: min-sum check update, leave-one-out by direct loops */
+            for (int32_t i = 0; i < C; ++i) {
+                double ssign = get_bit(syn, i) ? -1.0 : 1.0;
+                for (int32_t e = g->rptr[i]; e < g->rptr[i + 1]; ++e) {
+                    double prod = ssign, mn = INFINITY;
+                    for (int32_t f = g->rptr[i]; f < g->rptr[i + 1]; ++f) {
+                        if (f == e) continue;
+                        prod *= sgn(mu[f]);
+                        double m = fabs(mu[f]);
+                        if (m < mn) mn = m;
+                    }
+                    nu[e] = prod * mn;   /* a degree-1 check sends +-inf: the bit is forced */
+                }
+            }
+            /* a4 (second half): marginals and hard decisions */
+            for (int32_t j = 0; j < V; ++j) {
+                double s = Lam[j];
+                for (int32_t a = g->cptr[j]; a < g->cptr[j + 1]; ++a) s += nu[g->cedge[a]];
+                M[j] = s;
+                ehat[j] = (uint8_t)(s < 0.0);
+            }
+            iters++;
+            if (trace && iters <= trace_iters)
+                for (int32_t j = 0; j < V; ++j) trace[(int64_t)(iters - 1) * V + j] = M[j];
+            /* a5: residual H e^ + s */
+            int ok = 1;
+            for (int32_t i = 0; i < C && ok; ++i) {
+                int par = get_bit(syn, i);
+                for (int32_t e = g->rptr[i]; e < g->rptr[i + 1]; ++e) par ^= ehat[g->rcol[e]];
+                if (par) ok = 0;
+            }
+            if (ok) {
+                converged = 1;
+                double w = 0.0;                                  /* a7: FP64 weight */
+                for (int32_t j = 0; j < V; ++j) if (ehat[j]) w += L0[j];
+                nsol++;
+                if (!have_best || w < best_w) {
+                    have_best = 1;
+                    best_w = w;
+                    memcpy(best, ehat, (size_t)V);
+                }
+            }
+        }
+        if (!P->stop_all && nsol >= P->stop_nconv) break;
+    }
+    const uint8_t *out = have_best ? best : ehat;
+    double w = 0.0;
+    for (int32_t j = 0; j < V; ++j) if (out[j]) w += L0[j];
+    memset(corr, 0, sizeof(uint32_t) * (size_t)((V + 31) / 32));
+    for (int32_t j = 0; j < V; ++j) if (out[j]) flip_bit(corr, j);
+    stats[0] = have_best;
+    stats[1] = nsol;
+    stats[2] = legs;
+    stats[3] = iters;
+    *weight = w;
+}
+
+/* Decode `shots` syndromes.  stats: [shots][4] = converged, #solutions, legs,
+ * iterations; weights: [shots] FP64 weight of the returned correction; trace
+ * (optional): [shots][trace_iters][n_loc] marginals M after each iteration.
+ * Returns 0, or -1 on invalid input. */
+int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
+                          const int32_t *H_indptr, const int32_t *H_indices,
+                          const int32_t *O_indptr, const int32_t *O_indices,
+                          const double *priors, const oracle_params *P,
+                          const uint32_t *syndromes, uint64_t shot0, int64_t shots,
+                          uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
+                          int32_t trace_iters, double *trace, int32_t n_threads)
+{
+    if (n_det < 0 || n_loc < 0 || shots < 0 || !P) return -1;
+    if (P->pre_iter < 0 || P->max_iterations < 0 || P->num_sets < 0 || P->stop_nconv < 1) return -1;
+    int64_t wd = (n_det + 31) / 32, wv = (n_loc + 31) / 32, wo = (n_obs + 31) / 32;
+    int32_t E = H_indptr[n_det];
+    double *L0 = malloc(sizeof(double) * (size_t)(n_loc + 1));
+    for (int32_t j = 0; j < n_loc; ++j) {
+        double p = priors[j];
+        if (!(p > 0.0 && p < 1.0)) { free(L0); return -1; }
+        L0[j] = log((1.0 - p) / p);                          /* a1 */
+    }
+    for (int32_t e = 0; e < E; ++e)
+        if (H_indices[e] < 0 || H_indices[e] >= n_loc) { free(L0); return -1; }
+    graph_t g;
+    g.n_det = n_det; g.n_loc = n_loc; g.rptr = H_indptr; g.rcol = H_indices; g.L0 = L0;
+    g.cptr = calloc((size_t)n_loc + 1, sizeof(int32_t));
+    g.cedge = malloc(sizeof(int32_t) * (size_t)(E + 1));
+    for (int32_t e = 0; e < E; ++e) g.cptr[H_indices[e] + 1]++;
+    for (int32_t j = 0; j < n_loc; ++j) g.cptr[j + 1] += g.cptr[j];
+    {
+        int32_t *fill = calloc((size_t)n_loc + 1, sizeof(int32_t));
+        for (int32_t i = 0; i < n_det; ++i)
+            for (int32_t e = H_indptr[i]; e < H_indptr[i + 1]; ++e) {
+                int32_t j = H_indices[e];
+                g.cedge[g.cptr[j] + fill[j]++] = e;
+            }
+        free(fill);
+    }
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel
+    {
+        double *nu = malloc(sizeof(double) * (size_t)(E + 1));
+        double *mu = malloc(sizeof(double) * (size_t)(E + 1));
+        double *M = malloc(sizeof(double) * (size_t)(n_loc + 1));
+        double *Lam = malloc(sizeof(double) * (size_t)(n_loc + 1));
+        double *gam = malloc(sizeof(double) * (size_t)(n_loc + 1));
+        uint8_t *ehat = malloc((size_t)n_loc + 1);
+        uint8_t *best = malloc((size_t)n_loc + 1);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t s = 0; s < shots; ++s) {
+            uint32_t *corr = corrections + s * wv;
+            decode_one(&g, P, syndromes + s * wd, shot0 + (uint64_t)s, corr, stats + 4 * s, weights + s,
+                       trace_iters, trace ? trace + s * (int64_t)trace_iters * n_loc : NULL,
+                       nu, mu, M, Lam, gam, ehat, best);
+            if (pred_obs) {
+                uint32_t *po = pred_obs + s * wo;
+                memset(po, 0, sizeof(uint32_t) * (size_t)wo);
+                for (int32_t i = 0; i < n_obs; ++i) {
+                    int par = 0;
+                    for (int32_t e = O_indptr[i]; e < O_indptr[i + 1]; ++e) par ^= get_bit(corr, O_indices[e]);
+                    if (par) flip_bit(po, i);
+                }
+            }
+        }
+        free(nu); free(mu); free(M); free(Lam); free(gam); free(ehat); free(best);
+    }
+    free(L0); free(g.cptr); free(g.cedge);
+    return 0;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,254 @@
+"""Pins of the CPU oracle to things other than itself.
+
+  * Philox4x32-10: published known-answer vectors (Random123 / SC'11).
+  * Sampler: the fired faults are exactly the Philox words below floor(p 2^32);
+    syndromes equal H e mod 2 by an independent dense product; frequencies.
+  * Check + variable updates: on cycle-free Tanner graphs min-sum reaches the
+    exact min-marginals, which brute force gives independently.
+  * Memory term: a one-check, two-variable graph has a closed-form recurrence.
+  * Minimum-weight decoding of single errors on the [[60,12,6]] code (Table 13).
+  * Invariants on circuit-level DEMs: H e^ = s on every claimed success, the
+    reported weight, solution counts and leg limits.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import DecodeParams, unpack_bits, pack_bits
+from workloads.dem import circuit_dem, code_capacity_dem, dem_from_dense
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_philox_kat():
+    n = 0
+    for line in open(os.path.join(GOLD, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x, 16) for x in line.split()]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+        n += 1
+    assert n == 3
+
+
+def test_sampler_definition_and_syndrome():
+    D = circuit_dem("ZSZ-LP-60", 0.01, 2, "Z")
+    seed, shot0, shots = 0x1234_5678_9ABC, 1000, 40
+    syn, obs, err = oracle.sample(D, seed, shot0, shots, want_errors=True)
+    e = unpack_bits(err, D.n_loc)
+    thr = np.floor(D.priors * 2.0 ** 32)
+    for s in range(0, shots, 7):
+        shot = shot0 + s
+        want = np.zeros(D.n_loc, dtype=np.uint8)
+        for blk in range((D.n_loc + 3) // 4):
+            w = oracle.philox4x32_10([blk, shot & 0xFFFFFFFF, shot >> 32, 0], [seed & 0xFFFFFFFF, seed >> 32])
+            for t in range(4):
+                j = 4 * blk + t
+                if j < D.n_loc:
+                    want[j] = w[t] < thr[j]
+        assert np.array_equal(e[s], want)
+    Hd, Od = D.dense_H().astype(np.int64), D.dense_O().astype(np.int64)
+    assert np.array_equal(unpack_bits(syn, D.n_det), (e.astype(np.int64) @ Hd.T) % 2)
+    assert np.array_equal(unpack_bits(obs, D.n_obs), (e.astype(np.int64) @ Od.T) % 2)
+
+
+def test_sampler_frequencies():
+    pr = np.array([0.5, 0.25, 0.01, 0.001, 0.3, 0.07, 0.0, 1.0])
+    H = np.eye(len(pr), dtype=np.uint8)
+    D = dem_from_dense(H, pr)
+    n = 200_000
+    _, _, err = oracle.sample(D, 99, 0, n, want_errors=True)
+    f = unpack_bits(err, len(pr)).mean(0)
+    sig = np.sqrt(pr * (1 - pr) / n)
+    assert np.all(np.abs(f - pr) <= 5 * sig + 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# min-sum on trees equals brute-force min-marginals
+# ---------------------------------------------------------------------------
+def _random_tree_graph(rng, n_checks):
+    """Bipartite tree: every check has degree >= 2; returns dense H."""
+    checks = [[0, 1]]
+    nv = 2
+    for c in range(1, n_checks):
+        old = rng.integers(0, nv)                     # attach to an existing variable
+        k = int(rng.integers(1, 3))                   # plus 1-2 fresh variables
+        checks.append([old] + list(range(nv, nv + k)))
+        nv += k
+    H = np.zeros((n_checks, nv), dtype=np.uint8)
+    for i, vs in enumerate(checks):
+        H[i, vs] = 1
+    return H
+
+
+def _brute_min_marginals(H, L0, s):
+    V = H.shape[1]
+    best = {0: math.inf, 1: math.inf}
+    best_j = np.full((V, 2), math.inf)
+    Hi = H.astype(np.int64)
+    for bits in itertools.product((0, 1), repeat=V):
+        e = np.array(bits)
+        if np.any((Hi @ e) % 2 != s):
+            continue
+        w = float(e @ L0)
+        for j in range(V):
+            best_j[j, bits[j]] = min(best_j[j, bits[j]], w)
+    return best_j[:, 1] - best_j[:, 0]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_minsum_tree_min_marginals(seed):
+    rng = np.random.default_rng(seed)
+    H = _random_tree_graph(rng, int(rng.integers(3, 7)))
+    V = H.shape[1]
+    assert V <= 14
+    pr = rng.uniform(0.02, 0.45, V)
+    L0 = np.log((1 - pr) / pr)
+    e = (rng.random(V) < 0.3).astype(np.int64)
+    s = (H.astype(np.int64) @ e) % 2
+    # an extra check with no edges and syndrome 1 keeps the leg from stopping
+    Hx = np.vstack([H, np.zeros((1, V), dtype=np.uint8)])
+    sx = np.r_[s, 1]
+    D = dem_from_dense(Hx, pr)
+    T = 2 * Hx.shape[0] + 4
+    P = DecodeParams(gamma0=0.0, pre_iter=T, num_sets=0, max_iterations=0, stop_nconv=1)
+    r = oracle.decode(D, P, pack_bits(sx[None, :]), trace_iters=T)
+    M = r["trace"][0, T - 1]
+    want = _brute_min_marginals(H, L0, s)
+    assert np.allclose(M, want, rtol=1e-12, atol=1e-12)
+    assert r["stats"][0, 0] == 0 and r["stats"][0, 3] == T
+
+
+def test_memory_recurrence_closed_form():
+    """One check on two variables, syndrome 1, memory strength g.
+
+    nu_{->1} = -L_2(t) and nu_{->2} = -L_1(t), so M_1(t) = L_1(t) - L_2(t) =
+    -M_2(t).  With M(0) = L0 the first iteration has L(1) = L0 and
+    M_1(1) = a - b; from then on L_k(t) = (1-g) L0_k + g M_k(t-1) gives
+        M_1(t) = (1-g)(a-b) + 2g M_1(t-1),  t >= 2,
+    i.e. M_1(t) = (a-b) [(1-g) sum_{u<t-1} (2g)^u + (2g)^(t-1)].
+    Legs after the first use g = gamma_min = gamma_max and carry M, so the same
+    recurrence continues across the leg boundary.
+    """
+    pa, pb = 0.1, 0.3
+    a, b = math.log((1 - pa) / pa), math.log((1 - pb) / pb)
+    H = np.array([[1, 1], [0, 0]], dtype=np.uint8)
+    D = dem_from_dense(H, [pa, pb])
+    for g in (0.0, 0.125, 0.3, -0.2):
+        T0, T1 = 5, 4
+        P = DecodeParams(gamma0=g, pre_iter=T0, num_sets=1, max_iterations=T1, stop_nconv=5,
+                         gamma_min=g, gamma_max=g, seed=3)
+        r = oracle.decode(D, P, pack_bits(np.array([[1, 1]])), trace_iters=T0 + T1)
+        closed = [(a - b) * ((1 - g) * sum((2 * g) ** u for u in range(t - 1)) + (2 * g) ** (t - 1))
+                  for t in range(1, T0 + T1 + 1)]
+        tr = r["trace"][0]
+        assert np.allclose(tr[:, 0], closed, rtol=1e-12, atol=1e-12)
+        assert np.allclose(tr[:, 1], -np.array(closed), rtol=1e-12, atol=1e-12)
+        assert r["stats"][0, 2] == 2 and r["stats"][0, 3] == T0 + T1
+
+
+def test_gamma_draw_range_and_stream():
+    """Legs >= 1 draw g_j from stream 1 of the decoder seed: with a single
+    variable the first iteration of leg 1 gives M = (1-g) a + g M_prev exactly."""
+    p = 0.2
+    a = math.log((1 - p) / p)
+    H = np.zeros((1, 1), dtype=np.uint8)              # one check with no edges, syndrome 1
+    D = dem_from_dense(H, [p])
+    P = DecodeParams(gamma0=0.5, pre_iter=1, num_sets=3, max_iterations=1, stop_nconv=9,
+                     gamma_min=-0.24, gamma_max=0.66, seed=0xABCDEF)
+    shot = 17
+    r = oracle.decode(D, P, pack_bits(np.array([[1]])), shot0=shot, trace_iters=4)
+    M = r["trace"][0, :, 0]
+    assert np.isclose(M[0], a)                            # M(0) = a, so L(1) = a
+    for leg in (1, 2, 3):
+        w = oracle.philox4x32_10([leg * 1, shot, 0, 1], [0xABCDEF, 0])[0]
+        g = -0.24 + 0.9 * ((int(w) >> 8) / 2.0 ** 24)
+        assert -0.24 <= g <= 0.66
+        assert np.isclose(M[leg], (1 - g) * a + g * M[leg - 1], rtol=1e-13)
+
+
+def test_mw_single_errors_60():
+    """[[60,12,6]] code capacity: no nonzero vector of ker H_X has weight <= 2,
+    so each single Z error is the unique minimum-weight solution of its
+    syndrome; Relay-BP must return it exactly."""
+    D = code_capacity_dem("ZSZ-LP-60", 0.01)
+    Hd = D.dense_H().astype(np.int64)
+    V = D.n_loc
+    for j1, j2 in itertools.combinations(range(V), 2):
+        assert np.any(Hd[:, j1] ^ Hd[:, j2])
+    assert np.all(Hd.sum(0) > 0)
+    E = np.eye(V, dtype=np.uint8)
+    syn = pack_bits((E.astype(np.int64) @ Hd.T) % 2)
+    r = oracle.decode(D, DecodeParams(num_sets=20, seed=5), syn)
+    assert np.all(r["stats"][:, 0] == 1)
+    assert np.array_equal(unpack_bits(r["corrections"], V), E)
+
+
+def test_mw_double_errors_60_weight_bound():
+    """Weight-2 errors: every converged answer satisfies H e^ = s and has
+    weight >= the brute-force minimum weight of its syndrome (<= 2)."""
+    D = code_capacity_dem("ZSZ-LP-60", 0.01)
+    Hd = D.dense_H().astype(np.int64)
+    V = D.n_loc
+    pairs = list(itertools.combinations(range(V), 2))[::11]
+    E = np.zeros((len(pairs), V), dtype=np.uint8)
+    for t, (a, b) in enumerate(pairs):
+        E[t, [a, b]] = 1
+    S = (E.astype(np.int64) @ Hd.T) % 2
+    single = {tuple(Hd[:, j]) for j in range(V)}
+    r = oracle.decode(D, DecodeParams(num_sets=20, seed=5), pack_bits(S))
+    eh = unpack_bits(r["corrections"], V).astype(np.int64)
+    conv = r["stats"][:, 0] == 1
+    assert conv.mean() > 0.95
+    assert np.array_equal((eh[conv] @ Hd.T) % 2, S[conv])
+    for t in np.nonzero(conv)[0]:
+        mw = 0 if not S[t].any() else (1 if tuple(S[t]) in single else 2)
+        assert eh[t].sum() >= mw
+
+
+def test_invariants_circuit_level():
+    D = circuit_dem("ZSZ-LP-60", 0.004, 3, "Z")
+    syn, obs, _ = oracle.sample(D, 11, 0, 300)
+    P = DecodeParams(num_sets=30, stop_nconv=3, gamma_min=-0.15, gamma_max=0.61, seed=1)
+    r = oracle.decode(D, P, syn)
+    st = r["stats"]
+    eh = unpack_bits(r["corrections"], D.n_loc).astype(np.int64)
+    S = unpack_bits(syn, D.n_det).astype(np.int64)
+    Hd = D.dense_H().astype(np.int64)
+    conv = st[:, 0] == 1
+    assert conv.mean() > 0.9
+    assert np.array_equal((eh[conv] @ Hd.T) % 2, S[conv])
+    L0 = np.log((1 - D.priors) / D.priors)
+    assert np.allclose(r["weights"], eh @ L0, rtol=1e-12)
+    assert np.all(st[:, 1] <= 3) and np.all(st[:, 2] <= 31)
+    assert np.all(st[conv, 1] >= 1) and np.all(st[~conv, 1] == 0)
+    assert np.all(st[:, 3] <= 80 + 30 * 60)
+    # stop after stop_nconv solutions: a shot stops early only once it has them
+    assert np.all((st[:, 2] == 31) | (st[:, 1] == 3))
+    Od = D.dense_O().astype(np.int64)
+    assert np.array_equal(unpack_bits(r["pred_obs"], D.n_obs), (eh @ Od.T) % 2)
+
+
+def test_stop_all_runs_every_leg():
+    D = circuit_dem("ZSZ-LP-60", 0.004, 2, "Z")
+    syn, _, _ = oracle.sample(D, 12, 0, 20)
+    P = DecodeParams(num_sets=4, stop_nconv=1, stop_all=True, seed=2)
+    r = oracle.decode(D, P, syn)
+    assert np.all(r["stats"][:, 2] == 5)
+
+
+def test_deterministic_and_shard_invariant():
+    """Counter-based draws: decoding shots [0,40) at once equals two shards."""
+    D = circuit_dem("ZSZ-LP-60", 0.004, 2, "Z")
+    syn, _, _ = oracle.sample(D, 13, 0, 40)
+    P = DecodeParams(num_sets=10, seed=4)
+    full = oracle.decode(D, P, syn, shot0=0)
+    a = oracle.decode(D, P, syn[:25], shot0=0)
+    b = oracle.decode(D, P, syn[25:], shot0=25)
+    assert np.array_equal(full["corrections"], np.vstack([a["corrections"], b["corrections"]]))
+    assert np.array_equal(full["stats"], np.vstack([a["stats"], b["stats"]]))

@@ -1,0 +1,214 @@
+"""Pins of the input generators (ZSZ-LP codes, circuit DEMs) to the paper's tables."""
+import os
+
+import numpy as np
+import pytest
+
+from workloads.zsz import load_code, gf2_rank, ZSZGroup
+from workloads.dem import circuit_dem, code_capacity_dem, memory_circuit
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+def _girth(H):
+    """Tanner-graph girth by BFS from every vertex (plain)."""
+    m, n = H.shape
+    adj = [[] for _ in range(m + n)]
+    for i, j in zip(*np.nonzero(H)):
+        adj[i].append(m + j)
+        adj[m + j].append(i)
+    best = 10 ** 9
+    for s in range(m + n):
+        dist = {s: 0}
+        par = {s: -1}
+        q = [s]
+        for u in q:
+            for w in adj[u]:
+                if w not in dist:
+                    dist[w] = dist[u] + 1
+                    par[w] = u
+                    q.append(w)
+                elif par[u] != w:
+                    best = min(best, dist[u] + dist[w] + 1)
+    return best
+
+
+def _cycles46(H):
+    """Exact simple 4- and 6-cycle counts of a Tanner graph.
+
+    4-cycles: check pairs sharing o variables give C(o,2).  6-cycles: for each
+    unordered check triple with pairwise overlaps o12,o23,o13 and common
+    variables T, choose one variable per pair, all distinct:
+    o12*o23*o13 - T*(o12+o23+o13-2) (inclusion-exclusion).
+    """
+    H = H.astype(np.int64)
+    O = H @ H.T
+    m = H.shape[0]
+    np.fill_diagonal(O, 0)
+    c4 = int((O * (O - 1) // 2)[np.triu_indices(m, 1)].sum())
+    c6 = 0
+    nbr = [np.nonzero(O[i])[0] for i in range(m)]
+    for i in range(m):
+        for j in nbr[i]:
+            if j <= i:
+                continue
+            for k in nbr[j]:
+                if k <= j or O[i, k] == 0:
+                    continue
+                T = int((H[i] & H[j] & H[k]).sum())
+                o1, o2, o3 = O[i, j], O[j, k], O[i, k]
+                c6 += int(o1 * o2 * o3 - T * (o1 + o2 + o3 - 2))
+    return c4, c6
+
+
+@pytest.mark.parametrize("row", _table("zsz_lp_tables.txt"), ids=lambda r: r[0])
+def test_code_tables(row):
+    name, n, k, gl, gr, c4, c6, zc, nu2, nu3 = row[0], *map(int, row[1:])
+    code = load_code(name)
+    G = code.G
+    assert pow(code.q, code.l2, code.l1) == 1
+    assert code.n == n
+    # CSS orthogonality H_X H_Z^T = 0 (Eq. 5-block CSS orth)
+    assert not np.any((code.H_X.astype(np.int64) @ code.H_Z.T.astype(np.int64)) % 2)
+    # full-rank seeds give k = l (Sec. 2.4) and match Table 1
+    assert gf2_rank(code.H_left) == code.ell and gf2_rank(code.H_right) == code.ell
+    assert code.k == k == code.ell
+    # weight-9 checks; qubit degrees 3 on Q1..Q4 and 6 on Q5
+    for H in (code.H_X, code.H_Z):
+        assert set(H.sum(1).tolist()) == {9}
+        cw = H.sum(0)
+        assert set(cw[:4 * code.ell].tolist()) == {3} and set(cw[4 * code.ell:].tolist()) == {6}
+    # Table 8: cycle counts summed over H_X and H_Z
+    a, b = _cycles46(code.H_X), _cycles46(code.H_Z)
+    assert a[0] + b[0] == c4 and a[1] + b[1] == c6
+    # Table 11: center size; Table 6: element-order census
+    assert len(G.center()) == zc
+    orders = [G.element_order(g) for g in range(G.order)]
+    assert orders.count(2) == nu2 and orders.count(3) == nu3
+    # Table 2: classical girths (small codes only; BFS is quadratic)
+    if code.ell <= 64:
+        assert _girth(code.H_left) == gl and _girth(code.H_right) == gr
+
+
+def test_equivariance_and_center():
+    """R[g] H_left = H_left R[g]^{+2} (Eq. H_left symmetry) and H P_z^{+5} = P_z^{+2} H (App. D)."""
+    code = load_code("ZSZ-LP-160")
+    G = code.G
+    from workloads.zsz import R_mat, L_mat
+    for g in range(G.order):
+        Rg = R_mat(G, [g])
+        lhs = (Rg.astype(int) @ code.H_left) % 2
+        rhs = (code.H_left.astype(int) @ np.kron(np.eye(2, dtype=int), Rg)) % 2
+        assert np.array_equal(lhs, rhs)
+    for z in G.center():
+        P = L_mat(G, [z]).astype(int)
+        for H in (code.H_X, code.H_Z):
+            assert np.array_equal((H @ np.kron(np.eye(5, dtype=int), P)) % 2, (np.kron(np.eye(2, dtype=int), P) @ H) % 2)
+
+
+def test_ogm_generators_160():
+    """Table 7 generators satisfy u_L a~ + v_L b~ = 0 and c~ u_R + d~ v_R = 0 (Eq. generator validity)."""
+    code = load_code("ZSZ-LP-160")
+    G = code.G
+
+    def alg(terms):
+        v = np.zeros(G.order, dtype=np.uint8)
+        for (a, b) in terms:
+            v[G.elem(a, b)] ^= 1
+        return v
+
+    def mul(u, v):
+        out = np.zeros(G.order, dtype=np.uint8)
+        for g in np.nonzero(u)[0]:
+            for h in np.nonzero(v)[0]:
+                out[G.mul[g, h]] ^= 1
+        return out
+
+    def bar(u):
+        out = np.zeros_like(u)
+        out[G.inv[np.nonzero(u)[0]]] = 1
+        return out
+
+    uL = alg([(8, 0), (11, 0), (4, 1), (8, 1), (13, 1)])
+    vL = alg([(0, 0), (10, 0), (15, 0), (3, 1), (11, 1)])
+    uR = alg([(3, 0), (8, 0), (13, 0), (3, 1), (5, 1), (7, 1), (10, 1)])
+    vR = alg([(5, 0), (8, 0), (10, 1)])
+    a, b = alg(code.a_terms), alg(code.b_terms)
+    c, d = alg(code.c_terms), alg(code.d_terms)
+    assert not np.any(mul(uL, bar(a)) ^ mul(vL, bar(b)))
+    assert not np.any(mul(bar(c), uR) ^ mul(bar(d), vR))
+    assert uL.sum() + vL.sum() == code.d and uR.sum() + vR.sum() == code.d
+
+
+def test_dem_160_structure():
+    d = 10
+    D = circuit_dem("ZSZ-LP-160", 0.001, d, "Z")
+    code = load_code("ZSZ-LP-160")
+    assert D.n_det == 2 * code.ell * (d + 1)            # Table 5: N_det = 2 l (d+1)
+    assert D.n_obs == code.k
+    assert np.all(np.diff(D.H_indptr) >= 2)             # every detector sees >= 2 mechanisms
+    assert np.all((D.priors > 0) & (D.priors < 0.01))
+    Dx = circuit_dem("ZSZ-LP-160", 0.001, d, "X")
+    assert Dx.n_det == D.n_det and Dx.n_obs == D.n_obs
+
+
+def test_dem_noiseless_limit_and_scaling():
+    """Fault probabilities scale with p and the structure does not depend on p."""
+    a = circuit_dem("ZSZ-LP-60", 0.001, 3, "Z")
+    b = circuit_dem("ZSZ-LP-60", 0.002, 3, "Z")
+    assert np.array_equal(a.H_indices, b.H_indices) and np.array_equal(a.H_indptr, b.H_indptr)
+    r = b.priors / a.priors
+    assert np.all((r > 1.9) & (r <= 2.0 + 1e-12))
+
+
+@pytest.mark.parametrize("row", _table("dem_sizes.txt")[:1], ids=lambda r: r[0])
+def test_dem_sizes_table5(row):
+    """(N_det, N_loc) of Table 5 (ZSZ-LP-320; 390 and 550 run in the slow set)."""
+    name, rounds, ndet, nloc = row[0], *map(int, row[1:])
+    D = circuit_dem(name, 0.001, rounds, "Z")
+    assert (D.n_det, D.n_loc) == (ndet, nloc)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("row", _table("dem_sizes.txt")[1:], ids=lambda r: r[0])
+def test_dem_sizes_table5_large(row):
+    if not os.environ.get("RUN_SLOW"):
+        pytest.skip("set RUN_SLOW=1 for the 390/550 DEM builds")
+    name, rounds, ndet, nloc = row[0], *map(int, row[1:])
+    D = circuit_dem(name, 0.001, rounds, "Z")
+    assert (D.n_det, D.n_loc) == (ndet, nloc)
+
+
+def test_dem_single_fault_consistency():
+    """A tiny circuit: every column's detector set is what one fault propagates to.
+
+    Cross-check by an independent dense GF(2) propagation of a single X error on
+    a data qubit before round 1: it must flip exactly the Z-checks touching it
+    in round 1 (time-like pair) -- i.e. the column equals H_Z[:, q] in round 0.
+    """
+    code = load_code("ZSZ-LP-60")
+    D = circuit_dem("ZSZ-LP-60", 0.001, 2, "Z")
+    Hd = D.dense_H()
+    cols = {tuple(np.nonzero(Hd[:, j])[0]) for j in range(D.n_loc)}
+    for q in range(code.n):
+        want = tuple(np.nonzero(code.H_Z[:, q])[0])           # detectors of round 1
+        assert want in cols
+    # a measurement flip of Z-ancilla i in round 1 flips detectors (1,i) and (2,i)
+    l2 = 2 * code.ell
+    for i in range(l2):
+        assert (i, l2 + i) in cols
+
+
+def test_code_capacity_dem():
+    D = code_capacity_dem("ZSZ-LP-160", 0.05)
+    assert (D.n_det, D.n_loc, D.n_obs) == (64, 160, 32)
+    assert D.n_edges == 576
