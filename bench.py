@@ -1,0 +1,321 @@
+"""Benchmark: decoded shots/s of batched Relay-BP at p = 0.1% circuit noise.
+
+Workload (the configuration the metric is quoted on): ZSZ-LP-160, Table 10
+syndrome-extraction schedule, d = 10 rounds, Z-memory, idling-free
+depolarising circuit noise p = 0.001 (DEM 704 detectors x 10,400 faults), the
+paper's decoder settings (gamma0 0.125, pre_iter 80, num_sets 1000,
+max_iterations 60, stop_nconv 5, FP32 messages) with the ZSZ-LP-160 gamma
+interval [-0.15, 0.61] of Table 9; 10^6 shots per run (steps x batch).
+
+A step is one pass of the hot path over one batch: Philox fault sampling
+(s = H e, obs = O e), the persistent Relay-BP decode, and failure accounting.
+
+Arms:
+  default           the CUDA path (inputs resident on the device when timing
+                    starts; `e2e` repeats the decode through the host-buffer
+                    entry point with the copies inside the timed region)
+  --impl reference  the FP64 CPU oracle on the host cores, on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(code="ZSZ-LP-160", rounds=10, basis="Z", p=0.001)
+DECODER = dict(gamma0=0.125, pre_iter=80, num_sets=1000, max_iterations=60, stop_nconv=5,
+               gamma_min=-0.15, gamma_max=0.61, seed=0x5EED)
+METRIC = "decoded shots/s at p=0.1% circuit noise, learned vs plain Relay-BP at equal LER"
+SAMPLE_SEED = 2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=125_000, help="shots per step and per GPU")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=96, help="shots of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _dem():
+    from workloads.dem import circuit_dem
+    return circuit_dem(WORKLOAD["code"], WORKLOAD["p"], WORKLOAD["rounds"], WORKLOAD["basis"])
+
+
+def _config(dem, batch, steps, world, extra=None):
+    c = {"workload": f"{WORKLOAD['code']} circuit-level Z-memory, d={WORKLOAD['rounds']}, p={WORKLOAD['p']}, "
+                     f"DEM {dem.n_det}x{dem.n_loc} (E={dem.n_edges}), plain Relay-BP",
+         "decoder": dict(DECODER), "shots_per_step_per_gpu": batch, "steps": steps,
+         "shots_total": batch * steps * world,
+         "l2": "flushed between steps (256 MiB write); DEM structure (~1 MB) stays cache-resident by design",
+         "parallelism": f"replicas x{world} (shot ranges)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_baseline(dem, n_shots):
+    import numpy as np
+    import oracle
+    syn, _, _ = oracle.sample(dem, SAMPLE_SEED, 10**9, n_shots)
+    p = oracle.DecodeParams(**DECODER)
+    t0 = time.perf_counter()
+    oracle.decode(dem, p, syn, shot0=10**9)
+    dt = time.perf_counter() - t0
+    return n_shots / dt, dt, oracle.max_threads()
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    dem = _dem()
+    syn, _, _ = oracle.sample(dem, SAMPLE_SEED, 0, a.cpu_sample * (a.steps + a.warmup))
+    p = oracle.DecodeParams(**DECODER)
+    n = a.cpu_sample
+    for w in range(a.warmup):
+        oracle.decode(dem, p, syn[w * n:(w + 1) * n], shot0=w * n)
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        b = (a.warmup + k) * n
+        oracle.decode(dem, p, syn[b:b + n], shot0=b)
+    dt = time.perf_counter() - t0
+    v = n * a.steps / dt
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "shots/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox-sampled syndromes of the circuit DEM)",
+            "config": _config(dem, n, a.steps, 1, {"arm": "FP64 CPU oracle, OpenMP over shots"}),
+            "cpu_baseline": {"value": v, "unit": "shots/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} shots per step x {a.steps} steps"},
+            "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2607_27644_b300 import relaybp as R
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dem = _dem()
+    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **DECODER))
+    B, K, W = a.batch, a.steps, a.warmup
+    st = torch.cuda.Stream(device=dev)
+    syn = torch.empty((B, h.wc), dtype=torch.int32, device=dev)
+    obs = torch.empty((B, h.wk), dtype=torch.int32, device=dev)
+    pobs = torch.empty((B, h.wk), dtype=torch.int32, device=dev)
+    stats = torch.empty((B, 6), dtype=torch.int32, device=dev)
+    counters = torch.zeros(4, dtype=torch.int64, device=dev)
+    iters_total = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
+    base = rank * B * (K + W)
+
+    def step(k, dec_events=None):
+        shot0 = base + k * B
+        R.relaybp_sample(h, SAMPLE_SEED, shot0, B, syn, obs, None, st)
+        if dec_events:
+            dec_events[0].record(st)
+        R.relaybp_decode_batch(h, syn, shot0, B, None, pobs, stats, st)
+        if dec_events:
+            dec_events[1].record(st)
+        R.relaybp_count_failures(h, pobs, obs, stats, B, counters, st)
+
+    with torch.cuda.stream(st):
+        for w in range(W):
+            step(K + w)
+            flush.fill_(w)
+        torch.cuda.synchronize()
+        counters.zero_()
+        iters_total.zero_()
+        dec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = R.relaybp_launch_count(h)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t_start.record(st)
+            for k in range(K):
+                step(k, dec_ev[k])
+                iters_total += stats[:, 3].sum()
+                if k + 1 < K:
+                    flush.fill_(k)
+            t_end.record(st)
+            torch.cuda.synchronize()
+        launches = R.relaybp_launch_count(h) - l0
+        if world > 1:
+            dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    dec_ms = [e0.elapsed_time(e1) for e0, e1 in dec_ev]
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    cnt = counters.clone()
+    it = iters_total.clone()
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt)
+        dist.all_reduce(it)
+    ms_max = float(tmax.item())
+    shots_total = B * K * world
+    value = shots_total / (ms_max / 1e3)
+
+    # ---- end to end through the host-buffer entry point --------------------
+    e2e = None
+    if not a.no_e2e:
+        with torch.cuda.stream(st):
+            hsyn = []
+            for k in range(K):
+                R.relaybp_sample(h, SAMPLE_SEED, base + k * B, B, syn, obs, None, st)
+                t = torch.empty((B, h.wc), dtype=torch.int32, pin_memory=True)
+                t.copy_(syn, non_blocking=False)
+                hsyn.append(t)
+            hp = torch.empty((B, h.wk), dtype=torch.int32, pin_memory=True)
+            hs = torch.empty((B, 6), dtype=torch.int32, pin_memory=True)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for k in range(K):
+                R.relaybp_decode_host(h, hsyn[k], base + k * B, B, hp, hs, st)
+            e2e_s = time.perf_counter() - t0
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": shots_total / float(t.item()), "unit": "shots/s", "h2d_bytes_per_step": B * h.wc * 4,
+               "d2h_bytes_per_step": B * (h.wk * 4 + 24),
+               "path": "relaybp_decode_host: pinned host syndromes -> device -> decode -> host predicted "
+                       "observables + per-shot stats, synchronised each step"}
+
+    # ---- roofline of the dominant kernel (relay_decode_kernel) --------------
+    sink = torch.zeros(4096, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(st):
+        reps = 1 << 14
+        for _ in range(2):
+            R.relaybp_probe_smem_read(reps, sink, st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        nb = 0.0
+        for _ in range(5):
+            nb += R.relaybp_probe_smem_read(reps, sink, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+    smem_gbs = nb / (e0.elapsed_time(e1) / 1e3) / 1e9
+    iters_rank = int(iters_total.item())
+    E, V, C = dem.n_edges, dem.n_loc, dem.n_det
+    b_m = 4
+    bytes_per_iter = 4 * b_m * E + 16 * V + (V + C) / 8.0
+    dec_avg_s = sum(dec_ms) / len(dec_ms) / 1e3
+    achieved = (iters_rank / K) * bytes_per_iter / dec_avg_s / 1e9
+    edge_updates = iters_rank * E / (sum(dec_ms) / 1e3)
+    roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
+            "traffic": None,
+            "kernel": "relay_decode_kernel<float>",
+            "algorithmic_bytes": "per shot-iteration 4*b_m*E + 16*V + (V+C)/8 (b_m=4)",
+            "peak_source": "measured live: conflict-free 16-B shared-memory loads on all SMs (relaybp_probe_smem_read)",
+            "edge_updates_per_s": edge_updates, "decode_ms_per_launch": dec_avg_s * 1e3,
+            "mean_iterations_per_shot": iters_rank / (B * K)}
+    c = cnt.cpu().tolist()
+    line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEM (no dataset)",
+            "config": _config(dem, B, K, world), "clocks": clk.summary(), "gpu_launches": launches * world,
+            "roofline": roof, "e2e": e2e,
+            "ler": {"shots": c[0], "failures": c[3], "nonconverged": c[1], "logical": c[2],
+                    "block_ler": c[3] / max(1, c[0])}}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, dt, cores = _cpu_baseline(dem, a.cpu_sample)
+        line["cpu_baseline"] = {"value": v, "unit": "shots/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{a.cpu_sample} shots of the same workload ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.relaybp_destroy(h)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

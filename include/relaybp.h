@@ -1,0 +1,182 @@
+/*
+ * relaybp.h -- C ABI of the B300 (sm_103a) Relay-BP decoding library.
+ *
+ * The library samples syndromes from a detector error model (DEM) and decodes
+ * them with Relay-BP: min-sum belief propagation with disordered memory
+ * strengths, run as a chain of relay legs that keeps the lowest-weight of up to
+ * stop_nconv valid solutions.  arXiv 2607.27644 uses this decoder for every
+ * circuit-level result (Sec. 6.1, decoder configuration list: gamma0 = 0.125,
+ * pre_iter = 80, num_sets = 1000, max_iterations = 60, stop_nconv = 5, fp32
+ * messages, flooding schedule; gamma intervals in Table 9; DEM sizes in
+ * Table 5).  The paper cites Relay-BP without printing its update rule; the
+ * rule implemented here is:
+ *
+ *   L0_j    = log((1 - p_j) / p_j)                                 (host, FP64)
+ *   L_j(t)  = (1 - g_j) L0_j + g_j M_j(t-1)                       memory term
+ *   mu_ji   = L_j(t) + sum_{i' != i} nu_i'j(t-1)
+ *   nu_ij   = (-1)^{s_i} prod_{j' != j} sgn(mu_j'i) min_{j' != j} |mu_j'i|
+ *   M_j(t)  = L_j(t) + sum_i nu_ij(t),   e^_j = [M_j(t) < 0]
+ *   a leg stops at its first t with H e^ = s; leg 0 runs pre_iter iterations
+ *   at g_j = gamma0, legs 1..num_sets run max_iterations at
+ *   g_j ~ U[gamma_min, gamma_max]; M carries across legs, messages reset.
+ *
+ * Conventions shared by every call:
+ *   - Status: 0 on success, a negative RELAYBP_ERR_* code otherwise;
+ *     relaybp_last_error() returns a message for the calling thread.  No call
+ *     aborts the process or traps the device.
+ *   - Bit vectors are packed little-endian into uint32 words: bit b lives in
+ *     word b / 32 at position b % 32.  A batch of vectors is row-major, one row
+ *     of ceil(nbits / 32) words per shot.
+ *   - "d_" pointers are device memory owned by the caller; "h_" pointers are
+ *     host memory owned by the caller.  Structures passed to relaybp_build are
+ *     copied; the caller may free them on return.
+ *   - Calls taking a stream are asynchronous on that stream (NULL = the legacy
+ *     default stream); the caller synchronises before reading results.  A
+ *     handle is not thread-safe: use one handle per host thread and stream.
+ *   - Random draws are counter-based (Philox4x32-10, Salmon et al. SC'11):
+ *     fault j of shot s uses word j of stream 0 under key `seed`; the memory
+ *     strength of variable j in leg r uses word r*4*ceil(V/4) + j of stream 1
+ *     under key params.seed.  Results therefore depend only on (seed, global
+ *     shot index), never on batching or sharding.
+ */
+#ifndef RELAYBP_H
+#define RELAYBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RELAYBP_OK = 0,
+    RELAYBP_ERR_INVALID = -1,   /* bad argument: null pointer, size, index or value out of range */
+    RELAYBP_ERR_CUDA = -2,      /* a CUDA runtime call failed; message has the CUDA error string */
+    RELAYBP_ERR_UNSUPPORTED = -3/* valid input the library does not handle (e.g. too large for a kernel) */
+};
+
+enum {                           /* message storage precision */
+    RELAYBP_MSG_F64 = 0,         /* FP64 storage and arithmetic */
+    RELAYBP_MSG_F32 = 1          /* FP32 storage and arithmetic (the paper's proc_float = fp32) */
+};
+
+/* Compressed sparse rows of a binary matrix, host memory.
+ * indptr[rows + 1] nondecreasing with indptr[0] = 0; indices[indptr[rows]]
+ * column indices in [0, cols), strictly increasing within each row. */
+typedef struct {
+    int32_t rows, cols;
+    const int32_t *indptr;
+    const int32_t *indices;
+} relaybp_csr;
+
+/* Decoder parameters; names follow the paper's decoder configuration list. */
+typedef struct {
+    double gamma0;              /* memory strength of leg 0 (paper: 0.125) */
+    int32_t pre_iter;           /* iteration cap of leg 0 (paper: 80), >= 1 */
+    int32_t num_sets;           /* number of relay legs after leg 0 (paper: 1000), >= 0 */
+    int32_t max_iterations;     /* iteration cap of each later leg (paper: 60), >= 1 */
+    int32_t stop_nconv;         /* stop after this many solutions (paper: 5), >= 1 */
+    double gamma_min, gamma_max;/* memory-strength interval of legs >= 1 (Table 9) */
+    int32_t msg_dtype;          /* RELAYBP_MSG_* */
+    int32_t stop_all;           /* 1: run every leg regardless of solutions (the paper's 'All') */
+    int32_t carry_messages;     /* 1: keep check-to-variable messages across legs */
+    int32_t reserved;           /* must be 0 */
+    uint64_t seed;              /* key of the memory-strength draws */
+} relaybp_params;
+
+/* Per-shot decoding statistics (24 bytes). */
+typedef struct {
+    int32_t converged;          /* 1 if at least one leg reached H e^ = s */
+    int32_t nsol;               /* number of solutions found (<= stop_nconv unless stop_all) */
+    int32_t legs;               /* legs run, leg 0 included */
+    int32_t iters;              /* BP iterations run over all legs */
+    double weight;              /* sum_j e^_j L0_j of the returned correction, FP64 */
+} relaybp_shot_stats;
+
+typedef struct relaybp_handle relaybp_handle;
+
+/* Build a decoder for one DEM on the current CUDA device.
+ * H: detector x fault check matrix (C rows, V columns); every row has 0 or at
+ *    least 2 entries, C < 2^20, nnz < 2^30.
+ * priors: V fault probabilities, each in (0, 1).
+ * obs: observable x fault matrix (K rows, V columns), or NULL for K = 0.
+ * params: decoder parameters (validated here; copied into the handle).
+ * out: receives the handle, which owns all device memory it allocates.
+ * The DEM is copied to the device synchronously; the handle records the
+ * current device and must be used with that device current. */
+int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr *obs,
+                  const relaybp_params *params, relaybp_handle **out);
+
+/* Replace the decoder parameters of an existing handle (validated as above). */
+int relaybp_set_params(relaybp_handle *h, const relaybp_params *params);
+
+/* Query sizes: n_det (C), n_loc (V), n_obs (K), n_edges (nnz of H). */
+int relaybp_sizes(const relaybp_handle *h, int32_t *n_det, int32_t *n_loc, int32_t *n_obs, int64_t *n_edges);
+
+/* Draw `shots` shots with global indices shot0 .. shot0 + shots - 1.
+ * Fault j of a shot fires iff its Philox word is below floor(p_j * 2^32).
+ * d_syndromes: [shots][ceil(C/32)] words = H e;  d_obs: [shots][ceil(K/32)]
+ * words = O e (may be NULL); d_errors: [shots][ceil(V/32)] fired faults (may
+ * be NULL).  Exact integer work: bit-identical to any other implementation of
+ * the same definition. */
+int relaybp_sample(relaybp_handle *h, uint64_t seed, uint64_t shot0, int64_t shots,
+                   uint32_t *d_syndromes, uint32_t *d_obs, uint32_t *d_errors, void *cuda_stream);
+
+/* Decode `shots` syndromes d_syndromes [shots][ceil(C/32)] whose global shot
+ * indices start at shot0 (they key the memory-strength draws).
+ * d_corrections: [shots][ceil(V/32)] the returned e^ (lowest-weight solution,
+ *   earliest on ties; the last iterate if no leg converged), or NULL.
+ * d_pred_obs: [shots][ceil(K/32)] O e^, or NULL.
+ * d_stats: [shots] per-shot statistics, or NULL.
+ * One persistent kernel decodes the whole batch: each thread block takes the
+ * next undecoded shot from a device work counter owned by the handle, so
+ * blocks whose shots finish early move on at once. */
+int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                         uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
+                         void *cuda_stream);
+
+/* Diagnostic variant of relaybp_decode_batch for parity checks: also writes
+ * the marginals M_j after each of the first trace_iters iterations (counted
+ * over all legs) to d_trace [shots][trace_iters][V] as FP64 (entries past a
+ * shot's last iteration are left untouched).  d_stats may be NULL. */
+int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                         int32_t trace_iters, double *d_trace, relaybp_shot_stats *d_stats, void *cuda_stream);
+
+/* Same as relaybp_decode_batch with host buffers: copies h_syndromes to the
+ * device, decodes, copies the results back, and synchronises the stream before
+ * returning.  Staging buffers are owned by the handle and grow on demand.
+ * h_pred_obs and h_stats may be NULL. */
+int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
+                        uint32_t *h_pred_obs, relaybp_shot_stats *h_stats, void *cuda_stream);
+
+/* Failure accounting (paper Sec. 7, Outlook, "Improved decoding": failures
+ * are either flagged nonconvergences or undetected logical errors).  Adds to
+ * d_counters[0] the shots counted, [1] shots that did not converge, [2]
+ * converged shots whose predicted observables differ from d_true_obs, [3]
+ * all failures ([1] + [2]).  d_counters: 4 x uint64, caller-zeroed. */
+int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const uint32_t *d_true_obs,
+                           const relaybp_shot_stats *d_stats, int64_t shots, unsigned long long *d_counters,
+                           void *cuda_stream);
+
+/* Number of kernel launches this handle has issued since it was built. */
+int64_t relaybp_launch_count(const relaybp_handle *h);
+
+/* Measurement utility (no paper counterpart): launch a kernel on the current
+ * device that streams conflict-free 16-byte shared-memory loads, `reps` per
+ * thread, over every SM.  *bytes_read receives the bytes the launch reads;
+ * dividing by its event-timed duration gives the shared-memory bandwidth that
+ * bounds the decode kernel.  d_sink: one float per block, device memory. */
+int relaybp_probe_smem_read(int32_t reps, float *d_sink, double *bytes_read, void *cuda_stream);
+
+/* Free the handle and every device allocation it owns (synchronises its
+ * device first).  NULL is accepted. */
+int relaybp_destroy(relaybp_handle *h);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *relaybp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELAYBP_H */

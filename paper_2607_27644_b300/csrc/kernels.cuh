@@ -1,0 +1,445 @@
+// Device kernels of the Relay-BP hot path (sm_103a).
+//
+//   sample_kernel         a2: Philox Bernoulli fault draws, s = H e, obs = O e
+//   relay_decode_kernel   a3-a8: min-sum check update, memory-biased variable
+//                         update, residual, relay legs, minimum-weight select,
+//                         persistent work queue (early-exit compaction)
+//   count_failures_kernel a9: nonconvergences and undetected logical errors
+//
+// Relay-BP is the decoder arXiv 2607.27644 runs for all circuit-level results
+// (Sec. 6.1, decoder configuration list); the update rule is spelled out in
+// include/relaybp.h.
+//
+// Layout of one shot's decoder state in shared memory (per thread block):
+//   M[V], A[V]        marginal M_j(t) and A_j = L_j(t+1) + sum_i nu_ij(t)
+//   m1[C], m2[C]      smallest and second-smallest |mu| of each check row
+//   am[C]             sign-bit index of the row's argmin edge | parity << 31,
+//                     parity = s_i xor (xor of the row's mu sign bits)
+//   sgn[NW]           sign bit of mu for every edge; each row's bits start on
+//                     a 32-bit word boundary so a warp writes them by ballot
+//   ehat[WV], best[WV], res[WC], syn[WC], obsacc[WK]   bit vectors
+// With this compressed check state a message is rebuilt on demand:
+//   nu_ij = (-1)^(parity_i xor sign_e) * (e == argmin_i ? m2_i : m1_i),
+// which equals the leave-one-out product of signs and minimum of magnitudes.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "philox.cuh"
+
+namespace relaybp {
+
+struct DevDEM {
+    int32_t C, V, K;
+    int64_t E;
+    int32_t NW;                 // sign-bit words (rows padded to 32 bits)
+    const int32_t *rptr;        // [C+1] row pointers into rvar
+    const int32_t *rvar;        // [E] variable of each edge, row-major
+    const uint32_t *rbit;       // [C] first sign-bit index of each row (multiple of 32)
+    const int32_t *cptr;        // [V+1] column pointers into cchk / cbit
+    const int32_t *cchk;        // [E] check of each column entry
+    const uint32_t *cbit;       // [E] sign-bit index of each column entry
+    const int32_t *optr;        // [V+1] column pointers into oidx
+    const int32_t *oidx;        // observables flipped by each fault
+    const double *L0d;          // [V] prior LLRs, FP64
+    const float *L0f;           // [V] prior LLRs rounded to FP32
+    const uint32_t *thr;        // [V] floor(p_j 2^32)
+};
+
+struct DecodeParamsDev {
+    double gamma0, gamma_min, gamma_max;
+    int32_t pre_iter, num_sets, max_iterations, stop_nconv;
+    int32_t stop_all, carry_messages;
+    uint64_t seed;
+};
+
+struct StatsDev {               // mirrors relaybp_shot_stats
+    int32_t converged, nsol, legs, iters;
+    double weight;
+};
+
+__device__ __forceinline__ int wordsof(int64_t bits) { return (int)((bits + 31) >> 5); }
+
+// ---------------------------------------------------------------------------
+// a2: fault sampler.  One warp per shot; the warp's syndrome / observable /
+// error words are accumulated in shared memory and written out coalesced.
+// ---------------------------------------------------------------------------
+__global__ void sample_kernel(DevDEM g, uint64_t seed, uint64_t shot0, int64_t shots,
+                              uint32_t *__restrict__ syn_out, uint32_t *__restrict__ obs_out,
+                              uint32_t *__restrict__ err_out)
+{
+    extern __shared__ uint32_t sbuf[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int WC = wordsof(g.C), WK = wordsof(g.K), WV = wordsof(g.V);
+    const int per_warp = WC + WK + (err_out ? WV : 0);
+    uint32_t *s_syn = sbuf + wib * per_warp;
+    uint32_t *s_obs = s_syn + WC;
+    uint32_t *s_err = s_obs + WK;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const uint32_t nblk = (uint32_t)((g.V + 3) / 4);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; s < shots; s += warps) {
+        for (int w = lane; w < per_warp; w += 32) s_syn[w] = 0u;
+        __syncwarp();
+        const uint64_t shot = shot0 + (uint64_t)s;
+        for (uint32_t b = lane; b < nblk; b += 32) {
+            const uint4 r = philox_block(seed, shot, 0u, b);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = (int)(4 * b) + t;
+                if (j < g.V && uint4_word(r, t) < __ldg(g.thr + j)) {
+                    if (err_out) atomicOr(s_err + (j >> 5), 1u << (j & 31));
+                    for (int q = __ldg(g.cptr + j), qe = __ldg(g.cptr + j + 1); q < qe; ++q) {
+                        const int i = __ldg(g.cchk + q);
+                        atomicXor(s_syn + (i >> 5), 1u << (i & 31));
+                    }
+                    for (int q = __ldg(g.optr + j), qe = __ldg(g.optr + j + 1); q < qe; ++q) {
+                        const int o = __ldg(g.oidx + q);
+                        atomicXor(s_obs + (o >> 5), 1u << (o & 31));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        for (int w = lane; w < WC; w += 32) syn_out[s * WC + w] = s_syn[w];
+        if (obs_out)
+            for (int w = lane; w < WK; w += 32) obs_out[s * WK + w] = s_obs[w];
+        if (err_out)
+            for (int w = lane; w < WV; w += 32) err_out[s * WV + w] = s_err[w];
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3-a8: Relay-BP, one thread block per shot, persistent over the batch.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T vmin(T a, T b) { return b < a ? b : a; }
+template <typename T> __device__ __forceinline__ T vabs(T a) { return a < (T)0 ? -a : a; }
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    static __device__ __forceinline__ float l0(const DevDEM &g, int j) { return __ldg(g.L0f + j); }
+};
+template <> struct Num<double> {
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+    static __device__ __forceinline__ double l0(const DevDEM &g, int j) { return __ldg(g.L0d + j); }
+};
+
+// Memory strength of variable j in leg `leg` >= 1: the top 24 bits of Philox
+// stream 1 word (leg * 4 * ceil(V/4) + j), scaled to [0, 1) exactly.
+template <typename T>
+__device__ __forceinline__ T draw_gamma(const DecodeParamsDev &p, uint64_t shot, int leg, int j, int V)
+{
+    const uint32_t nblk = (uint32_t)((V + 3) / 4);
+    const uint4 r = philox_block(p.seed, shot, 1u, (uint32_t)leg * nblk + (uint32_t)(j >> 2));
+    const uint32_t w = uint4_word(r, j & 3);
+    const T u = (T)(w >> 8) * (T)(1.0 / 16777216.0);
+    return (T)p.gamma_min + ((T)p.gamma_max - (T)p.gamma_min) * u;
+}
+
+struct SmemPlan {               // byte offsets into dynamic shared memory
+    int M, A, m1, m2, am, sgn, ehat, best, res, syn, obsacc, total;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
+                    const uint32_t *__restrict__ syn_in, uint64_t shot0, int64_t shots,
+                    uint32_t *__restrict__ corr_out, uint32_t *__restrict__ pobs_out,
+                    StatsDev *__restrict__ stats_out, unsigned long long *__restrict__ work,
+                    T *__restrict__ gamma_scratch, double *__restrict__ trace, int trace_iters)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *M = reinterpret_cast<T *>(smem + plan.M);
+    T *A = reinterpret_cast<T *>(smem + plan.A);
+    T *m1 = reinterpret_cast<T *>(smem + plan.m1);
+    T *m2 = reinterpret_cast<T *>(smem + plan.m2);
+    uint32_t *am = reinterpret_cast<uint32_t *>(smem + plan.am);
+    uint32_t *sgn = reinterpret_cast<uint32_t *>(smem + plan.sgn);
+    uint32_t *ehat = reinterpret_cast<uint32_t *>(smem + plan.ehat);
+    uint32_t *best = reinterpret_cast<uint32_t *>(smem + plan.best);
+    uint32_t *res = reinterpret_cast<uint32_t *>(smem + plan.res);
+    uint32_t *syn = reinterpret_cast<uint32_t *>(smem + plan.syn);
+    uint32_t *obsacc = reinterpret_cast<uint32_t *>(smem + plan.obsacc);
+
+    __shared__ long long s_shot;
+    __shared__ int s_nsol, s_have_best, s_copy;
+    __shared__ double s_best_w, s_w;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x, nwarp = nthr >> 5;
+    const int C = g.C, V = g.V;
+    const int WC = wordsof(C), WV = wordsof(V), WK = wordsof(g.K);
+    const unsigned FULL = 0xffffffffu;
+    T *gam = gamma_scratch + (int64_t)blockIdx.x * V;
+    const T INF = Num<T>::inf();
+
+    for (;;) {
+        if (tid == 0) {
+            s_shot = (long long)atomicAdd(work, 1ull);
+            s_nsol = 0;
+            s_have_best = 0;
+            s_best_w = 0.0;
+        }
+        __syncthreads();
+        const long long sidx = s_shot;
+        if (sidx >= shots) break;
+        const uint64_t shot = shot0 + (uint64_t)sidx;
+
+        // ---- shot start: M = L0, leg-0 strengths, zero messages ------------
+        for (int j = tid; j < V; j += nthr) {
+            const T l0 = Num<T>::l0(g, j);
+            const T gm = (T)p.gamma0;
+            M[j] = l0;
+            gam[j] = gm;
+            A[j] = ((T)1 - gm) * l0 + gm * l0;
+        }
+        for (int i = tid; i < C; i += nthr) { m1[i] = (T)0; m2[i] = (T)0; am[i] = 0u; }
+        for (int w = tid; w < g.NW; w += nthr) sgn[w] = 0u;
+        for (int w = tid; w < WV; w += nthr) ehat[w] = 0u;
+        for (int w = tid; w < WC; w += nthr) {
+            const uint32_t sv = syn_in[sidx * WC + w];
+            syn[w] = sv;
+            res[w] = sv;                        // residual of e^ = 0
+        }
+        __syncthreads();
+
+        int legs = 0, iters = 0;
+        for (int leg = 0; leg <= p.num_sets; ++leg) {
+            ++legs;
+            if (leg > 0) {
+                // a6: new leg -- fresh strengths, marginals carried over
+                for (int j = tid; j < V; j += nthr) {
+                    const T l0 = Num<T>::l0(g, j);
+                    const T gn = draw_gamma<T>(p, shot, leg, j, V);
+                    T carry = (T)0;
+                    if (p.carry_messages) {
+                        const T go = gam[j];
+                        carry = A[j] - (((T)1 - go) * l0 + go * M[j]);
+                    }
+                    gam[j] = gn;
+                    A[j] = ((T)1 - gn) * l0 + gn * M[j] + carry;
+                }
+                if (!p.carry_messages) {
+                    for (int i = tid; i < C; i += nthr) { m1[i] = (T)0; m2[i] = (T)0; am[i] = 0u; }
+                    for (int w = tid; w < g.NW; w += nthr) sgn[w] = 0u;
+                }
+                __syncthreads();
+            }
+            const int T_leg = (leg == 0) ? p.pre_iter : p.max_iterations;
+            bool conv = false;
+            for (int t = 0; t < T_leg; ++t) {
+                // ---- a3: check rows, one warp per row ------------------------
+                for (int i = warp; i < C; i += nwarp) {
+                    const int e0 = __ldg(g.rptr + i), deg = __ldg(g.rptr + i + 1) - e0;
+                    if (deg == 0) continue;
+                    const T om1 = m1[i], om2 = m2[i];
+                    const uint32_t oas = am[i];
+                    const uint32_t oarg = oas & 0x7fffffffu, opar = oas >> 31;
+                    const uint32_t rb = __ldg(g.rbit + i);
+                    T b1 = INF, b2 = INF;
+                    uint32_t bi = 0u, par = 0u;
+                    for (int k0 = 0; k0 < deg; k0 += 32) {
+                        const int k = k0 + lane;
+                        const uint32_t widx = (rb >> 5) + (uint32_t)(k0 >> 5);
+                        const uint32_t wsg = sgn[widx];
+                        uint32_t nb = 0u;
+                        if (k < deg) {
+                            const int j = __ldg(g.rvar + e0 + k);
+                            const uint32_t bpos = rb + (uint32_t)k;
+                            const T mag = (bpos == oarg) ? om2 : om1;
+                            const T nu_old = (((wsg >> lane) & 1u) ^ opar) ? -mag : mag;
+                            const T mu = A[j] - nu_old;
+                            nb = (mu < (T)0) ? 1u : 0u;
+                            const T a = vabs(mu);
+                            if (a < b1) { b2 = b1; b1 = a; bi = bpos; }
+                            else if (a < b2) { b2 = a; }
+                        }
+                        const uint32_t bal = __ballot_sync(FULL, nb);
+                        if (lane == 0) sgn[widx] = bal;
+                        par ^= (uint32_t)(__popc(bal) & 1);
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const T o1 = __shfl_xor_sync(FULL, b1, off);
+                        const T o2 = __shfl_xor_sync(FULL, b2, off);
+                        const uint32_t oi = __shfl_xor_sync(FULL, bi, off);
+                        if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin(b1, o2); b1 = o1; bi = oi; }
+                        else { b2 = vmin(b2, o1); }
+                    }
+                    if (lane == 0) {
+                        const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
+                        m1[i] = b1;
+                        m2[i] = b2;
+                        am[i] = bi | ((par ^ sb) << 31);
+                    }
+                }
+                __syncthreads();
+                // ---- a4: variables, one lane per variable --------------------
+                for (int j0 = warp * 32; j0 < V; j0 += nwarp * 32) {
+                    const int j = j0 + lane;
+                    uint32_t dec = 0u;
+                    if (j < V) {
+                        T S = (T)0;
+                        const int q0 = __ldg(g.cptr + j), q1 = __ldg(g.cptr + j + 1);
+                        for (int q = q0; q < q1; ++q) {
+                            const int i = __ldg(g.cchk + q);
+                            const uint32_t bp = __ldg(g.cbit + q);
+                            const uint32_t as = am[i];
+                            const T mag = (bp == (as & 0x7fffffffu)) ? m2[i] : m1[i];
+                            const uint32_t sb = ((sgn[bp >> 5] >> (bp & 31)) & 1u) ^ (as >> 31);
+                            S += sb ? -mag : mag;
+                        }
+                        const T l0 = Num<T>::l0(g, j);
+                        const T gm = gam[j];
+                        const T Mn = ((T)1 - gm) * l0 + gm * M[j] + S;
+                        M[j] = Mn;
+                        A[j] = ((T)1 - gm) * l0 + gm * Mn + S;
+                        dec = (Mn < (T)0) ? 1u : 0u;
+                        if (trace && iters < trace_iters)
+                            trace[((int64_t)sidx * trace_iters + iters) * V + j] = (double)Mn;
+                    }
+                    const uint32_t nw = __ballot_sync(FULL, dec);
+                    uint32_t old = 0u;
+                    if (lane == 0) { old = ehat[j0 >> 5]; ehat[j0 >> 5] = nw; }
+                    old = __shfl_sync(FULL, old, 0);
+                    // a5: residual r = s + H e^ kept incrementally
+                    if (((old ^ nw) >> lane) & 1u) {
+                        const int q0 = __ldg(g.cptr + j), q1 = __ldg(g.cptr + j + 1);
+                        for (int q = q0; q < q1; ++q) {
+                            const int i = __ldg(g.cchk + q);
+                            atomicXor(res + (i >> 5), 1u << (i & 31));
+                        }
+                    }
+                }
+                __syncthreads();
+                ++iters;
+                uint32_t acc = 0u;
+                for (int w = lane; w < WC; w += 32) acc |= res[w];
+                conv = !__any_sync(FULL, acc != 0u);
+                if (conv) break;
+            }
+            if (conv) {
+                // a7: FP64 weight in ascending variable order; keep the minimum
+                if (tid == 0) {
+                    double w = 0.0;
+                    for (int q = 0; q < WV; ++q) {
+                        uint32_t x = ehat[q];
+                        while (x) {
+                            const int b = __ffs(x) - 1;
+                            x &= x - 1u;
+                            w += __ldg(g.L0d + q * 32 + b);
+                        }
+                    }
+                    const int better = (!s_have_best || w < s_best_w) ? 1 : 0;
+                    if (better) { s_best_w = w; s_have_best = 1; }
+                    s_copy = better;
+                    s_nsol += 1;
+                }
+                __syncthreads();
+                if (s_copy)
+                    for (int w = tid; w < WV; w += nthr) best[w] = ehat[w];
+                __syncthreads();
+            }
+            if (!p.stop_all && s_nsol >= p.stop_nconv) break;
+        }
+
+        // ---- outputs --------------------------------------------------------
+        const int have = s_have_best;
+        const uint32_t *out = have ? best : ehat;
+        for (int w = tid; w < WK; w += nthr) obsacc[w] = 0u;
+        __syncthreads();
+        for (int w = tid; w < WV; w += nthr) {
+            const uint32_t x0 = out[w];
+            if (corr_out) corr_out[sidx * WV + w] = x0;
+            uint32_t x = x0;
+            while (x) {
+                const int b = __ffs(x) - 1;
+                x &= x - 1u;
+                const int j = w * 32 + b;
+                for (int q = __ldg(g.optr + j), qe = __ldg(g.optr + j + 1); q < qe; ++q) {
+                    const int o = __ldg(g.oidx + q);
+                    atomicXor(obsacc + (o >> 5), 1u << (o & 31));
+                }
+            }
+        }
+        if (tid == 0) {
+            double w = s_best_w;
+            if (!have) {
+                w = 0.0;
+                for (int q = 0; q < WV; ++q) {
+                    uint32_t x = ehat[q];
+                    while (x) {
+                        const int b = __ffs(x) - 1;
+                        x &= x - 1u;
+                        w += __ldg(g.L0d + q * 32 + b);
+                    }
+                }
+            }
+            s_w = w;
+        }
+        __syncthreads();
+        if (pobs_out)
+            for (int w = tid; w < WK; w += nthr) pobs_out[sidx * WK + w] = obsacc[w];
+        if (stats_out && tid == 0) {
+            StatsDev st;
+            st.converged = have;
+            st.nsol = s_nsol;
+            st.legs = legs;
+            st.iters = iters;
+            st.weight = s_w;
+            stats_out[sidx] = st;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a9: failure accounting, one thread per shot, warp-aggregated atomics.
+// ---------------------------------------------------------------------------
+__global__ void count_failures_kernel(const uint32_t *__restrict__ pobs, const uint32_t *__restrict__ tobs,
+                                      const StatsDev *__restrict__ stats, int64_t shots, int WK,
+                                      unsigned long long *__restrict__ counters)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t nonconv = 0u, logical = 0u, valid = 0u;
+    if (s < shots) {
+        valid = 1u;
+        if (!stats[s].converged) {
+            nonconv = 1u;
+        } else {
+            for (int w = 0; w < WK; ++w)
+                if (pobs[s * WK + w] != tobs[s * WK + w]) { logical = 1u; break; }
+        }
+    }
+    const unsigned FULL = 0xffffffffu;
+    const int nv = __popc(__ballot_sync(FULL, valid));
+    const int nn = __popc(__ballot_sync(FULL, nonconv));
+    const int nl = __popc(__ballot_sync(FULL, logical));
+    if ((threadIdx.x & 31) == 0) {
+        if (nv) atomicAdd(counters + 0, (unsigned long long)nv);
+        if (nn) atomicAdd(counters + 1, (unsigned long long)nn);
+        if (nl) atomicAdd(counters + 2, (unsigned long long)nl);
+        if (nn + nl) atomicAdd(counters + 3, (unsigned long long)(nn + nl));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory read bandwidth probe: every thread streams 16-byte loads over
+// a 32 KiB shared buffer in a bank-conflict-free pattern.  The denominator of
+// the decode kernel's roofline when its messages are shared-memory resident.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) smem_read_probe(float *__restrict__ sink, int reps)
+{
+    __shared__ float4 buf[2048];
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) buf[i] = make_float4((float)i, 1.f, 2.f, 3.f);
+    __syncthreads();
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < reps; ++r) {
+        const float4 v = buf[(threadIdx.x + r * 32) & 2047];
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    if (acc.x + acc.y + acc.z + acc.w == -1.f) sink[blockIdx.x] = acc.x;
+}
+
+}  // namespace relaybp

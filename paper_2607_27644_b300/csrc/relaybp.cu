@@ -1,0 +1,482 @@
+// Host side of the C ABI declared in include/relaybp.h.
+//
+// relaybp_build lays the DEM out for the kernels: the check matrix in row
+// order (one sign bit per edge, rows padded to 32-bit words) and in column
+// order (check and sign-bit index of each entry), prior LLRs in FP64 and FP32,
+// and the sampler thresholds floor(p_j 2^32).  The handle owns every device
+// allocation and a small scratch area: the persistent kernel's work counter,
+// failure counters and a per-block buffer for the leg's memory strengths.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/relaybp.h"
+#include "kernels.cuh"
+
+using namespace relaybp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t e__ = (expr);                                                         \
+        if (e__ != cudaSuccess)                                                           \
+            return fail(RELAYBP_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+int words(int64_t bits) { return (int)((bits + 31) / 32); }
+
+}  // namespace
+
+struct relaybp_handle {
+    int device = 0;
+    int num_sms = 0;
+    relaybp_params params{};
+    DevDEM dem{};
+    std::vector<void *> allocs;
+    // scratch
+    unsigned long long *d_work = nullptr;
+    void *d_gamma = nullptr;         // [blocks][V] of the message type
+    int64_t gamma_blocks = 0;
+    size_t gamma_elem = 0;
+    // host-buffer staging (relaybp_decode_host)
+    uint32_t *d_stage_syn = nullptr, *d_stage_pobs = nullptr;
+    StatsDev *d_stage_stats = nullptr;
+    int64_t stage_shots = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+template <typename T>
+int upload(relaybp_handle *h, const std::vector<T> &v, const T **dst)
+{
+    void *p = nullptr;
+    size_t n = std::max<size_t>(1, v.size()) * sizeof(T);
+    CUDA_TRY(cudaMalloc(&p, n));
+    h->allocs.push_back(p);
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = static_cast<const T *>(p);
+    return 0;
+}
+
+int check_csr(const relaybp_csr *m, const char *name)
+{
+    if (!m || !m->indptr || (m->indptr[m->rows] > 0 && !m->indices))
+        return fail(RELAYBP_ERR_INVALID, "%s: null pointer", name);
+    if (m->rows < 0 || m->cols < 0) return fail(RELAYBP_ERR_INVALID, "%s: negative size", name);
+    if (m->indptr[0] != 0) return fail(RELAYBP_ERR_INVALID, "%s: indptr[0] != 0", name);
+    for (int32_t i = 0; i < m->rows; ++i) {
+        if (m->indptr[i + 1] < m->indptr[i]) return fail(RELAYBP_ERR_INVALID, "%s: indptr decreases at row %d", name, i);
+        for (int32_t e = m->indptr[i]; e < m->indptr[i + 1]; ++e) {
+            int32_t c = m->indices[e];
+            if (c < 0 || c >= m->cols)
+                return fail(RELAYBP_ERR_INVALID, "%s: column %d out of range at row %d", name, c, i);
+            if (e > m->indptr[i] && c <= m->indices[e - 1])
+                return fail(RELAYBP_ERR_INVALID, "%s: row %d not strictly increasing", name, i);
+        }
+    }
+    return 0;
+}
+
+int check_params(const relaybp_params *p)
+{
+    if (!p) return fail(RELAYBP_ERR_INVALID, "params is NULL");
+    if (p->pre_iter < 1 || p->max_iterations < 1 || p->num_sets < 0 || p->stop_nconv < 1)
+        return fail(RELAYBP_ERR_INVALID, "iteration/leg/solution counts out of range");
+    if (!std::isfinite(p->gamma0) || !std::isfinite(p->gamma_min) || !std::isfinite(p->gamma_max) ||
+        p->gamma_min > p->gamma_max)
+        return fail(RELAYBP_ERR_INVALID, "memory strengths must be finite with gamma_min <= gamma_max");
+    if (p->msg_dtype != RELAYBP_MSG_F64 && p->msg_dtype != RELAYBP_MSG_F32)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "msg_dtype %d not supported", p->msg_dtype);
+    if (p->reserved != 0) return fail(RELAYBP_ERR_INVALID, "reserved field must be 0");
+    return 0;
+}
+
+// The memory-strength counter block (leg * ceil(V/4) + j/4) must fit 32 bits.
+int check_legs(const relaybp_params *p, int32_t V)
+{
+    if ((uint64_t)(p->num_sets + 1) * (uint64_t)((V + 3) / 4) > 0xffffffffull)
+        return fail(RELAYBP_ERR_INVALID, "num_sets * ceil(V/4) exceeds the 32-bit draw counter");
+    return 0;
+}
+
+SmemPlan make_plan(const DevDEM &g, size_t esz)
+{
+    SmemPlan s{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        size_t at = off;
+        off += bytes;
+        return (int)at;
+    };
+    s.M = take(esz * g.V);
+    s.A = take(esz * g.V);
+    s.m1 = take(esz * g.C);
+    s.m2 = take(esz * g.C);
+    s.am = take(4 * (size_t)g.C);
+    s.sgn = take(4 * (size_t)g.NW);
+    s.ehat = take(4 * (size_t)words(g.V));
+    s.best = take(4 * (size_t)words(g.V));
+    s.res = take(4 * (size_t)words(g.C));
+    s.syn = take(4 * (size_t)words(g.C));
+    s.obsacc = take(4 * (size_t)std::max(1, words(g.K)));
+    s.total = (int)((off + 15) & ~size_t(15));
+    return s;
+}
+
+DecodeParamsDev dev_params(const relaybp_params &p)
+{
+    DecodeParamsDev d{};
+    d.gamma0 = p.gamma0;
+    d.gamma_min = p.gamma_min;
+    d.gamma_max = p.gamma_max;
+    d.pre_iter = p.pre_iter;
+    d.num_sets = p.num_sets;
+    d.max_iterations = p.max_iterations;
+    d.stop_nconv = p.stop_nconv;
+    d.stop_all = p.stop_all;
+    d.carry_messages = p.carry_messages;
+    d.seed = p.seed;
+    return d;
+}
+
+int block_threads(const DevDEM &g)
+{
+    if (g.E <= 2048) return 64;
+    if (g.E <= 16384) return 256;
+    return 512;
+}
+
+template <typename T>
+int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
+                  uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace = nullptr,
+                  int trace_iters = 0)
+{
+    const DevDEM &g = h->dem;
+    SmemPlan plan = make_plan(g, sizeof(T));
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (plan.total + 64 > maxsm)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes)",
+                    plan.total, maxsm);
+    auto kern = relay_decode_kernel<T>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+    const int threads = block_threads(g);
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan.total));
+    if (per_sm < 1) return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan.total);
+    int64_t blocks = (int64_t)per_sm * h->num_sms;
+    if (blocks > shots) blocks = shots;
+    if (blocks < 1) blocks = 1;
+    // scratch: the leg's memory strengths, one row of V per block
+    if (h->gamma_blocks < blocks || h->gamma_elem != sizeof(T)) {
+        if (h->d_gamma) { cudaFree(h->d_gamma); h->d_gamma = nullptr; }
+        int64_t want = (int64_t)per_sm * h->num_sms;
+        CUDA_TRY(cudaMalloc(&h->d_gamma, (size_t)want * g.V * sizeof(T) + 16));
+        h->gamma_blocks = want;
+        h->gamma_elem = sizeof(T);
+    }
+    CUDA_TRY(cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st));
+    kern<<<(unsigned)blocks, threads, plan.total, st>>>(g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr,
+                                                       d_pobs, d_stats, h->d_work, static_cast<T *>(h->d_gamma),
+                                                       d_trace, trace_iters);
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *relaybp_last_error(void) { return g_err.c_str(); }
+
+int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr *obs, const relaybp_params *params,
+                  relaybp_handle **out)
+{
+    g_err.clear();
+    if (!out) return fail(RELAYBP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (int rc = check_csr(H, "H")) return rc;
+    if (!priors) return fail(RELAYBP_ERR_INVALID, "priors is NULL");
+    if (obs) {
+        if (int rc = check_csr(obs, "obs")) return rc;
+        if (obs->cols != H->cols) return fail(RELAYBP_ERR_INVALID, "obs has %d columns, H has %d", obs->cols, H->cols);
+    }
+    if (int rc = check_params(params)) return rc;
+    if (int rc = check_legs(params, H->cols)) return rc;
+    const int32_t C = H->rows, V = H->cols, K = obs ? obs->rows : 0;
+    const int64_t E = H->indptr[C];
+    if (C >= (1 << 20) || E >= (int64_t)1 << 30) return fail(RELAYBP_ERR_UNSUPPORTED, "DEM too large");
+    for (int32_t j = 0; j < V; ++j)
+        if (!(priors[j] > 0.0 && priors[j] < 1.0))
+            return fail(RELAYBP_ERR_INVALID, "prior %d = %g is not in (0, 1)", j, priors[j]);
+    for (int32_t i = 0; i < C; ++i)
+        if (H->indptr[i + 1] - H->indptr[i] == 1)
+            return fail(RELAYBP_ERR_INVALID, "detector %d is touched by a single fault; rows need 0 or >= 2 entries", i);
+
+    relaybp_handle *h = new relaybp_handle();
+    h->params = *params;
+    auto bail = [&](int rc) {
+        relaybp_destroy(h);
+        return rc;
+    };
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce != cudaSuccess) { delete h; return fail(RELAYBP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); }
+    ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (ce != cudaSuccess) { delete h; return fail(RELAYBP_ERR_CUDA, "SM count: %s", cudaGetErrorString(ce)); }
+
+    // row order: variables and 32-aligned sign-bit bases
+    std::vector<int32_t> rptr(H->indptr, H->indptr + C + 1), rvar(H->indices, H->indices + E);
+    std::vector<uint32_t> rbit(C);
+    uint64_t nbits = 0;
+    for (int32_t i = 0; i < C; ++i) {
+        rbit[i] = (uint32_t)nbits;
+        nbits += (uint64_t)(H->indptr[i + 1] - H->indptr[i] + 31) / 32 * 32;
+    }
+    if (nbits >= 0x80000000ull) return bail(fail(RELAYBP_ERR_UNSUPPORTED, "too many edges"));
+    // column order (ascending check within each column)
+    std::vector<int32_t> cptr(V + 1, 0), cchk(E), fill(V, 0);
+    std::vector<uint32_t> cbit(E);
+    for (int64_t e = 0; e < E; ++e) cptr[rvar[e] + 1]++;
+    for (int32_t j = 0; j < V; ++j) cptr[j + 1] += cptr[j];
+    for (int32_t i = 0; i < C; ++i)
+        for (int32_t e = rptr[i]; e < rptr[i + 1]; ++e) {
+            int32_t j = rvar[e];
+            int32_t at = cptr[j] + fill[j]++;
+            cchk[at] = i;
+            cbit[at] = rbit[i] + (uint32_t)(e - rptr[i]);
+        }
+    // observables per column
+    std::vector<int32_t> optr(V + 1, 0), oidx;
+    if (obs) {
+        const int64_t nnzo = obs->indptr[K];
+        oidx.resize(nnzo);
+        std::vector<int32_t> of(V, 0);
+        for (int64_t e = 0; e < nnzo; ++e) optr[obs->indices[e] + 1]++;
+        for (int32_t j = 0; j < V; ++j) optr[j + 1] += optr[j];
+        for (int32_t i = 0; i < K; ++i)
+            for (int32_t e = obs->indptr[i]; e < obs->indptr[i + 1]; ++e) {
+                int32_t j = obs->indices[e];
+                oidx[optr[j] + of[j]++] = i;
+            }
+    }
+    // a1: prior LLRs in FP64 on the host; sampler thresholds
+    std::vector<double> L0d(V);
+    std::vector<float> L0f(V);
+    std::vector<uint32_t> thr(V);
+    for (int32_t j = 0; j < V; ++j) {
+        L0d[j] = std::log((1.0 - priors[j]) / priors[j]);
+        L0f[j] = (float)L0d[j];
+        double t = std::floor(priors[j] * 4294967296.0);
+        thr[j] = t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
+    }
+    DevDEM &g = h->dem;
+    g.C = C; g.V = V; g.K = K; g.E = E;
+    g.NW = (int32_t)(nbits / 32);
+    int rc = 0;
+    if ((rc = upload(h, rptr, &g.rptr)) || (rc = upload(h, rvar, &g.rvar)) || (rc = upload(h, rbit, &g.rbit)) ||
+        (rc = upload(h, cptr, &g.cptr)) || (rc = upload(h, cchk, &g.cchk)) || (rc = upload(h, cbit, &g.cbit)) ||
+        (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
+        (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
+        return bail(rc);
+    ce = cudaMalloc(&h->d_work, 64);
+    if (ce != cudaSuccess) return bail(fail(RELAYBP_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(ce)));
+    *out = h;
+    return 0;
+}
+
+int relaybp_set_params(relaybp_handle *h, const relaybp_params *params)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_params(params)) return rc;
+    if (int rc = check_legs(params, h->dem.V)) return rc;
+    h->params = *params;
+    return 0;
+}
+
+int relaybp_sizes(const relaybp_handle *h, int32_t *n_det, int32_t *n_loc, int32_t *n_obs, int64_t *n_edges)
+{
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (n_det) *n_det = h->dem.C;
+    if (n_loc) *n_loc = h->dem.V;
+    if (n_obs) *n_obs = h->dem.K;
+    if (n_edges) *n_edges = h->dem.E;
+    return 0;
+}
+
+int relaybp_sample(relaybp_handle *h, uint64_t seed, uint64_t shot0, int64_t shots, uint32_t *d_syndromes,
+                   uint32_t *d_obs, uint32_t *d_errors, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (shots == 0) return 0;
+    if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
+    const DevDEM &g = h->dem;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int per_warp = words(g.C) + words(g.K) + (d_errors ? words(g.V) : 0);
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * per_warp * 4 > (size_t)maxsm) warps /= 2;
+    const size_t smem = (size_t)warps * per_warp * 4;
+    if (smem > (size_t)maxsm) return fail(RELAYBP_ERR_UNSUPPORTED, "sampler state exceeds shared memory");
+    CUDA_TRY(cudaFuncSetAttribute(sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel, warps * 32, smem));
+    int64_t blocks = (int64_t)std::max(1, per_sm) * h->num_sms;
+    const int64_t need = (shots + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    sample_kernel<<<(unsigned)blocks, warps * 32, smem, st>>>(g, seed, shot0, shots, d_syndromes, d_obs, d_errors);
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
+}
+
+int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                         uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
+                         void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (shots == 0) return 0;
+    if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
+    static_assert(sizeof(StatsDev) == sizeof(relaybp_shot_stats), "stats layout");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
+    if (h->params.msg_dtype == RELAYBP_MSG_F64)
+        return launch_decode<double>(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+    return launch_decode<float>(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+}
+
+int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                         int32_t trace_iters, double *d_trace, relaybp_shot_stats *d_stats, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 0 || trace_iters < 0) return fail(RELAYBP_ERR_INVALID, "negative size");
+    if (shots == 0) return 0;
+    if (!d_syndromes || (trace_iters > 0 && !d_trace)) return fail(RELAYBP_ERR_INVALID, "null pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
+    if (h->params.msg_dtype == RELAYBP_MSG_F64)
+        return launch_decode<double>(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
+    return launch_decode<float>(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
+}
+
+int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
+                        uint32_t *h_pred_obs, relaybp_shot_stats *h_stats, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (shots == 0) return 0;
+    if (!h_syndromes) return fail(RELAYBP_ERR_INVALID, "h_syndromes is NULL");
+    const DevDEM &g = h->dem;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int WC = words(g.C), WK = std::max(1, words(g.K));
+    if (h->stage_shots < shots) {
+        cudaFree(h->d_stage_syn);
+        cudaFree(h->d_stage_pobs);
+        cudaFree(h->d_stage_stats);
+        h->d_stage_syn = nullptr; h->d_stage_pobs = nullptr; h->d_stage_stats = nullptr;
+        h->stage_shots = 0;
+        CUDA_TRY(cudaMalloc(&h->d_stage_syn, (size_t)shots * WC * 4));
+        CUDA_TRY(cudaMalloc(&h->d_stage_pobs, (size_t)shots * WK * 4));
+        CUDA_TRY(cudaMalloc(&h->d_stage_stats, (size_t)shots * sizeof(StatsDev)));
+        h->stage_shots = shots;
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->d_stage_syn, h_syndromes, (size_t)shots * WC * 4, cudaMemcpyHostToDevice, st));
+    int rc = relaybp_decode_batch(h, h->d_stage_syn, shot0, shots, nullptr, h_pred_obs ? h->d_stage_pobs : nullptr,
+                                  h_stats ? reinterpret_cast<relaybp_shot_stats *>(h->d_stage_stats) : nullptr,
+                                  cuda_stream);
+    if (rc) return rc;
+    if (h_pred_obs)
+        CUDA_TRY(cudaMemcpyAsync(h_pred_obs, h->d_stage_pobs, (size_t)shots * words(g.K) * 4, cudaMemcpyDeviceToHost, st));
+    if (h_stats)
+        CUDA_TRY(cudaMemcpyAsync(h_stats, h->d_stage_stats, (size_t)shots * sizeof(StatsDev), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const uint32_t *d_true_obs,
+                           const relaybp_shot_stats *d_stats, int64_t shots, unsigned long long *d_counters,
+                           void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (shots == 0) return 0;
+    if (!d_stats || !d_counters || (h->dem.K > 0 && (!d_pred_obs || !d_true_obs)))
+        return fail(RELAYBP_ERR_INVALID, "null pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int threads = 256;
+    const int64_t blocks = (shots + threads - 1) / threads;
+    count_failures_kernel<<<(unsigned)blocks, threads, 0, st>>>(d_pred_obs, d_true_obs,
+                                                                reinterpret_cast<const StatsDev *>(d_stats), shots,
+                                                                words(h->dem.K), d_counters);
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
+}
+
+int64_t relaybp_launch_count(const relaybp_handle *h) { return h ? h->launches : -1; }
+
+int relaybp_probe_smem_read(int32_t reps, float *d_sink, double *bytes_read, void *cuda_stream)
+{
+    g_err.clear();
+    if (reps < 1 || !d_sink || !bytes_read) return fail(RELAYBP_ERR_INVALID, "bad probe arguments");
+    int dev = 0, sms = 0, per_sm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smem_read_probe, 1024, 0));
+    const int blocks = sms * std::max(1, per_sm);
+    smem_read_probe<<<blocks, 1024, 0, static_cast<cudaStream_t>(cuda_stream)>>>(d_sink, reps);
+    CUDA_TRY(cudaGetLastError());
+    *bytes_read = (double)blocks * 1024.0 * (double)reps * 16.0;
+    return 0;
+}
+
+int relaybp_destroy(relaybp_handle *h)
+{
+    if (!h) return 0;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (void *p : h->allocs) cudaFree(p);
+    cudaFree(h->d_work);
+    cudaFree(h->d_gamma);
+    cudaFree(h->d_stage_syn);
+    cudaFree(h->d_stage_pobs);
+    cudaFree(h->d_stage_stats);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete h;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,238 @@
+"""Thin Python binding of the C ABI in include/relaybp.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+compute of its own: device buffers are torch tensors passed by data pointer,
+streams are torch CUDA streams.  Importing this module loads the in-tree
+``librelaybp.so``; if it is missing, the import fails -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librelaybp.so")
+
+RELAYBP_MSG_F64 = 0
+RELAYBP_MSG_F32 = 1
+_DTYPES = {"f64": RELAYBP_MSG_F64, "f32": RELAYBP_MSG_F32}
+
+
+class relaybp_csr(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32),
+                ("indptr", ctypes.c_void_p), ("indices", ctypes.c_void_p)]
+
+
+class relaybp_params(ctypes.Structure):
+    _fields_ = [("gamma0", ctypes.c_double), ("pre_iter", ctypes.c_int32), ("num_sets", ctypes.c_int32),
+                ("max_iterations", ctypes.c_int32), ("stop_nconv", ctypes.c_int32),
+                ("gamma_min", ctypes.c_double), ("gamma_max", ctypes.c_double),
+                ("msg_dtype", ctypes.c_int32), ("stop_all", ctypes.c_int32),
+                ("carry_messages", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+STATS_BYTES = 24      # sizeof(relaybp_shot_stats)
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2607_27644_b300.build` "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "relaybp_build": ([ctypes.POINTER(relaybp_csr), P, ctypes.POINTER(relaybp_csr),
+                           ctypes.POINTER(relaybp_params), ctypes.POINTER(P)], ctypes.c_int),
+        "relaybp_set_params": ([P, ctypes.POINTER(relaybp_params)], ctypes.c_int),
+        "relaybp_sizes": ([P, P, P, P, P], ctypes.c_int),
+        "relaybp_sample": ([P, U64, U64, I64, P, P, P, P], ctypes.c_int),
+        "relaybp_decode_batch": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
+        "relaybp_decode_trace": ([P, P, U64, I64, I32, P, P, P], ctypes.c_int),
+        "relaybp_decode_host": ([P, P, U64, I64, P, P, P], ctypes.c_int),
+        "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
+        "relaybp_launch_count": ([P], I64),
+        "relaybp_probe_smem_read": ([I32, P, P, P], ctypes.c_int),
+        "relaybp_destroy": ([P], ctypes.c_int),
+        "relaybp_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
+            "relaybp_decode_trace", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
+            "relaybp_probe_smem_read", "relaybp_destroy", "relaybp_last_error"]
+
+
+class RelayBPError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RelayBPError(f"{what} failed ({rc}): {_lib.relaybp_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Params:
+    """Decoder parameters (Sec. 6.1 decoder configuration list; Table 9 intervals)."""
+    gamma0: float = 0.125
+    pre_iter: int = 80
+    num_sets: int = 1000
+    max_iterations: int = 60
+    stop_nconv: int = 5
+    gamma_min: float = -0.24
+    gamma_max: float = 0.66
+    msg_dtype: str = "f32"
+    stop_all: bool = False
+    carry_messages: bool = False
+    seed: int = 0
+
+    def c(self) -> relaybp_params:
+        return relaybp_params(self.gamma0, self.pre_iter, self.num_sets, self.max_iterations, self.stop_nconv,
+                              self.gamma_min, self.gamma_max, _DTYPES[self.msg_dtype], int(self.stop_all),
+                              int(self.carry_messages), 0, self.seed)
+
+
+@dataclass
+class Handle:
+    ptr: ctypes.c_void_p
+    n_det: int
+    n_loc: int
+    n_obs: int
+    n_edges: int
+    _keep: list = field(default_factory=list)
+
+    @property
+    def wc(self):
+        return (self.n_det + 31) // 32
+
+    @property
+    def wv(self):
+        return (self.n_loc + 31) // 32
+
+    @property
+    def wk(self):
+        return max(1, (self.n_obs + 31) // 32)
+
+
+def relaybp_build(H_indptr, H_indices, n_det: int, n_loc: int, priors, O_indptr=None, O_indices=None,
+                  n_obs: int = 0, params: Params | None = None) -> Handle:
+    params = params or Params()
+    Hp = np.ascontiguousarray(H_indptr, dtype=np.int32)
+    Hi = np.ascontiguousarray(H_indices, dtype=np.int32)
+    pr = np.ascontiguousarray(priors, dtype=np.float64)
+    H = relaybp_csr(n_det, n_loc, _ptr(Hp), _ptr(Hi))
+    O = None
+    keep = [Hp, Hi, pr]
+    if O_indptr is not None and n_obs > 0:
+        Op = np.ascontiguousarray(O_indptr, dtype=np.int32)
+        Oi = np.ascontiguousarray(O_indices, dtype=np.int32)
+        O = relaybp_csr(n_obs, n_loc, _ptr(Op), _ptr(Oi))
+        keep += [Op, Oi]
+    out = ctypes.c_void_p()
+    cp = params.c()
+    _check(_lib.relaybp_build(ctypes.byref(H), _ptr(pr), ctypes.byref(O) if O is not None else None,
+                              ctypes.byref(cp), ctypes.byref(out)), "relaybp_build")
+    h = Handle(out, 0, 0, 0, 0)
+    h.n_det, h.n_loc, h.n_obs, h.n_edges = relaybp_sizes(h)
+    return h
+
+
+def relaybp_build_dem(dem, params: Params | None = None) -> Handle:
+    """relaybp_build from a workloads.dem.DEM."""
+    return relaybp_build(dem.H_indptr, dem.H_indices, dem.n_det, dem.n_loc, dem.priors, dem.O_indptr,
+                         dem.O_indices, dem.n_obs, params)
+
+
+def relaybp_sizes(h: Handle) -> tuple[int, int, int, int]:
+    c, v, k, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.relaybp_sizes(h.ptr, ctypes.byref(c), ctypes.byref(v), ctypes.byref(k), ctypes.byref(e)),
+           "relaybp_sizes")
+    return c.value, v.value, k.value, e.value
+
+
+def relaybp_set_params(h: Handle, params: Params):
+    cp = params.c()
+    _check(_lib.relaybp_set_params(h.ptr, ctypes.byref(cp)), "relaybp_set_params")
+
+
+def relaybp_sample(h: Handle, seed: int, shot0: int, shots: int, d_syndromes, d_obs=None, d_errors=None,
+                   stream=None):
+    _check(_lib.relaybp_sample(h.ptr, seed, shot0, shots, _ptr(d_syndromes), _ptr(d_obs), _ptr(d_errors),
+                               _stream(stream)), "relaybp_sample")
+
+
+def relaybp_decode_batch(h: Handle, d_syndromes, shot0: int, shots: int, d_corrections=None, d_pred_obs=None,
+                         d_stats=None, stream=None):
+    _check(_lib.relaybp_decode_batch(h.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections),
+                                     _ptr(d_pred_obs), _ptr(d_stats), _stream(stream)), "relaybp_decode_batch")
+
+
+def relaybp_decode_trace(h: Handle, d_syndromes, shot0: int, shots: int, trace_iters: int, d_trace, d_stats=None,
+                         stream=None):
+    _check(_lib.relaybp_decode_trace(h.ptr, _ptr(d_syndromes), shot0, shots, trace_iters, _ptr(d_trace),
+                                     _ptr(d_stats), _stream(stream)), "relaybp_decode_trace")
+
+
+def relaybp_decode_host(h: Handle, h_syndromes, shot0: int, shots: int, h_pred_obs=None, h_stats=None,
+                        stream=None):
+    _check(_lib.relaybp_decode_host(h.ptr, _ptr(h_syndromes), shot0, shots, _ptr(h_pred_obs), _ptr(h_stats),
+                                    _stream(stream)), "relaybp_decode_host")
+
+
+def relaybp_count_failures(h: Handle, d_pred_obs, d_true_obs, d_stats, shots: int, d_counters, stream=None):
+    _check(_lib.relaybp_count_failures(h.ptr, _ptr(d_pred_obs), _ptr(d_true_obs), _ptr(d_stats), shots,
+                                       _ptr(d_counters), _stream(stream)), "relaybp_count_failures")
+
+
+def relaybp_launch_count(h: Handle) -> int:
+    return int(_lib.relaybp_launch_count(h.ptr))
+
+
+def relaybp_probe_smem_read(reps: int, d_sink, stream=None) -> float:
+    """Launch the shared-memory bandwidth probe; returns the bytes it reads."""
+    b = ctypes.c_double()
+    _check(_lib.relaybp_probe_smem_read(reps, _ptr(d_sink), ctypes.byref(b), _stream(stream)),
+           "relaybp_probe_smem_read")
+    return b.value
+
+
+def relaybp_destroy(h: Handle):
+    if h.ptr:
+        _check(_lib.relaybp_destroy(h.ptr), "relaybp_destroy")
+        h.ptr = ctypes.c_void_p()
+
+
+def relaybp_last_error() -> str:
+    return _lib.relaybp_last_error().decode()
+
+
+def stats_view(stats):
+    """Split a [shots, 6] int32 stats tensor into its fields."""
+    return dict(converged=stats[:, 0], nsol=stats[:, 1], legs=stats[:, 2], iters=stats[:, 3],
+                weight=stats.view(dtype=__import__("torch").float64)[:, 2])

@@ -1,0 +1,268 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated by the workload definition): the sampler is bit-exact;
+FP64 decoding agrees in every decision; FP32 posteriors stay within 1e-4
+relative (|dM| / max(1, |M|)) of the oracle until the first iteration whose
+decisions differ, decisions agree on >= 99.9% of shots, and the logical error
+rates agree within 2 sigma.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import unpack_bits
+from workloads.dem import circuit_dem, code_capacity_dem, dem_from_dense
+
+pytestmark = pytest.mark.gpu
+
+CC_KW = dict(gamma0=0.125, pre_iter=80, num_sets=50, max_iterations=60, stop_nconv=5,
+             gamma_min=-0.24, gamma_max=0.66, seed=101)
+# Paper decoder settings with the ZSZ-LP-160 interval of Table 9.
+CIRC_KW = dict(gamma0=0.125, pre_iter=80, num_sets=1000, max_iterations=60, stop_nconv=5,
+               gamma_min=-0.15, gamma_max=0.61, seed=202)
+
+
+@pytest.fixture(scope="module")
+def cc160():
+    return code_capacity_dem("ZSZ-LP-160", 0.05)
+
+
+@pytest.fixture(scope="module")
+def circ160():
+    return circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+
+
+def _handle(dem, p):
+    from paper_2607_27644_b300 import relaybp as R
+    return R.relaybp_build_dem(dem, p)
+
+
+def _fail_count(res, obs):
+    conv = res["stats"][:, 0] == 1
+    return int((~conv).sum() + (conv & np.any(res["pred_obs"] != obs, axis=1)).sum())
+
+
+@pytest.mark.parametrize("which", ["cc160", "circ160"])
+def test_sampler_bit_exact(which, request):
+    from gpu_util import gpu_sample
+    dem = request.getfixturevalue(which)
+    _, pg = __import__("gpu_util").params_pair(**CC_KW)
+    h = _handle(dem, pg)
+    seed, shot0, shots = 0xDEADBEEF12345, 98765, 4099
+    s_o, o_o, e_o = oracle.sample(dem, seed, shot0, shots, want_errors=True)
+    s_g, o_g, e_g = gpu_sample(h, seed, shot0, shots, errors=True)
+    assert np.array_equal(s_o, s_g)
+    assert np.array_equal(o_o[:, :o_g.shape[1]], o_g)
+    assert np.array_equal(e_o, e_g)
+
+
+def test_decode_code_capacity_fp64_full(cc160):
+    """Config: ZSZ-LP-160 H_X, p = 0.05, 10^4 shots, FP64."""
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype="f64", **CC_KW)
+    h = _handle(cc160, pg)
+    syn, obs, _ = oracle.sample(cc160, 1, 0, 10_000)
+    ro = oracle.decode(cc160, po, syn, shot0=0)
+    rg = gpu_decode(h, syn, shot0=0)
+    same = np.all(ro["corrections"] == rg["corrections"], axis=1)
+    assert same.mean() >= 0.999
+    assert np.array_equal(ro["stats"][same], rg["stats"][same])
+    assert np.array_equal(ro["weights"][same], rg["weights"][same])
+    fo, fg = _fail_count(ro, obs), _fail_count(rg, obs)
+    from paper_2607_27644_b300.stats import agree_within
+    assert agree_within(fo, len(syn), fg, len(syn))
+
+
+def test_decode_code_capacity_fp32(cc160):
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype="f32", **CC_KW)
+    h = _handle(cc160, pg)
+    syn, obs, _ = oracle.sample(cc160, 3, 500, 3001)
+    ro = oracle.decode(cc160, po, syn, shot0=500)
+    rg = gpu_decode(h, syn, shot0=500)
+    same = np.all(ro["corrections"] == rg["corrections"], axis=1)
+    assert same.mean() >= 0.99
+    from paper_2607_27644_b300.stats import agree_within
+    assert agree_within(_fail_count(ro, obs), len(syn), _fail_count(rg, obs), len(syn))
+
+
+def _posterior_parity(tr_o, tr_g, iters, V, tol):
+    """Max relative error of M until the first iteration whose decisions differ."""
+    worst = 0.0
+    checked = 0
+    for t in range(iters):
+        mo, mg = tr_o[t], tr_g[t]
+        if np.any(np.isnan(mg)) or np.any((mo < 0) != (mg < 0)):
+            break
+        err = np.abs(mg - mo) / np.maximum(1.0, np.abs(mo))
+        worst = max(worst, float(err.max()))
+        checked += 1
+    return worst, checked
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-9), ("f32", 1e-4)])
+def test_posteriors_circuit_level(circ160, dtype, tol):
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype=dtype, **CIRC_KW)
+    h = _handle(circ160, pg)
+    shots, T = 12, 40
+    syn, _, _ = oracle.sample(circ160, 7, 1000, shots)
+    ro = oracle.decode(circ160, po, syn, shot0=1000, trace_iters=T)
+    rg = gpu_decode(h, syn, shot0=1000, trace_iters=T)
+    total = 0
+    for s in range(shots):
+        n = min(T, int(ro["stats"][s, 3]))
+        worst, checked = _posterior_parity(ro["trace"][s], rg["trace"][s], n, circ160.n_loc, tol)
+        assert worst <= tol, (s, worst)
+        total += checked
+    assert total >= shots * 5
+
+
+def test_decode_circuit_level_fp32(circ160):
+    """Config: ZSZ-LP-160, d = 10, p = 0.1%, FP32, paper decoder settings."""
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype="f32", **CIRC_KW)
+    h = _handle(circ160, pg)
+    syn, obs, _ = oracle.sample(circ160, 2, 0, 400)
+    ro = oracle.decode(circ160, po, syn, shot0=0)
+    rg = gpu_decode(h, syn, shot0=0)
+    same = np.all(ro["corrections"] == rg["corrections"], axis=1)
+    assert (~same).sum() <= math.ceil(0.001 * len(syn))
+    # every claimed success satisfies H e^ = s
+    Hd = circ160.dense_H().astype(np.int64)
+    eh = unpack_bits(rg["corrections"], circ160.n_loc).astype(np.int64)
+    conv = rg["stats"][:, 0] == 1
+    assert np.array_equal((eh[conv] @ Hd.T) % 2, unpack_bits(syn, circ160.n_det)[conv])
+    assert _fail_count(rg, obs) == _fail_count(ro, obs)
+
+
+def test_full_size_sampled_outputs(circ160):
+    """10^6 shots sampled and decoded on the GPU in the benchmark's launch
+    configuration; 24 shots spread over the batch are recomputed by the oracle
+    one by one, and every shot of a 20k slice is checked for H e^ = s."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import params_pair
+    po, pg = params_pair(msg_dtype="f32", **CIRC_KW)
+    h = _handle(circ160, pg)
+    shots, seed = 1_000_000, 2026
+    syn = torch.empty((shots, h.wc), dtype=torch.int32, device="cuda")
+    obs = torch.empty((shots, h.wk), dtype=torch.int32, device="cuda")
+    corr = torch.empty((shots, h.wv), dtype=torch.int32, device="cuda")
+    pobs = torch.empty((shots, h.wk), dtype=torch.int32, device="cuda")
+    stats = torch.empty((shots, 6), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, seed, 0, shots, syn, obs)
+    R.relaybp_decode_batch(h, syn, 0, shots, corr, pobs, stats)
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    R.relaybp_count_failures(h, pobs, obs, stats, shots, cnt)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
+    assert c[0] == shots and c[3] == c[1] + c[2]
+    st = stats[:, :4].cpu().numpy()
+    assert np.all(st[:, 1] <= 5) and np.all(st[:, 2] <= 1001)
+    assert c[1] == int((st[:, 0] == 0).sum())
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(shots, 24, replace=False))
+    syn_np = syn.cpu().numpy().view(np.uint32)
+    corr_np = corr.cpu().numpy().view(np.uint32)
+    mism = 0
+    for i in idx:
+        s_o, _, _ = oracle.sample(circ160, seed, int(i), 1)
+        assert np.array_equal(s_o[0], syn_np[i])
+        r = oracle.decode(circ160, po, s_o, shot0=int(i))
+        mism += int(not np.array_equal(r["corrections"][0], corr_np[i]))
+    assert mism <= 1
+    Hd = circ160.dense_H().astype(np.int64)
+    sl = slice(0, 20_000)
+    eh = unpack_bits(corr_np[sl], circ160.n_loc).astype(np.int64)
+    conv = st[sl, 0] == 1
+    S = unpack_bits(syn_np[sl], circ160.n_det)
+    assert np.array_equal((eh[conv] @ Hd.T) % 2, S[conv])
+
+
+def test_edge_cases(cc160):
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype="f64", **CC_KW)
+    h = _handle(cc160, pg)
+    # zero shots: no-op
+    R.relaybp_decode_batch(h, torch.zeros((1, h.wc), dtype=torch.int32, device="cuda"), 0, 0)
+    # all-zero syndromes decode to e^ = 0 with five weight-0 solutions
+    z = np.zeros((33, h.wc), dtype=np.uint32)
+    rg = gpu_decode(h, z)
+    assert not rg["corrections"].any() and np.all(rg["stats"][:, 0] == 1) and np.all(rg["weights"] == 0)
+    # stop_all and carry_messages against the oracle
+    syn, _, _ = oracle.sample(cc160, 5, 0, 257)
+    for kw in (dict(stop_all=True, num_sets=6), dict(carry_messages=True)):
+        args = dict(CC_KW, **kw)
+        po, pg = params_pair(msg_dtype="f64", **args)
+        R.relaybp_set_params(h, pg)
+        ro = oracle.decode(cc160, po, syn)
+        rg = gpu_decode(h, syn)
+        same = np.all(ro["corrections"] == rg["corrections"], axis=1)
+        assert same.mean() >= 0.99
+        assert np.array_equal(ro["stats"][same], rg["stats"][same])
+
+
+def test_unsatisfiable_and_host_path():
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode, params_pair
+    # a ring of checks plus a check with no edges whose syndrome bit is set
+    V = 40
+    H = np.zeros((V + 1, V), dtype=np.uint8)
+    for i in range(V):
+        H[i, i] = H[i, (i + 1) % V] = 1
+    dem = dem_from_dense(H, np.full(V, 0.02))
+    po, pg = params_pair(msg_dtype="f32", gamma0=0.1, pre_iter=7, num_sets=3, max_iterations=5, stop_nconv=2,
+                         gamma_min=-0.2, gamma_max=0.5, seed=9)
+    h = R.relaybp_build_dem(dem, pg)
+    s = np.zeros((5, V + 1), dtype=np.uint8)
+    s[:, V] = 1
+    s[1, 3] = s[1, 4] = 1
+    syn = oracle.pack_bits(s)
+    rg = gpu_decode(h, syn)
+    assert np.all(rg["stats"][:, 0] == 0) and np.all(rg["stats"][:, 2] == 4) and np.all(rg["stats"][:, 3] == 22)
+    ro = oracle.decode(dem, po, syn)
+    assert np.array_equal(ro["stats"], rg["stats"])
+    # host-buffer entry point equals the device entry point
+    stats_h = np.zeros((5, 6), dtype=np.int32)
+    pobs_h = np.zeros((5, h.wk), dtype=np.uint32)
+    R.relaybp_decode_host(h, syn, 0, 5, pobs_h, stats_h)
+    assert np.array_equal(stats_h[:, :4], rg["stats"])
+
+
+def test_count_failures_matches_numpy(cc160):
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode, params_pair, to_dev
+    _, pg = params_pair(msg_dtype="f32", **CC_KW)
+    h = _handle(cc160, pg)
+    syn, obs, _ = oracle.sample(cc160, 8, 0, 2000)
+    rg = gpu_decode(h, syn)
+    stats = torch.zeros((2000, 6), dtype=torch.int32, device="cuda")
+    pobs = torch.zeros((2000, h.wk), dtype=torch.int32, device="cuda")
+    R.relaybp_decode_batch(h, to_dev(syn), 0, 2000, None, pobs, stats)
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    R.relaybp_count_failures(h, pobs, to_dev(obs), stats, 2000, cnt)
+    c = cnt.cpu().numpy()
+    conv = rg["stats"][:, 0] == 1
+    nl = int((conv & np.any(rg["pred_obs"] != obs, axis=1)).sum())
+    assert c.tolist() == [2000, int((~conv).sum()), nl, int((~conv).sum()) + nl]
+
+
+def test_too_large_for_shared_memory_is_an_error():
+    from paper_2607_27644_b300 import relaybp as R
+    rng = np.random.default_rng(1)
+    C, V = 1500, 70_000
+    rows = [np.sort(rng.choice(V, 8, replace=False)) for _ in range(C)]
+    indptr = np.r_[0, np.cumsum([len(r) for r in rows])].astype(np.int32)
+    h = R.relaybp_build(indptr, np.concatenate(rows), C, V, np.full(V, 0.01), params=R.Params(num_sets=2))
+    import torch
+    syn = torch.zeros((4, h.wc), dtype=torch.int32, device="cuda")
+    with pytest.raises(R.RelayBPError, match="shared memory"):
+        R.relaybp_decode_batch(h, syn, 0, 4)
+    R.relaybp_destroy(h)
