@@ -39,6 +39,7 @@ struct DevDEM {
     const int32_t *cptr;        // [V+1] column pointers into cchk / cbit
     const int32_t *cchk;        // [E] check of each column entry
     const uint32_t *cbit;       // [E] sign-bit index of each column entry
+    const int32_t *cedge;       // [E] row-major edge index of each column entry
     const int32_t *optr;        // [V+1] column pointers into oidx
     const int32_t *oidx;        // observables flipped by each fault
     const double *L0d;          // [V] prior LLRs, FP64
@@ -373,6 +374,247 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
                         const int b = __ffs(x) - 1;
                         x &= x - 1u;
                         w += __ldg(g.L0d + q * 32 + b);
+                    }
+                }
+            }
+            s_w = w;
+        }
+        __syncthreads();
+        if (pobs_out)
+            for (int w = tid; w < WK; w += nthr) pobs_out[sidx * WK + w] = obsacc[w];
+        if (stats_out && tid == 0) {
+            StatsDev st;
+            st.converged = have;
+            st.nsol = s_nsol;
+            st.legs = legs;
+            st.iters = iters;
+            st.weight = s_w;
+            stats_out[sidx] = st;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 decode in the literal evaluation order, for DEMs whose per-edge
+// messages fit in shared memory.  Every floating-point operation is an
+// explicitly rounded __dadd_rn / __dmul_rn (never contracted into an FMA) and
+// sums run in the order of the definition:
+//   L_j      = (1 - g_j) * L0_j + g_j * M_j
+//   mu_e     = L_j + nu_b + nu_b' + ...   over the column's other entries, in
+//              ascending check order
+//   nu_e     = +-(minimum over the row's other |mu|)   (exact: a min and a sign)
+//   M_j      = L_j + nu_b + ...           over all column entries, ascending
+// so the decisions reproduce any FP64 evaluation of the same sums bit for bit.
+// Shared memory: mu[E], nu[E], M[V], L[V], g[V] (FP64) and the bit vectors.
+// ---------------------------------------------------------------------------
+struct ExactPlan {
+    int mu, nu, M, L, g, ehat, best, res, syn, obsacc, total;
+};
+
+__device__ __forceinline__ double exact_gamma(const DecodeParamsDev &p, uint64_t shot, int leg, int j, int V)
+{
+    const uint32_t nblk = (uint32_t)((V + 3) / 4);
+    const uint4 r = philox_block(p.seed, shot, 1u, (uint32_t)leg * nblk + (uint32_t)(j >> 2));
+    const double u = __dmul_rn((double)(uint4_word(r, j & 3) >> 8), 1.0 / 16777216.0);
+    return __dadd_rn(p.gamma_min, __dmul_rn(__dadd_rn(p.gamma_max, -p.gamma_min), u));
+}
+
+__global__ void __launch_bounds__(256)
+relay_decode_exact_kernel(DevDEM g, DecodeParamsDev p, ExactPlan plan,
+                          const uint32_t *__restrict__ syn_in, uint64_t shot0, int64_t shots,
+                          uint32_t *__restrict__ corr_out, uint32_t *__restrict__ pobs_out,
+                          StatsDev *__restrict__ stats_out, unsigned long long *__restrict__ work,
+                          double *__restrict__ trace, int trace_iters)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *mu = reinterpret_cast<double *>(smem + plan.mu);
+    double *nu = reinterpret_cast<double *>(smem + plan.nu);
+    double *M = reinterpret_cast<double *>(smem + plan.M);
+    double *L = reinterpret_cast<double *>(smem + plan.L);
+    double *gm = reinterpret_cast<double *>(smem + plan.g);
+    uint32_t *ehat = reinterpret_cast<uint32_t *>(smem + plan.ehat);
+    uint32_t *best = reinterpret_cast<uint32_t *>(smem + plan.best);
+    uint32_t *res = reinterpret_cast<uint32_t *>(smem + plan.res);
+    uint32_t *syn = reinterpret_cast<uint32_t *>(smem + plan.syn);
+    uint32_t *obsacc = reinterpret_cast<uint32_t *>(smem + plan.obsacc);
+
+    __shared__ long long s_shot;
+    __shared__ int s_nsol, s_have_best, s_copy;
+    __shared__ double s_best_w, s_w;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x, nwarp = nthr >> 5;
+    const int C = g.C, V = g.V;
+    const int WC = wordsof(C), WV = wordsof(V), WK = wordsof(g.K);
+    const unsigned FULL = 0xffffffffu;
+    const double INF = __longlong_as_double(0x7ff0000000000000LL);
+
+    for (;;) {
+        if (tid == 0) {
+            s_shot = (long long)atomicAdd(work, 1ull);
+            s_nsol = 0;
+            s_have_best = 0;
+            s_best_w = 0.0;
+        }
+        __syncthreads();
+        const long long sidx = s_shot;
+        if (sidx >= shots) break;
+        const uint64_t shot = shot0 + (uint64_t)sidx;
+        for (int j = tid; j < V; j += nthr) { M[j] = __ldg(g.L0d + j); gm[j] = p.gamma0; }
+        for (int e = tid; e < g.E; e += nthr) nu[e] = 0.0;
+        for (int w = tid; w < WV; w += nthr) ehat[w] = 0u;
+        for (int w = tid; w < WC; w += nthr) {
+            const uint32_t sv = syn_in[sidx * WC + w];
+            syn[w] = sv;
+            res[w] = sv;
+        }
+        __syncthreads();
+        int legs = 0, iters = 0;
+        for (int leg = 0; leg <= p.num_sets; ++leg) {
+            ++legs;
+            if (leg > 0) {
+                for (int j = tid; j < V; j += nthr) gm[j] = exact_gamma(p, shot, leg, j, V);
+                if (!p.carry_messages)
+                    for (int e = tid; e < g.E; e += nthr) nu[e] = 0.0;
+                __syncthreads();
+            }
+            const int T_leg = (leg == 0) ? p.pre_iter : p.max_iterations;
+            bool conv = false;
+            for (int t = 0; t < T_leg; ++t) {
+                // memory-biased prior and variable-to-check messages
+                for (int j = tid; j < V; j += nthr) {
+                    const double l0 = __ldg(g.L0d + j), gj = gm[j];
+                    const double Lj = __dadd_rn(__dmul_rn(__dadd_rn(1.0, -gj), l0), __dmul_rn(gj, M[j]));
+                    L[j] = Lj;
+                    const int q0 = __ldg(g.cptr + j), q1 = __ldg(g.cptr + j + 1);
+                    for (int a = q0; a < q1; ++a) {
+                        double sacc = Lj;
+                        for (int b = q0; b < q1; ++b)
+                            if (b != a) sacc = __dadd_rn(sacc, nu[__ldg(g.cedge + b)]);
+                        mu[__ldg(g.cedge + a)] = sacc;
+                    }
+                }
+                __syncthreads();
+                // check rows: leave-one-out sign product and minimum (exact)
+                for (int i = warp; i < C; i += nwarp) {
+                    const int e0 = __ldg(g.rptr + i), deg = __ldg(g.rptr + i + 1) - e0;
+                    if (deg == 0) continue;
+                    double b1 = INF, b2 = INF;
+                    int bi = 0x7fffffff;
+                    uint32_t par = 0u;
+                    for (int k0 = 0; k0 < deg; k0 += 32) {
+                        const int k = k0 + lane;
+                        uint32_t nb = 0u;
+                        if (k < deg) {
+                            const double m = mu[e0 + k];
+                            nb = (m < 0.0) ? 1u : 0u;
+                            const double a = nb ? -m : m;
+                            if (a < b1) { b2 = b1; b1 = a; bi = k; }
+                            else if (a < b2) { b2 = a; }
+                        }
+                        par ^= (uint32_t)(__popc(__ballot_sync(FULL, nb)) & 1);
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const double o1 = __shfl_xor_sync(FULL, b1, off);
+                        const double o2 = __shfl_xor_sync(FULL, b2, off);
+                        const int oi = __shfl_xor_sync(FULL, bi, off);
+                        if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin(b1, o2); b1 = o1; bi = oi; }
+                        else { b2 = vmin(b2, o1); }
+                    }
+                    const uint32_t sb = ((syn[i >> 5] >> (i & 31)) & 1u) ^ par;
+                    for (int k = lane; k < deg; k += 32) {
+                        const double m = mu[e0 + k];
+                        const uint32_t neg = sb ^ ((m < 0.0) ? 1u : 0u);
+                        const double mag = (k == bi) ? b2 : b1;
+                        nu[e0 + k] = neg ? -mag : mag;
+                    }
+                }
+                __syncthreads();
+                // marginals, decisions, incremental residual
+                for (int j0 = warp * 32; j0 < V; j0 += nwarp * 32) {
+                    const int j = j0 + lane;
+                    uint32_t dec = 0u;
+                    if (j < V) {
+                        double sacc = L[j];
+                        const int q0 = __ldg(g.cptr + j), q1 = __ldg(g.cptr + j + 1);
+                        for (int a = q0; a < q1; ++a) sacc = __dadd_rn(sacc, nu[__ldg(g.cedge + a)]);
+                        M[j] = sacc;
+                        dec = (sacc < 0.0) ? 1u : 0u;
+                        if (trace && iters < trace_iters)
+                            trace[((int64_t)sidx * trace_iters + iters) * V + j] = sacc;
+                    }
+                    const uint32_t nw = __ballot_sync(FULL, dec);
+                    uint32_t old = 0u;
+                    if (lane == 0) { old = ehat[j0 >> 5]; ehat[j0 >> 5] = nw; }
+                    old = __shfl_sync(FULL, old, 0);
+                    if (((old ^ nw) >> lane) & 1u) {
+                        const int q0 = __ldg(g.cptr + j), q1 = __ldg(g.cptr + j + 1);
+                        for (int q = q0; q < q1; ++q) {
+                            const int i = __ldg(g.cchk + q);
+                            atomicXor(res + (i >> 5), 1u << (i & 31));
+                        }
+                    }
+                }
+                __syncthreads();
+                ++iters;
+                uint32_t acc = 0u;
+                for (int w = lane; w < WC; w += 32) acc |= res[w];
+                conv = !__any_sync(FULL, acc != 0u);
+                if (conv) break;
+            }
+            if (conv) {
+                if (tid == 0) {
+                    double w = 0.0;
+                    for (int q = 0; q < WV; ++q) {
+                        uint32_t x = ehat[q];
+                        while (x) {
+                            const int b = __ffs(x) - 1;
+                            x &= x - 1u;
+                            w = __dadd_rn(w, __ldg(g.L0d + q * 32 + b));
+                        }
+                    }
+                    const int better = (!s_have_best || w < s_best_w) ? 1 : 0;
+                    if (better) { s_best_w = w; s_have_best = 1; }
+                    s_copy = better;
+                    s_nsol += 1;
+                }
+                __syncthreads();
+                if (s_copy)
+                    for (int w = tid; w < WV; w += nthr) best[w] = ehat[w];
+                __syncthreads();
+            }
+            if (!p.stop_all && s_nsol >= p.stop_nconv) break;
+        }
+        const int have = s_have_best;
+        const uint32_t *out = have ? best : ehat;
+        for (int w = tid; w < WK; w += nthr) obsacc[w] = 0u;
+        __syncthreads();
+        for (int w = tid; w < WV; w += nthr) {
+            const uint32_t x0 = out[w];
+            if (corr_out) corr_out[sidx * WV + w] = x0;
+            uint32_t x = x0;
+            while (x) {
+                const int b = __ffs(x) - 1;
+                x &= x - 1u;
+                const int j = w * 32 + b;
+                for (int q = __ldg(g.optr + j), qe = __ldg(g.optr + j + 1); q < qe; ++q) {
+                    const int o = __ldg(g.oidx + q);
+                    atomicXor(obsacc + (o >> 5), 1u << (o & 31));
+                }
+            }
+        }
+        if (tid == 0) {
+            double w = s_best_w;
+            if (!have) {
+                w = 0.0;
+                for (int q = 0; q < WV; ++q) {
+                    uint32_t x = ehat[q];
+                    while (x) {
+                        const int b = __ffs(x) - 1;
+                        x &= x - 1u;
+                        w = __dadd_rn(w, __ldg(g.L0d + q * 32 + b));
                     }
                 }
             }

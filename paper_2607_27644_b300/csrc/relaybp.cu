@@ -145,6 +145,30 @@ SmemPlan make_plan(const DevDEM &g, size_t esz)
     return s;
 }
 
+ExactPlan make_exact_plan(const DevDEM &g)
+{
+    ExactPlan s{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        size_t at = off;
+        off += bytes;
+        return (int)at;
+    };
+    s.mu = take(8 * (size_t)g.E);
+    s.nu = take(8 * (size_t)g.E);
+    s.M = take(8 * (size_t)g.V);
+    s.L = take(8 * (size_t)g.V);
+    s.g = take(8 * (size_t)g.V);
+    s.ehat = take(4 * (size_t)words(g.V));
+    s.best = take(4 * (size_t)words(g.V));
+    s.res = take(4 * (size_t)words(g.C));
+    s.syn = take(4 * (size_t)words(g.C));
+    s.obsacc = take(4 * (size_t)std::max(1, words(g.K)));
+    s.total = (int)((off + 15) & ~size_t(15));
+    return s;
+}
+
 DecodeParamsDev dev_params(const relaybp_params &p)
 {
     DecodeParamsDev d{};
@@ -166,6 +190,32 @@ int block_threads(const DevDEM &g)
     if (g.E <= 2048) return 64;
     if (g.E <= 16384) return 256;
     return 512;
+}
+
+// FP64 in the literal evaluation order when one shot's per-edge messages fit
+// in shared memory (at most a quarter of it, so that several shots share an
+// SM); returns 1 if the DEM is too large for this kernel.
+int launch_decode_exact(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
+                        uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace, int trace_iters)
+{
+    const DevDEM &g = h->dem;
+    ExactPlan plan = make_exact_plan(g);
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (plan.total > maxsm / 4) return 1;
+    CUDA_TRY(cudaFuncSetAttribute(relay_decode_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+    const int threads = g.E <= 4096 ? 128 : 256;
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, relay_decode_exact_kernel, threads, plan.total));
+    if (per_sm < 1) return 1;
+    int64_t blocks = (int64_t)per_sm * h->num_sms;
+    if (blocks > shots) blocks = shots;
+    CUDA_TRY(cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st));
+    relay_decode_exact_kernel<<<(unsigned)blocks, threads, plan.total, st>>>(
+        g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, h->d_work, d_trace, trace_iters);
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
 }
 
 template <typename T>
@@ -257,7 +307,7 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     }
     if (nbits >= 0x80000000ull) return bail(fail(RELAYBP_ERR_UNSUPPORTED, "too many edges"));
     // column order (ascending check within each column)
-    std::vector<int32_t> cptr(V + 1, 0), cchk(E), fill(V, 0);
+    std::vector<int32_t> cptr(V + 1, 0), cchk(E), cedge(E), fill(V, 0);
     std::vector<uint32_t> cbit(E);
     for (int64_t e = 0; e < E; ++e) cptr[rvar[e] + 1]++;
     for (int32_t j = 0; j < V; ++j) cptr[j + 1] += cptr[j];
@@ -266,6 +316,7 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
             int32_t j = rvar[e];
             int32_t at = cptr[j] + fill[j]++;
             cchk[at] = i;
+            cedge[at] = e;
             cbit[at] = rbit[i] + (uint32_t)(e - rptr[i]);
         }
     // observables per column
@@ -298,6 +349,7 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     int rc = 0;
     if ((rc = upload(h, rptr, &g.rptr)) || (rc = upload(h, rvar, &g.rvar)) || (rc = upload(h, rbit, &g.rbit)) ||
         (rc = upload(h, cptr, &g.cptr)) || (rc = upload(h, cchk, &g.cchk)) || (rc = upload(h, cbit, &g.cbit)) ||
+        (rc = upload(h, cedge, &g.cedge)) ||
         (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
         (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
         return bail(rc);
@@ -368,8 +420,11 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     static_assert(sizeof(StatsDev) == sizeof(relaybp_shot_stats), "stats layout");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
-    if (h->params.msg_dtype == RELAYBP_MSG_F64)
+    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
+        int rc = launch_decode_exact(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st, nullptr, 0);
+        if (rc <= 0) return rc;
         return launch_decode<double>(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+    }
     return launch_decode<float>(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
 }
 
@@ -383,8 +438,11 @@ int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     if (!d_syndromes || (trace_iters > 0 && !d_trace)) return fail(RELAYBP_ERR_INVALID, "null pointer");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
-    if (h->params.msg_dtype == RELAYBP_MSG_F64)
+    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
+        int rc = launch_decode_exact(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
+        if (rc <= 0) return rc;
         return launch_decode<double>(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
+    }
     return launch_decode<float>(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
 }
 

@@ -59,31 +59,58 @@ def test_sampler_bit_exact(which, request):
 
 
 def test_decode_code_capacity_fp64_full(cc160):
-    """Config: ZSZ-LP-160 H_X, p = 0.05, 10^4 shots, FP64."""
+    """Config: ZSZ-LP-160 H_X, p = 0.05, 10^4 shots, FP64.
+
+    The FP64 kernel evaluates every sum in the order of the definition with
+    explicitly rounded operations, so it reproduces the oracle bit for bit:
+    corrections, statistics, weights and predicted observables."""
     from gpu_util import gpu_decode, params_pair
     po, pg = params_pair(msg_dtype="f64", **CC_KW)
     h = _handle(cc160, pg)
     syn, obs, _ = oracle.sample(cc160, 1, 0, 10_000)
     ro = oracle.decode(cc160, po, syn, shot0=0)
     rg = gpu_decode(h, syn, shot0=0)
-    same = np.all(ro["corrections"] == rg["corrections"], axis=1)
-    assert same.mean() >= 0.999
-    assert np.array_equal(ro["stats"][same], rg["stats"][same])
-    assert np.array_equal(ro["weights"][same], rg["weights"][same])
-    fo, fg = _fail_count(ro, obs), _fail_count(rg, obs)
-    from paper_2607_27644_b300.stats import agree_within
-    assert agree_within(fo, len(syn), fg, len(syn))
+    assert np.array_equal(ro["corrections"], rg["corrections"])
+    assert np.array_equal(ro["stats"], rg["stats"])
+    assert np.array_equal(ro["weights"], rg["weights"])
+    assert np.array_equal(ro["pred_obs"][:, :rg["pred_obs"].shape[1]], rg["pred_obs"])
+    assert _fail_count(ro, obs) == _fail_count(rg, obs)
+
+
+def test_trace_code_capacity_fp64_bit_exact(cc160):
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype="f64", **CC_KW)
+    h = _handle(cc160, pg)
+    syn, _, _ = oracle.sample(cc160, 4, 77, 64)
+    T = 200
+    ro = oracle.decode(cc160, po, syn, shot0=77, trace_iters=T)
+    rg = gpu_decode(h, syn, shot0=77, trace_iters=T)
+    for s in range(64):
+        n = min(T, int(ro["stats"][s, 3]))
+        assert np.array_equal(ro["trace"][s, :n], rg["trace"][s, :n])
 
 
 def test_decode_code_capacity_fp32(cc160):
+    """FP32 messages at p = 0.05 with identical priors: exact ties (M_j = 0,
+    equal |mu|) are frequent, and which side of a tie a sum lands on depends on
+    the precision and order of its rounding, so decisions are compared where
+    they are determined: posteriors until the first diverging decision,
+    converged shots' validity, and the logical error rate."""
     from gpu_util import gpu_decode, params_pair
     po, pg = params_pair(msg_dtype="f32", **CC_KW)
     h = _handle(cc160, pg)
     syn, obs, _ = oracle.sample(cc160, 3, 500, 3001)
-    ro = oracle.decode(cc160, po, syn, shot0=500)
-    rg = gpu_decode(h, syn, shot0=500)
-    same = np.all(ro["corrections"] == rg["corrections"], axis=1)
-    assert same.mean() >= 0.99
+    T = 30
+    ro = oracle.decode(cc160, po, syn, shot0=500, trace_iters=T)
+    rg = gpu_decode(h, syn, shot0=500, trace_iters=T)
+    for s in range(0, 3001, 97):
+        n = min(T, int(ro["stats"][s, 3]))
+        worst, _ = _posterior_parity(ro["trace"][s], rg["trace"][s], n, cc160.n_loc, 1e-4)
+        assert worst <= 1e-4
+    Hd = cc160.dense_H().astype(np.int64)
+    eh = unpack_bits(rg["corrections"], cc160.n_loc).astype(np.int64)
+    conv = rg["stats"][:, 0] == 1
+    assert np.array_equal((eh[conv] @ Hd.T) % 2, unpack_bits(syn, cc160.n_det)[conv])
     from paper_2607_27644_b300.stats import agree_within
     assert agree_within(_fail_count(ro, obs), len(syn), _fail_count(rg, obs), len(syn))
 
@@ -202,9 +229,8 @@ def test_edge_cases(cc160):
         R.relaybp_set_params(h, pg)
         ro = oracle.decode(cc160, po, syn)
         rg = gpu_decode(h, syn)
-        same = np.all(ro["corrections"] == rg["corrections"], axis=1)
-        assert same.mean() >= 0.99
-        assert np.array_equal(ro["stats"][same], rg["stats"][same])
+        assert np.array_equal(ro["corrections"], rg["corrections"])
+        assert np.array_equal(ro["stats"], rg["stats"])
 
 
 def test_unsatisfiable_and_host_path():
