@@ -66,8 +66,8 @@ def _config(dem, batch, steps, world, extra=None):
                      f"DEM {dem.n_det}x{dem.n_loc} (E={dem.n_edges}), plain Relay-BP",
          "decoder": dict(DECODER), "shots_per_step_per_gpu": batch, "steps": steps,
          "shots_total": batch * steps * world,
-         "l2": "flushed between steps (256 MiB write); DEM structure (~1 MB) stays cache-resident by design",
-         "parallelism": f"replicas x{world} (shot ranges)"}
+         "l2": "flushed before every step on that step's stream (256 MiB write)",
+         "parallelism": f"replicas x{world} (shot ranges); 2 streams x 1 handle each, steps alternate"}
     if extra:
         c.update(extra)
     return c
@@ -175,53 +175,67 @@ def run_ours(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dem = _dem()
-    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **DECODER))
+    # Two handles on two streams, alternating steps: the rare shot that runs all
+    # relay legs overlaps the next batch instead of idling the GPU at the end of
+    # its launch.  (Each handle owns its work counter, so launches may overlap.)
+    NS = 2
+    hs = [R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **DECODER)) for _ in range(NS)]
+    h = hs[0]
     B, K, W = a.batch, a.steps, a.warmup
-    st = torch.cuda.Stream(device=dev)
-    syn = torch.empty((B, h.wc), dtype=torch.int32, device=dev)
-    obs = torch.empty((B, h.wk), dtype=torch.int32, device=dev)
-    pobs = torch.empty((B, h.wk), dtype=torch.int32, device=dev)
-    stats = torch.empty((B, 6), dtype=torch.int32, device=dev)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
+    st = streams[0]
+    bufs = [dict(syn=torch.empty((B, h.wc), dtype=torch.int32, device=dev),
+                 obs=torch.empty((B, h.wk), dtype=torch.int32, device=dev),
+                 pobs=torch.empty((B, h.wk), dtype=torch.int32, device=dev),
+                 stats=torch.empty((B, 6), dtype=torch.int32, device=dev)) for _ in range(NS)]
+    syn, obs, pobs, stats = bufs[0]["syn"], bufs[0]["obs"], bufs[0]["pobs"], bufs[0]["stats"]
     counters = torch.zeros(4, dtype=torch.int64, device=dev)
     iters_total = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
     base = rank * B * (K + W)
 
     def step(k, dec_events=None):
+        q = k % NS
+        s_, b_, h_ = streams[q], bufs[q], hs[q]
         shot0 = base + k * B
-        R.relaybp_sample(h, SAMPLE_SEED, shot0, B, syn, obs, None, st)
-        if dec_events:
-            dec_events[0].record(st)
-        R.relaybp_decode_batch(h, syn, shot0, B, None, pobs, stats, st)
-        if dec_events:
-            dec_events[1].record(st)
-        R.relaybp_count_failures(h, pobs, obs, stats, B, counters, st)
+        with torch.cuda.stream(s_):
+            flush.fill_(k)                      # evict L2 before each step (256 MiB write)
+            R.relaybp_sample(h_, SAMPLE_SEED, shot0, B, b_["syn"], b_["obs"], None, s_)
+            if dec_events:
+                dec_events[0].record(s_)
+            R.relaybp_decode_batch(h_, b_["syn"], shot0, B, None, b_["pobs"], b_["stats"], s_)
+            if dec_events:
+                dec_events[1].record(s_)
+            R.relaybp_count_failures(h_, b_["pobs"], b_["obs"], b_["stats"], B, counters, s_)
+            iters_total.add_(b_["stats"][:, 3].sum())
 
-    with torch.cuda.stream(st):
-        for w in range(W):
-            step(K + w)
-            flush.fill_(w)
+    def join():
+        for s_ in streams[1:]:
+            streams[0].wait_stream(s_)
+
+    for w in range(W):
+        step(K + w)
+    torch.cuda.synchronize()
+    counters.zero_()
+    iters_total.zero_()
+    dec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sum(R.relaybp_launch_count(x) for x in hs)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(streams[0])
+        for s_ in streams[1:]:
+            s_.wait_stream(streams[0])
+        for k in range(K):
+            step(k, dec_ev[k])
+        join()
+        t_end.record(streams[0])
         torch.cuda.synchronize()
-        counters.zero_()
-        iters_total.zero_()
-        dec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = R.relaybp_launch_count(h)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            t_start.record(st)
-            for k in range(K):
-                step(k, dec_ev[k])
-                iters_total += stats[:, 3].sum()
-                if k + 1 < K:
-                    flush.fill_(k)
-            t_end.record(st)
-            torch.cuda.synchronize()
-        launches = R.relaybp_launch_count(h) - l0
-        if world > 1:
-            dist.barrier()
+    launches = sum(R.relaybp_launch_count(x) for x in hs) - l0
+    if world > 1:
+        dist.barrier()
     ms = t_start.elapsed_time(t_end)
     dec_ms = [e0.elapsed_time(e1) for e0, e1 in dec_ev]
     tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -246,13 +260,13 @@ def run_ours(a):
                 t.copy_(syn, non_blocking=False)
                 hsyn.append(t)
             hp = torch.empty((B, h.wk), dtype=torch.int32, pin_memory=True)
-            hs = torch.empty((B, 6), dtype=torch.int32, pin_memory=True)
+            hstat = torch.empty((B, 6), dtype=torch.int32, pin_memory=True)
             torch.cuda.synchronize()
             if world > 1:
                 dist.barrier()
             t0 = time.perf_counter()
             for k in range(K):
-                R.relaybp_decode_host(h, hsyn[k], base + k * B, B, hp, hs, st)
+                R.relaybp_decode_host(h, hsyn[k], base + k * B, B, hp, hstat, st)
             e2e_s = time.perf_counter() - t0
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         if world > 1:
@@ -277,18 +291,22 @@ def run_ours(a):
         torch.cuda.synchronize()
     smem_gbs = nb / (e0.elapsed_time(e1) / 1e3) / 1e9
     iters_rank = int(iters_total.item())
+    wall_s = ms / 1e3
     E, V, C = dem.n_edges, dem.n_loc, dem.n_det
     b_m = 4
     bytes_per_iter = 4 * b_m * E + 16 * V + (V + C) / 8.0
     dec_avg_s = sum(dec_ms) / len(dec_ms) / 1e3
     achieved = (iters_rank / K) * bytes_per_iter / dec_avg_s / 1e9
-    edge_updates = iters_rank * E / (sum(dec_ms) / 1e3)
+    edge_updates = iters_rank * E / wall_s
     roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
             "traffic": None,
             "kernel": "relay_decode_kernel<float>",
             "algorithmic_bytes": "per shot-iteration 4*b_m*E + 16*V + (V+C)/8 (b_m=4)",
             "peak_source": "measured live: conflict-free 16-B shared-memory loads on all SMs (relaybp_probe_smem_read)",
-            "edge_updates_per_s": edge_updates, "decode_ms_per_launch": dec_avg_s * 1e3,
+            "edge_updates_per_s_wall": edge_updates, "decode_ms_per_launch": dec_avg_s * 1e3,
+            "achieved_wall": iters_rank * bytes_per_iter / wall_s / 1e9,
+            "note": "two decode launches overlap on two streams; per-launch durations include the overlap, "
+                    "so `achieved` (per-launch) is conservative and `achieved_wall` is the aggregate rate",
             "mean_iterations_per_shot": iters_rank / (B * K)}
     c = cnt.cpu().tolist()
     line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -304,7 +322,8 @@ def run_ours(a):
                                 "sample": f"{a.cpu_sample} shots of the same workload ({dt:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    R.relaybp_destroy(h)
+    for x in hs:
+        R.relaybp_destroy(x)
     if world > 1:
         dist.destroy_process_group()
 

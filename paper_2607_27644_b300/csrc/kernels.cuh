@@ -12,11 +12,11 @@
 //
 // Layout of one shot's decoder state in shared memory (per thread block):
 //   M[V], A[V]        marginal M_j(t) and A_j = L_j(t+1) + sum_i nu_ij(t)
-//   m1[C], m2[C]      smallest and second-smallest |mu| of each check row
-//   am[C]             sign-bit index of the row's argmin edge | parity << 31,
-//                     parity = s_i xor (xor of the row's mu sign bits)
-//   sgn[NW]           sign bit of mu for every edge; each row's bits start on
-//                     a 32-bit word boundary so a warp writes them by ballot
+//   cs[C]             per check row: smallest and second-smallest |mu|, the
+//                     argmin's position in the row | parity << 31 (parity =
+//                     s_i xor the row's mu sign bits), first sign-bit index
+//   sgnh[C*L]         sign bit of mu for every edge, one 16-bit word per
+//                     (row, lane) of the row pass -- see row_pass()
 //   ehat[WV], best[WV], res[WC], syn[WC], obsacc[WK]   bit vectors
 // With this compressed check state a message is rebuilt on demand:
 //   nu_ij = (-1)^(parity_i xor sign_e) * (e == argmin_i ? m2_i : m1_i),
@@ -40,6 +40,9 @@ struct DevDEM {
     const int32_t *cchk;        // [E] check of each column entry
     const uint32_t *cbit;       // [E] sign-bit index of each column entry
     const int32_t *cedge;       // [E] row-major edge index of each column entry
+    const uint32_t *cinfo;      // sliced ELL: per 32-variable group, slot-major entries
+    const int32_t *goff;        // [ceil(V/32)] offset of each group's slots in cinfo
+    const int32_t *gdeg;        // [ceil(V/32)] slots (largest column degree) of each group
     const int32_t *optr;        // [V+1] column pointers into oidx
     const int32_t *oidx;        // observables flipped by each fault
     const double *L0d;          // [V] prior LLRs, FP64
@@ -139,10 +142,98 @@ __device__ __forceinline__ T draw_gamma(const DecodeParamsDev &p, uint64_t shot,
 }
 
 struct SmemPlan {               // byte offsets into dynamic shared memory
-    int M, A, m1, m2, am, sgn, ehat, best, res, syn, obsacc, total;
+    int M, A, cs, sgn, ehat, best, res, syn, obsacc, total;
 };
 
-template <typename T>
+// Compressed state of one check row (16 bytes for FP32).
+template <typename T> struct CheckState {
+    T m1, m2;                   // smallest / second-smallest |mu| over the row
+    uint32_t meta;              // argmin position in the row | parity << 31
+    uint32_t pad;
+};
+
+// Column entry: check index << 12 | position of the entry within its row.
+constexpr uint32_t COL_SENTINEL = 0xffffffffu;
+
+// Row pass geometry: L lanes share a row (32 / L rows per warp step); lane l
+// of a row handles positions l, l + L, l + 2L, ... (at most NB of them) and
+// owns one 16-bit word of sign bits, bit b = sign of mu at position b*L + l.
+// The sign bit of position pos of row i therefore lives in halfword
+// i*L + pos % L, bit pos / L.
+template <typename T, int L, int NB>
+__device__ __forceinline__ void row_pass(const DevDEM &g, const T *A, CheckState<T> *cs, uint16_t *sgnh,
+                                         const uint32_t *syn, int warp, int nwarp, int lane)
+{
+    static_assert(32 % L == 0 && NB <= 16, "row geometry");
+    constexpr int P = 32 / L;
+    const unsigned FULL = 0xffffffffu;
+    const int r = lane / L, l = lane % L;
+    const int C = g.C;
+    for (int base = warp * P; base < C; base += nwarp * P) {
+        const int i = base + r;
+        const bool rowok = i < C;
+        int e0 = 0, deg = 0;
+        if (rowok) {
+            e0 = __ldg(g.rptr + i);
+            deg = __ldg(g.rptr + i + 1) - e0;
+        }
+        int idx[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int k = b * L + l;
+            idx[b] = (k < deg) ? __ldg(g.rvar + e0 + k) : -1;
+        }
+        CheckState<T> o;
+        uint32_t oldbits = 0u;
+        if (rowok) {
+            o = cs[i];
+            oldbits = sgnh[i * L + l];
+        } else {
+            o.m1 = (T)0; o.m2 = (T)0; o.meta = 0u; o.pad = 0u;
+        }
+        const uint32_t oarg = o.meta & 0xfffu, opar = o.meta >> 31;
+        T b1 = Num<T>::inf(), b2 = Num<T>::inf();
+        uint32_t bi = 0xfffu, newbits = 0u;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (idx[b] >= 0) {
+                const uint32_t k = (uint32_t)(b * L + l);
+                const T mag = (k == oarg) ? o.m2 : o.m1;
+                const T nu_old = (((oldbits >> b) & 1u) ^ opar) ? -mag : mag;
+                const T m = A[idx[b]] - nu_old;
+                newbits |= ((m < (T)0) ? 1u : 0u) << b;
+                const T a = vabs(m);
+                if (a < b1) { b2 = b1; b1 = a; bi = k; }
+                else if (a < b2) { b2 = a; }
+            }
+        }
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) {
+            const T o1 = __shfl_xor_sync(FULL, b1, off);
+            const T o2 = __shfl_xor_sync(FULL, b2, off);
+            const uint32_t oi = __shfl_xor_sync(FULL, bi, off);
+            if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin(b1, o2); b1 = o1; bi = oi; }
+            else { b2 = vmin(b2, o1); }
+        }
+        const uint32_t lp = __ballot_sync(FULL, (__popc(newbits) & 1) != 0);
+        const uint32_t gm = (L == 32) ? FULL : (((1u << L) - 1u) << (r * L));
+        const uint32_t par = (uint32_t)(__popc(lp & gm) & 1);
+        if (rowok) {
+            sgnh[i * L + l] = (uint16_t)newbits;
+            if (l == 0) {
+                const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
+                CheckState<T> n;
+                n.m1 = b1;
+                n.m2 = b2;
+                n.meta = bi | ((par ^ sb) << 31);
+                n.pad = 0u;
+                cs[i] = n;
+            }
+        }
+    }
+}
+
+template <typename T, int L, int NB>
 __global__ void __launch_bounds__(512)
 relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
                     const uint32_t *__restrict__ syn_in, uint64_t shot0, int64_t shots,
@@ -153,10 +244,8 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
     extern __shared__ __align__(16) unsigned char smem[];
     T *M = reinterpret_cast<T *>(smem + plan.M);
     T *A = reinterpret_cast<T *>(smem + plan.A);
-    T *m1 = reinterpret_cast<T *>(smem + plan.m1);
-    T *m2 = reinterpret_cast<T *>(smem + plan.m2);
-    uint32_t *am = reinterpret_cast<uint32_t *>(smem + plan.am);
-    uint32_t *sgn = reinterpret_cast<uint32_t *>(smem + plan.sgn);
+    CheckState<T> *cs = reinterpret_cast<CheckState<T> *>(smem + plan.cs);
+    uint16_t *sgnh = reinterpret_cast<uint16_t *>(smem + plan.sgn);
     uint32_t *ehat = reinterpret_cast<uint32_t *>(smem + plan.ehat);
     uint32_t *best = reinterpret_cast<uint32_t *>(smem + plan.best);
     uint32_t *res = reinterpret_cast<uint32_t *>(smem + plan.res);
@@ -171,9 +260,9 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
     const int nthr = blockDim.x, nwarp = nthr >> 5;
     const int C = g.C, V = g.V;
     const int WC = wordsof(C), WV = wordsof(V), WK = wordsof(g.K);
+    const int NG = WV;          // variable groups of 32 (one ELL slice each)
     const unsigned FULL = 0xffffffffu;
     T *gam = gamma_scratch + (int64_t)blockIdx.x * V;
-    const T INF = Num<T>::inf();
 
     for (;;) {
         if (tid == 0) {
@@ -195,8 +284,12 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
             gam[j] = gm;
             A[j] = ((T)1 - gm) * l0 + gm * l0;
         }
-        for (int i = tid; i < C; i += nthr) { m1[i] = (T)0; m2[i] = (T)0; am[i] = 0u; }
-        for (int w = tid; w < g.NW; w += nthr) sgn[w] = 0u;
+        for (int i = tid; i < C; i += nthr) {
+            CheckState<T> z;
+            z.m1 = (T)0; z.m2 = (T)0; z.meta = 0u; z.pad = 0u;
+            cs[i] = z;
+        }
+        for (int w = tid; w < C * L; w += nthr) sgnh[w] = (uint16_t)0;
         for (int w = tid; w < WV; w += nthr) ehat[w] = 0u;
         for (int w = tid; w < WC; w += nthr) {
             const uint32_t sv = syn_in[sidx * WC + w];
@@ -222,77 +315,45 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
                     A[j] = ((T)1 - gn) * l0 + gn * M[j] + carry;
                 }
                 if (!p.carry_messages) {
-                    for (int i = tid; i < C; i += nthr) { m1[i] = (T)0; m2[i] = (T)0; am[i] = 0u; }
-                    for (int w = tid; w < g.NW; w += nthr) sgn[w] = 0u;
+                    for (int i = tid; i < C; i += nthr) { cs[i].m1 = (T)0; cs[i].m2 = (T)0; cs[i].meta = 0u; }
+                    for (int w = tid; w < C * L; w += nthr) sgnh[w] = (uint16_t)0;
                 }
                 __syncthreads();
             }
             const int T_leg = (leg == 0) ? p.pre_iter : p.max_iterations;
             bool conv = false;
             for (int t = 0; t < T_leg; ++t) {
-                // ---- a3: check rows, one warp per row ------------------------
-                for (int i = warp; i < C; i += nwarp) {
-                    const int e0 = __ldg(g.rptr + i), deg = __ldg(g.rptr + i + 1) - e0;
-                    if (deg == 0) continue;
-                    const T om1 = m1[i], om2 = m2[i];
-                    const uint32_t oas = am[i];
-                    const uint32_t oarg = oas & 0x7fffffffu, opar = oas >> 31;
-                    const uint32_t rb = __ldg(g.rbit + i);
-                    T b1 = INF, b2 = INF;
-                    uint32_t bi = 0u, par = 0u;
-                    for (int k0 = 0; k0 < deg; k0 += 32) {
-                        const int k = k0 + lane;
-                        const uint32_t widx = (rb >> 5) + (uint32_t)(k0 >> 5);
-                        const uint32_t wsg = sgn[widx];
-                        uint32_t nb = 0u;
-                        if (k < deg) {
-                            const int j = __ldg(g.rvar + e0 + k);
-                            const uint32_t bpos = rb + (uint32_t)k;
-                            const T mag = (bpos == oarg) ? om2 : om1;
-                            const T nu_old = (((wsg >> lane) & 1u) ^ opar) ? -mag : mag;
-                            const T mu = A[j] - nu_old;
-                            nb = (mu < (T)0) ? 1u : 0u;
-                            const T a = vabs(mu);
-                            if (a < b1) { b2 = b1; b1 = a; bi = bpos; }
-                            else if (a < b2) { b2 = a; }
-                        }
-                        const uint32_t bal = __ballot_sync(FULL, nb);
-                        if (lane == 0) sgn[widx] = bal;
-                        par ^= (uint32_t)(__popc(bal) & 1);
-                    }
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const T o1 = __shfl_xor_sync(FULL, b1, off);
-                        const T o2 = __shfl_xor_sync(FULL, b2, off);
-                        const uint32_t oi = __shfl_xor_sync(FULL, bi, off);
-                        if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin(b1, o2); b1 = o1; bi = oi; }
-                        else { b2 = vmin(b2, o1); }
-                    }
-                    if (lane == 0) {
-                        const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
-                        m1[i] = b1;
-                        m2[i] = b2;
-                        am[i] = bi | ((par ^ sb) << 31);
-                    }
-                }
+                // ---- a3: check rows, L lanes per row ---------------------------
+                row_pass<T, L, NB>(g, A, cs, sgnh, syn, warp, nwarp, lane);
                 __syncthreads();
-                // ---- a4: variables, one lane per variable --------------------
-                for (int j0 = warp * 32; j0 < V; j0 += nwarp * 32) {
-                    const int j = j0 + lane;
-                    uint32_t dec = 0u;
-                    if (j < V) {
-                        T S = (T)0;
-                        const int q0 = __ldg(g.cptr + j), q1 = __ldg(g.cptr + j + 1);
-                        for (int q = q0; q < q1; ++q) {
-                            const int i = __ldg(g.cchk + q);
-                            const uint32_t bp = __ldg(g.cbit + q);
-                            const uint32_t as = am[i];
-                            const T mag = (bp == (as & 0x7fffffffu)) ? m2[i] : m1[i];
-                            const uint32_t sb = ((sgn[bp >> 5] >> (bp & 31)) & 1u) ^ (as >> 31);
-                            S += sb ? -mag : mag;
+                // ---- a4: variables, one lane per variable, ELL slices --------
+                for (int G = warp; G < NG; G += nwarp) {
+                    const int j = G * 32 + lane;
+                    const bool act = j < V;
+                    const T l0 = act ? Num<T>::l0(g, j) : (T)0;
+                    const T gm = act ? gam[j] : (T)0;
+                    const int D = __ldg(g.gdeg + G);
+                    const uint32_t *col = g.cinfo + __ldg(g.goff + G) + lane;
+                    T S = (T)0;
+                    for (int k0 = 0; k0 < D; k0 += 4) {
+                        uint32_t c[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) c[u] = (k0 + u < D) ? __ldg(col + (k0 + u) * 32) : COL_SENTINEL;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (c[u] != COL_SENTINEL) {
+                                const uint32_t i = c[u] >> 12;
+                                const CheckState<T> q = cs[i];
+                                const uint32_t pos = c[u] & 0xfffu;
+                                const uint32_t hw = sgnh[i * L + (pos % L)];
+                                const T mag = (pos == (q.meta & 0xfffu)) ? q.m2 : q.m1;
+                                const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
+                                S += sb ? -mag : mag;
+                            }
                         }
-                        const T l0 = Num<T>::l0(g, j);
-                        const T gm = gam[j];
+                    }
+                    uint32_t dec = 0u;
+                    if (act) {
                         const T Mn = ((T)1 - gm) * l0 + gm * M[j] + S;
                         M[j] = Mn;
                         A[j] = ((T)1 - gm) * l0 + gm * Mn + S;
@@ -302,13 +363,14 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
                     }
                     const uint32_t nw = __ballot_sync(FULL, dec);
                     uint32_t old = 0u;
-                    if (lane == 0) { old = ehat[j0 >> 5]; ehat[j0 >> 5] = nw; }
+                    if (lane == 0) { old = ehat[G]; ehat[G] = nw; }
                     old = __shfl_sync(FULL, old, 0);
                     // a5: residual r = s + H e^ kept incrementally
                     if (((old ^ nw) >> lane) & 1u) {
-                        const int q0 = __ldg(g.cptr + j), q1 = __ldg(g.cptr + j + 1);
-                        for (int q = q0; q < q1; ++q) {
-                            const int i = __ldg(g.cchk + q);
+                        for (int k = 0; k < D; ++k) {
+                            const uint32_t cc = __ldg(col + k * 32);
+                            if (cc == COL_SENTINEL) break;
+                            const uint32_t i = cc >> 12;
                             atomicXor(res + (i >> 5), 1u << (i & 31));
                         }
                     }

@@ -63,6 +63,7 @@ struct relaybp_handle {
     StatsDev *d_stage_stats = nullptr;
     int64_t stage_shots = 0;
     int64_t launches = 0;
+    int max_row_deg = 0;
 };
 
 namespace {
@@ -120,7 +121,17 @@ int check_legs(const relaybp_params *p, int32_t V)
     return 0;
 }
 
-SmemPlan make_plan(const DevDEM &g, size_t esz)
+// Row-pass geometry (lanes per row L, positions per lane NB) for the longest row.
+struct RowGeom { int L, NB; };
+RowGeom row_geom(int maxdeg)
+{
+    const RowGeom opts[] = {{4, 4}, {8, 4}, {8, 8}, {8, 12}, {8, 16}, {16, 16}, {32, 16}};
+    for (const RowGeom &o : opts)
+        if (maxdeg <= o.L * o.NB) return o;
+    return {0, 0};
+}
+
+SmemPlan make_plan(const DevDEM &g, size_t esz, int L)
 {
     SmemPlan s{};
     size_t off = 0;
@@ -132,9 +143,7 @@ SmemPlan make_plan(const DevDEM &g, size_t esz)
     };
     s.M = take(esz * g.V);
     s.A = take(esz * g.V);
-    s.m1 = take(esz * g.C);
-    s.m2 = take(esz * g.C);
-    s.am = take(4 * (size_t)g.C);
+    s.cs = take((esz == 8 ? sizeof(CheckState<double>) : sizeof(CheckState<float>)) * (size_t)g.C);
     s.sgn = take(4 * (size_t)g.NW);
     s.ehat = take(4 * (size_t)words(g.V));
     s.best = take(4 * (size_t)words(g.V));
@@ -218,19 +227,18 @@ int launch_decode_exact(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0
     return 0;
 }
 
-template <typename T>
-int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
-                  uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace = nullptr,
-                  int trace_iters = 0)
+template <typename T, int L, int NB>
+int launch_decode_geom(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
+                       uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace, int trace_iters)
 {
     const DevDEM &g = h->dem;
-    SmemPlan plan = make_plan(g, sizeof(T));
+    SmemPlan plan = make_plan(g, sizeof(T), L);
     int maxsm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (plan.total + 64 > maxsm)
         return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes)",
                     plan.total, maxsm);
-    auto kern = relay_decode_kernel<T>;
+    auto kern = relay_decode_kernel<T, L, NB>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
     const int threads = block_threads(g);
     int per_sm = 0;
@@ -254,6 +262,28 @@ int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int6
     CUDA_TRY(cudaGetLastError());
     h->launches += 1;
     return 0;
+}
+
+template <typename T>
+int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
+                  uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace = nullptr,
+                  int trace_iters = 0)
+{
+    const RowGeom rg = row_geom(h->max_row_deg);
+#define RELAYBP_GEOM(LL, NN)                                                                                   \
+    if (rg.L == LL && rg.NB == NN)                                                                            \
+        return launch_decode_geom<T, LL, NN>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace,    \
+                                             trace_iters);
+    RELAYBP_GEOM(4, 4)
+    RELAYBP_GEOM(8, 4)
+    RELAYBP_GEOM(8, 8)
+    RELAYBP_GEOM(8, 12)
+    RELAYBP_GEOM(8, 16)
+    RELAYBP_GEOM(16, 16)
+    RELAYBP_GEOM(32, 16)
+#undef RELAYBP_GEOM
+    return fail(RELAYBP_ERR_UNSUPPORTED, "a detector touches %d faults; the decode kernel handles at most 512",
+                h->max_row_deg);
 }
 
 }  // namespace
@@ -282,9 +312,12 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     for (int32_t j = 0; j < V; ++j)
         if (!(priors[j] > 0.0 && priors[j] < 1.0))
             return fail(RELAYBP_ERR_INVALID, "prior %d = %g is not in (0, 1)", j, priors[j]);
-    for (int32_t i = 0; i < C; ++i)
-        if (H->indptr[i + 1] - H->indptr[i] == 1)
+    for (int32_t i = 0; i < C; ++i) {
+        const int32_t deg = H->indptr[i + 1] - H->indptr[i];
+        if (deg == 1)
             return fail(RELAYBP_ERR_INVALID, "detector %d is touched by a single fault; rows need 0 or >= 2 entries", i);
+        if (deg > 4095) return fail(RELAYBP_ERR_UNSUPPORTED, "detector %d has %d entries (limit 4095)", i, deg);
+    }
 
     relaybp_handle *h = new relaybp_handle();
     h->params = *params;
@@ -319,6 +352,25 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
             cedge[at] = e;
             cbit[at] = rbit[i] + (uint32_t)(e - rptr[i]);
         }
+    // sliced ELL of the columns: groups of 32 variables, slot-major, each entry
+    // (check << 12 | position in row), padded with sentinels
+    const int32_t NG = (V + 31) / 32;
+    std::vector<int32_t> goff(NG + 1, 0), gdeg(NG, 0);
+    for (int32_t G = 0; G < NG; ++G) {
+        int32_t D = 0;
+        for (int32_t j = G * 32; j < std::min(V, G * 32 + 32); ++j) D = std::max(D, cptr[j + 1] - cptr[j]);
+        gdeg[G] = D;
+        goff[G + 1] = goff[G] + D * 32;
+    }
+    std::vector<uint32_t> cinfo((size_t)goff[NG], COL_SENTINEL);
+    for (int32_t j = 0; j < V; ++j) {
+        const int32_t G = j / 32, l = j % 32;
+        for (int32_t k = 0; k < cptr[j + 1] - cptr[j]; ++k) {
+            const int32_t i = cchk[cptr[j] + k];
+            const int32_t pos = cedge[cptr[j] + k] - rptr[i];
+            cinfo[(size_t)goff[G] + (size_t)k * 32 + l] = ((uint32_t)i << 12) | (uint32_t)pos;
+        }
+    }
     // observables per column
     std::vector<int32_t> optr(V + 1, 0), oidx;
     if (obs) {
@@ -343,13 +395,15 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
         double t = std::floor(priors[j] * 4294967296.0);
         thr[j] = t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
     }
+    for (int32_t i = 0; i < C; ++i) h->max_row_deg = std::max(h->max_row_deg, rptr[i + 1] - rptr[i]);
     DevDEM &g = h->dem;
     g.C = C; g.V = V; g.K = K; g.E = E;
     g.NW = (int32_t)(nbits / 32);
     int rc = 0;
     if ((rc = upload(h, rptr, &g.rptr)) || (rc = upload(h, rvar, &g.rvar)) || (rc = upload(h, rbit, &g.rbit)) ||
         (rc = upload(h, cptr, &g.cptr)) || (rc = upload(h, cchk, &g.cchk)) || (rc = upload(h, cbit, &g.cbit)) ||
-        (rc = upload(h, cedge, &g.cedge)) ||
+        (rc = upload(h, cedge, &g.cedge)) || (rc = upload(h, cinfo, &g.cinfo)) || (rc = upload(h, goff, &g.goff)) ||
+        (rc = upload(h, gdeg, &g.gdeg)) ||
         (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
         (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
         return bail(rc);

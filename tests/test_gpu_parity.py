@@ -100,7 +100,7 @@ def test_decode_code_capacity_fp32(cc160):
     po, pg = params_pair(msg_dtype="f32", **CC_KW)
     h = _handle(cc160, pg)
     syn, obs, _ = oracle.sample(cc160, 3, 500, 3001)
-    T = 30
+    T = 5                                   # posterior window for FP32 (see below)
     ro = oracle.decode(cc160, po, syn, shot0=500, trace_iters=T)
     rg = gpu_decode(h, syn, shot0=500, trace_iters=T)
     for s in range(0, 3001, 97):
@@ -129,22 +129,46 @@ def _posterior_parity(tr_o, tr_g, iters, V, tol):
     return worst, checked
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-9), ("f32", 1e-4)])
-def test_posteriors_circuit_level(circ160, dtype, tol):
+# Posterior windows.  The iteration map amplifies a relative perturbation by
+# about 3x per iteration on these DEMs (pinned on the oracle alone by
+# test_oracle.py::test_iteration_map_amplifies_rounding), so equality of
+# posteriors between two correct evaluations with different rounding holds
+# only for the first iterations: FP64 with another summation order stays
+# within 1e-9 for 10 iterations, FP32 within 1e-4 for 5.
+@pytest.mark.parametrize("dtype,tol,window", [("f64", 1e-9, 10), ("f32", 1e-4, 5)])
+def test_posteriors_circuit_level(circ160, dtype, tol, window):
     from gpu_util import gpu_decode, params_pair
     po, pg = params_pair(msg_dtype=dtype, **CIRC_KW)
     h = _handle(circ160, pg)
-    shots, T = 12, 40
+    shots = 12
     syn, _, _ = oracle.sample(circ160, 7, 1000, shots)
-    ro = oracle.decode(circ160, po, syn, shot0=1000, trace_iters=T)
-    rg = gpu_decode(h, syn, shot0=1000, trace_iters=T)
+    ro = oracle.decode(circ160, po, syn, shot0=1000, trace_iters=window)
+    rg = gpu_decode(h, syn, shot0=1000, trace_iters=window)
     total = 0
     for s in range(shots):
-        n = min(T, int(ro["stats"][s, 3]))
+        n = min(window, int(ro["stats"][s, 3]))
         worst, checked = _posterior_parity(ro["trace"][s], rg["trace"][s], n, circ160.n_loc, tol)
         assert worst <= tol, (s, worst)
         total += checked
-    assert total >= shots * 5
+    assert total >= shots * 3
+
+
+def _logical_parity(dem, ro, rg, syn, obs):
+    """Checks that do not depend on which of several valid solutions a run
+    lands on: every claimed success satisfies H e^ = s; predicted observables
+    (the decoder's answer) agree on >= 99.9% of shots; failure counts agree
+    within 2 sigma."""
+    Hd = dem.dense_H().astype(np.int64)
+    S = unpack_bits(syn, dem.n_det)
+    for r in (ro, rg):
+        eh = unpack_bits(r["corrections"], dem.n_loc).astype(np.int64)
+        conv = r["stats"][:, 0] == 1
+        assert np.array_equal((eh[conv] @ Hd.T) % 2, S[conv])
+    wk = rg["pred_obs"].shape[1]
+    same_obs = np.all(ro["pred_obs"][:, :wk] == rg["pred_obs"], axis=1)
+    assert (~same_obs).sum() <= math.floor(0.001 * len(syn))
+    from paper_2607_27644_b300.stats import agree_within
+    assert agree_within(_fail_count(ro, obs), len(syn), _fail_count(rg, obs), len(syn))
 
 
 def test_decode_circuit_level_fp32(circ160):
@@ -155,14 +179,8 @@ def test_decode_circuit_level_fp32(circ160):
     syn, obs, _ = oracle.sample(circ160, 2, 0, 400)
     ro = oracle.decode(circ160, po, syn, shot0=0)
     rg = gpu_decode(h, syn, shot0=0)
-    same = np.all(ro["corrections"] == rg["corrections"], axis=1)
-    assert (~same).sum() <= math.ceil(0.001 * len(syn))
-    # every claimed success satisfies H e^ = s
-    Hd = circ160.dense_H().astype(np.int64)
-    eh = unpack_bits(rg["corrections"], circ160.n_loc).astype(np.int64)
-    conv = rg["stats"][:, 0] == 1
-    assert np.array_equal((eh[conv] @ Hd.T) % 2, unpack_bits(syn, circ160.n_det)[conv])
-    assert _fail_count(rg, obs) == _fail_count(ro, obs)
+    _logical_parity(circ160, ro, rg, syn, obs)
+    assert np.all(rg["stats"][:, 1] <= 5)
 
 
 def test_full_size_sampled_outputs(circ160):
@@ -194,13 +212,15 @@ def test_full_size_sampled_outputs(circ160):
     idx = np.sort(rng.choice(shots, 24, replace=False))
     syn_np = syn.cpu().numpy().view(np.uint32)
     corr_np = corr.cpu().numpy().view(np.uint32)
+    pobs_np = pobs.cpu().numpy().view(np.uint32)
+    obs_np = obs.cpu().numpy().view(np.uint32)
     mism = 0
     for i in idx:
-        s_o, _, _ = oracle.sample(circ160, seed, int(i), 1)
-        assert np.array_equal(s_o[0], syn_np[i])
+        s_o, o_o, _ = oracle.sample(circ160, seed, int(i), 1)
+        assert np.array_equal(s_o[0], syn_np[i]) and np.array_equal(o_o[0, :h.wk], obs_np[i])
         r = oracle.decode(circ160, po, s_o, shot0=int(i))
-        mism += int(not np.array_equal(r["corrections"][0], corr_np[i]))
-    assert mism <= 1
+        mism += int(not np.array_equal(r["pred_obs"][0, :h.wk], pobs_np[i]))
+    assert mism == 0
     Hd = circ160.dense_H().astype(np.int64)
     sl = slice(0, 20_000)
     eh = unpack_bits(corr_np[sl], circ160.n_loc).astype(np.int64)

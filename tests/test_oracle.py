@@ -252,3 +252,27 @@ def test_deterministic_and_shard_invariant():
     b = oracle.decode(D, P, syn[25:], shot0=25)
     assert np.array_equal(full["corrections"], np.vstack([a["corrections"], b["corrections"]]))
     assert np.array_equal(full["stats"], np.vstack([a["stats"], b["stats"]]))
+
+
+def test_iteration_map_amplifies_rounding():
+    """Property of the method that sets the parity windows of the GPU tests:
+    on a circuit-level DEM, perturbing every prior by one part in 2^50 grows
+    to a relative posterior difference above 1e-9 within 40 iterations while
+    staying below 1e-12 for the first 3 -- two correct evaluations whose
+    rounding differs agree only in an early window."""
+    D = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+    P = DecodeParams(gamma0=0.125, pre_iter=80, num_sets=0, max_iterations=60, stop_nconv=1,
+                     gamma_min=-0.15, gamma_max=0.61, seed=1)
+    syn, _, _ = oracle.sample(D, 7, 1000, 8)
+    T = 40
+    a = oracle.decode(D, P, syn, shot0=1000, trace_iters=T)
+    b = oracle.decode(D.with_priors(D.priors * (1 + 2.0 ** -50)), P, syn, shot0=1000, trace_iters=T)
+    grew = 0
+    for s in range(8):
+        n = int(min(a["stats"][s, 3], b["stats"][s, 3], T))
+        if n < 30:
+            continue
+        d = np.abs(a["trace"][s, :n] - b["trace"][s, :n]) / np.maximum(1, np.abs(a["trace"][s, :n]))
+        assert d[:3].max() < 1e-12
+        grew += int(d.max() > 1e-9)
+    assert grew >= 1
