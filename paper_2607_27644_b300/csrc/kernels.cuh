@@ -32,13 +32,10 @@ namespace relaybp {
 struct DevDEM {
     int32_t C, V, K;
     int64_t E;
-    int32_t NW;                 // sign-bit words (rows padded to 32 bits)
     const int32_t *rptr;        // [C+1] row pointers into rvar
     const int32_t *rvar;        // [E] variable of each edge, row-major
-    const uint32_t *rbit;       // [C] first sign-bit index of each row (multiple of 32)
     const int32_t *cptr;        // [V+1] column pointers into cchk / cbit
     const int32_t *cchk;        // [E] check of each column entry
-    const uint32_t *cbit;       // [E] sign-bit index of each column entry
     const int32_t *cedge;       // [E] row-major edge index of each column entry
     const uint32_t *cinfo;      // sliced ELL: per 32-variable group, slot-major entries
     const int32_t *goff;        // [ceil(V/32)] offset of each group's slots in cinfo

@@ -1,9 +1,9 @@
 // Host side of the C ABI declared in include/relaybp.h.
 //
 // relaybp_build lays the DEM out for the kernels: the check matrix in row
-// order (one sign bit per edge, rows padded to 32-bit words) and in column
-// order (check and sign-bit index of each entry), prior LLRs in FP64 and FP32,
-// and the sampler thresholds floor(p_j 2^32).  The handle owns every device
+// order, in column order (check and row-major edge of each entry) and as
+// sliced-ELL column groups of 32 variables (check << 12 | position in row),
+// prior LLRs in FP64 and FP32, and the sampler thresholds floor(p_j 2^32).  The handle owns every device
 // allocation and a small scratch area: the persistent kernel's work counter,
 // failure counters and a per-block buffer for the leg's memory strengths.
 #include <cmath>
@@ -144,7 +144,7 @@ SmemPlan make_plan(const DevDEM &g, size_t esz, int L)
     s.M = take(esz * g.V);
     s.A = take(esz * g.V);
     s.cs = take((esz == 8 ? sizeof(CheckState<double>) : sizeof(CheckState<float>)) * (size_t)g.C);
-    s.sgn = take(4 * (size_t)g.NW);
+    s.sgn = take(2 * (size_t)g.C * (size_t)L);      // row_pass: one 16-bit sign word per (row, lane)
     s.ehat = take(4 * (size_t)words(g.V));
     s.best = take(4 * (size_t)words(g.V));
     s.res = take(4 * (size_t)words(g.C));
@@ -330,18 +330,10 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (ce != cudaSuccess) { delete h; return fail(RELAYBP_ERR_CUDA, "SM count: %s", cudaGetErrorString(ce)); }
 
-    // row order: variables and 32-aligned sign-bit bases
+    // row order
     std::vector<int32_t> rptr(H->indptr, H->indptr + C + 1), rvar(H->indices, H->indices + E);
-    std::vector<uint32_t> rbit(C);
-    uint64_t nbits = 0;
-    for (int32_t i = 0; i < C; ++i) {
-        rbit[i] = (uint32_t)nbits;
-        nbits += (uint64_t)(H->indptr[i + 1] - H->indptr[i] + 31) / 32 * 32;
-    }
-    if (nbits >= 0x80000000ull) return bail(fail(RELAYBP_ERR_UNSUPPORTED, "too many edges"));
     // column order (ascending check within each column)
     std::vector<int32_t> cptr(V + 1, 0), cchk(E), cedge(E), fill(V, 0);
-    std::vector<uint32_t> cbit(E);
     for (int64_t e = 0; e < E; ++e) cptr[rvar[e] + 1]++;
     for (int32_t j = 0; j < V; ++j) cptr[j + 1] += cptr[j];
     for (int32_t i = 0; i < C; ++i)
@@ -350,7 +342,6 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
             int32_t at = cptr[j] + fill[j]++;
             cchk[at] = i;
             cedge[at] = e;
-            cbit[at] = rbit[i] + (uint32_t)(e - rptr[i]);
         }
     // sliced ELL of the columns: groups of 32 variables, slot-major, each entry
     // (check << 12 | position in row), padded with sentinels
@@ -398,10 +389,9 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     for (int32_t i = 0; i < C; ++i) h->max_row_deg = std::max(h->max_row_deg, rptr[i + 1] - rptr[i]);
     DevDEM &g = h->dem;
     g.C = C; g.V = V; g.K = K; g.E = E;
-    g.NW = (int32_t)(nbits / 32);
     int rc = 0;
-    if ((rc = upload(h, rptr, &g.rptr)) || (rc = upload(h, rvar, &g.rvar)) || (rc = upload(h, rbit, &g.rbit)) ||
-        (rc = upload(h, cptr, &g.cptr)) || (rc = upload(h, cchk, &g.cchk)) || (rc = upload(h, cbit, &g.cbit)) ||
+    if ((rc = upload(h, rptr, &g.rptr)) || (rc = upload(h, rvar, &g.rvar)) || 
+        (rc = upload(h, cptr, &g.cptr)) || (rc = upload(h, cchk, &g.cchk)) || 
         (rc = upload(h, cedge, &g.cedge)) || (rc = upload(h, cinfo, &g.cinfo)) || (rc = upload(h, goff, &g.goff)) ||
         (rc = upload(h, gdeg, &g.gdeg)) ||
         (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
