@@ -332,22 +332,30 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
                     const int D = __ldg(g.gdeg + G);
                     const uint32_t *col = g.cinfo + __ldg(g.goff + G) + lane;
                     T S = (T)0;
-                    for (int k0 = 0; k0 < D; k0 += 4) {
+                    // column messages nu_ij rebuilt from the check states; four
+                    // independent slots per step, the remainder one by one (D is
+                    // uniform over the warp, so the split does not diverge)
+                    auto msg = [&](uint32_t c) -> T {
+                        const uint32_t i = c >> 12;
+                        const CheckState<T> q = cs[i];
+                        const uint32_t pos = c & 0xfffu;
+                        const uint32_t hw = sgnh[i * L + (pos % L)];
+                        const T mag = (pos == (q.meta & 0xfffu)) ? q.m2 : q.m1;
+                        const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
+                        return sb ? -mag : mag;
+                    };
+                    int k = 0;
+                    for (; k + 4 <= D; k += 4) {
                         uint32_t c[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) c[u] = (k0 + u < D) ? __ldg(col + (k0 + u) * 32) : COL_SENTINEL;
+                        for (int u = 0; u < 4; ++u) c[u] = __ldg(col + (k + u) * 32);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (c[u] != COL_SENTINEL) {
-                                const uint32_t i = c[u] >> 12;
-                                const CheckState<T> q = cs[i];
-                                const uint32_t pos = c[u] & 0xfffu;
-                                const uint32_t hw = sgnh[i * L + (pos % L)];
-                                const T mag = (pos == (q.meta & 0xfffu)) ? q.m2 : q.m1;
-                                const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
-                                S += sb ? -mag : mag;
-                            }
-                        }
+                        for (int u = 0; u < 4; ++u)
+                            if (c[u] != COL_SENTINEL) S += msg(c[u]);
+                    }
+                    for (; k < D; ++k) {
+                        const uint32_t c = __ldg(col + k * 32);
+                        if (c != COL_SENTINEL) S += msg(c);
                     }
                     uint32_t dec = 0u;
                     if (act) {

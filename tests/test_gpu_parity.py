@@ -100,7 +100,7 @@ def test_decode_code_capacity_fp32(cc160):
     po, pg = params_pair(msg_dtype="f32", **CC_KW)
     h = _handle(cc160, pg)
     syn, obs, _ = oracle.sample(cc160, 3, 500, 3001)
-    T = 5                                   # posterior window for FP32 (see below)
+    T = 4                                   # FP32 posterior window (see test_posteriors_circuit_level)
     ro = oracle.decode(cc160, po, syn, shot0=500, trace_iters=T)
     rg = gpu_decode(h, syn, shot0=500, trace_iters=T)
     for s in range(0, 3001, 97):
@@ -130,12 +130,13 @@ def _posterior_parity(tr_o, tr_g, iters, V, tol):
 
 
 # Posterior windows.  The iteration map amplifies a relative perturbation by
-# about 3x per iteration on these DEMs (pinned on the oracle alone by
-# test_oracle.py::test_iteration_map_amplifies_rounding), so equality of
-# posteriors between two correct evaluations with different rounding holds
-# only for the first iterations: FP64 with another summation order stays
-# within 1e-9 for 10 iterations, FP32 within 1e-4 for 5.
-@pytest.mark.parametrize("dtype,tol,window", [("f64", 1e-9, 10), ("f32", 1e-4, 5)])
+# about 3x per iteration on these DEMs, up to ~4.4x on some shots (pinned on
+# the oracle alone by test_oracle.py::test_iteration_map_amplifies_rounding),
+# so equality of posteriors between two correct evaluations with different
+# rounding holds only for the first iterations: FP64 with another summation
+# order stays within 1e-9 for 10 iterations; FP32 (unit roundoff 6e-8) stays
+# within 1e-4 for 4 (6e-8 * 4.4^4 = 2e-5, with margin for the first rounding).
+@pytest.mark.parametrize("dtype,tol,window", [("f64", 1e-9, 10), ("f32", 1e-4, 4)])
 def test_posteriors_circuit_level(circ160, dtype, tol, window):
     from gpu_util import gpu_decode, params_pair
     po, pg = params_pair(msg_dtype=dtype, **CIRC_KW)
