@@ -192,12 +192,12 @@ def run_ours(a):
     counters = torch.zeros(4, dtype=torch.int64, device=dev)
     iters_total = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
-    base = rank * B * (K + W)
+    from paper_2607_27644_b300.replicas import shot_range, reduce_counters
 
     def step(k, dec_events=None):
         q = k % NS
         s_, b_, h_ = streams[q], bufs[q], hs[q]
-        shot0 = base + k * B
+        shot0, _ = shot_range(rank, world, K + W, B, k)
         with torch.cuda.stream(s_):
             flush.fill_(k)                      # evict L2 before each step (256 MiB write)
             R.relaybp_sample(h_, SAMPLE_SEED, shot0, B, b_["syn"], b_["obs"], None, s_)
@@ -238,14 +238,8 @@ def run_ours(a):
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     dec_ms = [e0.elapsed_time(e1) for e0, e1 in dec_ev]
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    cnt = counters.clone()
-    it = iters_total.clone()
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cnt)
-        dist.all_reduce(it)
-    ms_max = float(tmax.item())
+    cnt, ms_max = reduce_counters(torch.cat([counters, iters_total]), ms)
+    cnt = cnt[:4]
     shots_total = B * K * world
     value = shots_total / (ms_max / 1e3)
 
@@ -255,7 +249,7 @@ def run_ours(a):
         with torch.cuda.stream(st):
             hsyn = []
             for k in range(K):
-                R.relaybp_sample(h, SAMPLE_SEED, base + k * B, B, syn, obs, None, st)
+                R.relaybp_sample(h, SAMPLE_SEED, shot_range(rank, world, K + W, B, k)[0], B, syn, obs, None, st)
                 t = torch.empty((B, h.wc), dtype=torch.int32, pin_memory=True)
                 t.copy_(syn, non_blocking=False)
                 hsyn.append(t)
@@ -266,12 +260,10 @@ def run_ours(a):
                 dist.barrier()
             t0 = time.perf_counter()
             for k in range(K):
-                R.relaybp_decode_host(h, hsyn[k], base + k * B, B, hp, hstat, st)
+                R.relaybp_decode_host(h, hsyn[k], shot_range(rank, world, K + W, B, k)[0], B, hp, hstat, st)
             e2e_s = time.perf_counter() - t0
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": shots_total / float(t.item()), "unit": "shots/s", "h2d_bytes_per_step": B * h.wc * 4,
+        _, e2e_max = reduce_counters(torch.zeros(1, dtype=torch.int64, device=dev), e2e_s)
+        e2e = {"value": shots_total / e2e_max, "unit": "shots/s", "h2d_bytes_per_step": B * h.wc * 4,
                "d2h_bytes_per_step": B * (h.wk * 4 + 24),
                "path": "relaybp_decode_host: pinned host syndromes -> device -> decode -> host predicted "
                        "observables + per-shot stats, synchronised each step"}
