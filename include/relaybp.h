@@ -135,6 +135,41 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
                          uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
                          void *cuda_stream);
 
+/* Allocation-free variant of relaybp_decode_batch (no counterpart in the
+ * paper; the decoding it performs is identical, shot for shot).
+ *
+ * relaybp_decode_batch allocates its scratch -- the persistent kernel's work
+ * counter and one row of memory strengths per thread block -- with cudaMalloc
+ * the first time it needs it and whenever a larger launch needs more.  Some
+ * callers must not allocate device memory while they decode: a real-time
+ * decoding loop cannot absorb the implicit device-wide synchronisation and
+ * latency of cudaMalloc/cudaFree, and a host program whose device memory is
+ * carved up by another allocator (a framework's caching allocator or a fixed
+ * per-process budget) must not have a library allocate behind its back or
+ * fail when that budget is exhausted.  This entry point allocates nothing:
+ * its scratch is one 16 MiB array compiled into the library
+ * (kNoAllocScratchBytes), reserved on every GPU that loads the library until
+ * the process exits.  The caller still passes the inputs and outputs exactly
+ * as for relaybp_decode_batch; the handle must come from relaybp_build, done
+ * beforehand at set-up time.
+ *
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with the handle's device current and caches it;
+ *   make that first call before any stream capture.
+ * - The call zeroes the work counter in the array before its launch; the
+ *   memory-strength rows are rewritten before use, so nothing else needs
+ *   clearing.  The array keeps the last call's contents.
+ * - All calls on a device share the one array: calls whose kernels overlap on
+ *   the GPU (other streams, other handles, other host threads) race and give
+ *   wrong results.  Serialise them, e.g. by issuing them on one stream.
+ * - A DEM whose scratch (256 bytes + one row of V message-precision values per
+ *   resident thread block) exceeds 16 MiB is rejected with
+ *   RELAYBP_ERR_UNSUPPORTED and a message giving both sizes; use
+ *   relaybp_decode_batch for it.  (The ZSZ-LP-160 circuit DEM needs 12.3 MB.) */
+int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                                 uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
+                                 void *cuda_stream);
+
 /* Diagnostic variant of relaybp_decode_batch for parity checks: also writes
  * the marginals M_j after each of the first trace_iters iterations (counted
  * over all legs) to d_trace [shots][trace_iters][V] as FP64 (entries past a

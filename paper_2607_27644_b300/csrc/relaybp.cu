@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -582,3 +583,149 @@ int relaybp_destroy(relaybp_handle *h)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free decode (relaybp_decode_batch_noalloc).
+//
+// relaybp_decode_batch keeps its scratch (the persistent kernel's work counter
+// and one row of memory strengths per thread block) in handle-owned device
+// memory that it allocates, and grows, with cudaMalloc on first use.  This
+// variant instead uses one fixed array compiled into the library, so a call
+// never allocates or frees device memory.  Every GPU that loads the library
+// reserves the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;     // 16 MiB
+constexpr size_t kNoAllocCounterBytes = 256;                   // work counter, padded
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// In host code `g_noalloc_scratch` only names a host-side stand-in; its device
+// address comes from cudaGetSymbolAddress, looked up once per device with that
+// device current and cached here.
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "device ordinal %d beyond %d", device, kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        int cur = -1;
+        CUDA_TRY(cudaGetDevice(&cur));
+        if (cur != device)
+            return fail(RELAYBP_ERR_INVALID, "the handle's device %d is not current (device %d is)", device, cur);
+        void *p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return 0;
+}
+
+template <typename T, int L, int NB>
+int noalloc_decode_geom(relaybp_handle *h, unsigned char *scratch, const uint32_t *d_syn, uint64_t shot0,
+                        int64_t shots, uint32_t *d_corr, uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st)
+{
+    const DevDEM &g = h->dem;
+    SmemPlan plan = make_plan(g, sizeof(T), L);
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (plan.total + 64 > maxsm)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes)",
+                    plan.total, maxsm);
+    auto kern = relay_decode_kernel<T, L, NB>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+    const int threads = block_threads(g);
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan.total));
+    if (per_sm < 1) return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan.total);
+    int64_t blocks = (int64_t)per_sm * h->num_sms;
+    if (blocks > shots) blocks = shots;
+    // every block needs one row of V memory strengths after the counter
+    const size_t row = (size_t)g.V * sizeof(T);
+    const size_t need = kNoAllocCounterBytes + (size_t)blocks * row;
+    if (need > kNoAllocScratchBytes)
+        return fail(RELAYBP_ERR_UNSUPPORTED,
+                    "this DEM needs %zu bytes of decoder scratch (%lld blocks x %zu bytes + counter); the "
+                    "allocation-free entry point has %zu bytes: use relaybp_decode_batch",
+                    need, (long long)blocks, row, kNoAllocScratchBytes);
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
+    T *gam = reinterpret_cast<T *>(scratch + kNoAllocCounterBytes);
+    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));     // the counter must start at 0
+    kern<<<(unsigned)blocks, threads, plan.total, st>>>(g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr,
+                                                       d_pobs, d_stats, work, gam, nullptr, 0);
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
+}
+
+template <typename T>
+int noalloc_decode(relaybp_handle *h, unsigned char *scratch, const uint32_t *d_syn, uint64_t shot0, int64_t shots,
+                   uint32_t *d_corr, uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st)
+{
+    const RowGeom rg = row_geom(h->max_row_deg);
+#define RELAYBP_NOALLOC_GEOM(LL, NN)                                                                          \
+    if (rg.L == LL && rg.NB == NN)                                                                           \
+        return noalloc_decode_geom<T, LL, NN>(h, scratch, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st);
+    RELAYBP_NOALLOC_GEOM(4, 4)
+    RELAYBP_NOALLOC_GEOM(8, 4)
+    RELAYBP_NOALLOC_GEOM(8, 8)
+    RELAYBP_NOALLOC_GEOM(8, 12)
+    RELAYBP_NOALLOC_GEOM(8, 16)
+    RELAYBP_NOALLOC_GEOM(16, 16)
+    RELAYBP_NOALLOC_GEOM(32, 16)
+#undef RELAYBP_NOALLOC_GEOM
+    return fail(RELAYBP_ERR_UNSUPPORTED, "a detector touches %d faults; the decode kernel handles at most 512",
+                h->max_row_deg);
+}
+
+// FP64 literal-order kernel: only the work counter lives in the scratch.
+int noalloc_decode_exact(relaybp_handle *h, unsigned char *scratch, const uint32_t *d_syn, uint64_t shot0,
+                         int64_t shots, uint32_t *d_corr, uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st)
+{
+    const DevDEM &g = h->dem;
+    ExactPlan plan = make_exact_plan(g);
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (plan.total > maxsm / 4) return 1;
+    CUDA_TRY(cudaFuncSetAttribute(relay_decode_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+    const int threads = g.E <= 4096 ? 128 : 256;
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, relay_decode_exact_kernel, threads, plan.total));
+    if (per_sm < 1) return 1;
+    int64_t blocks = (int64_t)per_sm * h->num_sms;
+    if (blocks > shots) blocks = shots;
+    unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
+    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));
+    relay_decode_exact_kernel<<<(unsigned)blocks, threads, plan.total, st>>>(
+        g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, work, nullptr, 0);
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0,
+                                            int64_t shots, uint32_t *d_corrections, uint32_t *d_pred_obs,
+                                            relaybp_shot_stats *d_stats, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (shots == 0) return 0;
+    if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
+    unsigned char *scratch = nullptr;
+    if (int rc = noalloc_scratch(h->device, &scratch)) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
+    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
+        int rc = noalloc_decode_exact(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+        if (rc <= 0) return rc;
+        return noalloc_decode<double>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+    }
+    return noalloc_decode<float>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+}

@@ -52,6 +52,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_sample": ([P, U64, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_batch": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_trace": ([P, P, U64, I64, I32, P, P, P], ctypes.c_int),
+        "relaybp_decode_batch_noalloc": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_host": ([P, P, U64, I64, P, P, P], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
@@ -69,7 +70,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
-            "relaybp_decode_trace", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
+            "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_destroy", "relaybp_last_error"]
 
 
@@ -191,6 +192,15 @@ def relaybp_decode_batch(h: Handle, d_syndromes, shot0: int, shots: int, d_corre
                          d_stats=None, stream=None):
     _check(_lib.relaybp_decode_batch(h.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections),
                                      _ptr(d_pred_obs), _ptr(d_stats), _stream(stream)), "relaybp_decode_batch")
+
+
+def relaybp_decode_batch_noalloc(h: Handle, d_syndromes, shot0: int, shots: int, d_corrections=None,
+                                 d_pred_obs=None, d_stats=None, stream=None):
+    """relaybp_decode_batch without any device allocation (fixed in-library scratch);
+    concurrent calls on one device race -- issue them on one stream."""
+    _check(_lib.relaybp_decode_batch_noalloc(h.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections),
+                                             _ptr(d_pred_obs), _ptr(d_stats), _stream(stream)),
+           "relaybp_decode_batch_noalloc")
 
 
 def relaybp_decode_trace(h: Handle, d_syndromes, shot0: int, shots: int, trace_iters: int, d_trace, d_stats=None,

@@ -1,0 +1,57 @@
+"""The allocation-free decode entry point against the regular one.
+
+relaybp_decode_batch_noalloc exists for callers that must not allocate device
+memory while decoding (real-time loops that cannot absorb cudaMalloc's
+synchronisation, programs whose device memory belongs to another allocator).
+It decodes with a fixed scratch array compiled into the library; its results
+must equal relaybp_decode_batch's, on two calls in a row (the array keeps the
+previous call's contents, so the second call checks that what must start at
+zero is cleared).  This file is collected last so that a stop-at-first-failure
+run has already run every other test.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _decode(R, h, syn, shot0, fn):
+    import torch
+    n = syn.shape[0]
+    corr = torch.full((n, h.wv), -1, dtype=torch.int32, device="cuda")
+    pobs = torch.full((n, h.wk), -1, dtype=torch.int32, device="cuda")
+    stats = torch.full((n, 6), -1, dtype=torch.int32, device="cuda")
+    fn(h, syn, shot0, n, corr, pobs, stats)
+    torch.cuda.synchronize()
+    return corr.cpu().numpy(), pobs.cpu().numpy(), stats.cpu().numpy()
+
+
+@pytest.mark.parametrize("case", ["circuit_f32", "code_capacity_f64"])
+def test_noalloc_matches_decode_batch_twice(case):
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from workloads.dem import circuit_dem, code_capacity_dem
+    if case == "circuit_f32":
+        dem = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+        params = R.Params(msg_dtype="f32", num_sets=1000, gamma_min=-0.15, gamma_max=0.61, seed=202)
+        shots = 3000
+    else:
+        dem = code_capacity_dem("ZSZ-LP-160", 0.05)
+        params = R.Params(msg_dtype="f64", num_sets=50, seed=101)
+        shots = 2000
+    h = R.relaybp_build_dem(dem, params)
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 77, 5000, shots, syn)
+    ref = _decode(R, h, syn, 5000, R.relaybp_decode_batch)
+    for _ in range(2):
+        got = _decode(R, h, syn, 5000, R.relaybp_decode_batch_noalloc)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b)
+    # a different shot range through the same array right after
+    syn2 = torch.zeros((shots // 2, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 78, 0, shots // 2, syn2)
+    a = _decode(R, h, syn2, 0, R.relaybp_decode_batch)
+    b = _decode(R, h, syn2, 0, R.relaybp_decode_batch_noalloc)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    R.relaybp_destroy(h)
