@@ -57,7 +57,9 @@ enum {
 
 enum {                           /* message storage precision */
     RELAYBP_MSG_F64 = 0,         /* FP64 storage and arithmetic */
-    RELAYBP_MSG_F32 = 1          /* FP32 storage and arithmetic (the paper's proc_float = fp32) */
+    RELAYBP_MSG_F32 = 1,         /* FP32 storage and arithmetic (the paper's proc_float = fp32) */
+    RELAYBP_MSG_F16 = 2,         /* FP16 storage (saturating at +-65504), FP32 arithmetic */
+    RELAYBP_MSG_BF16 = 3         /* BF16 storage, FP32 arithmetic */
 };
 
 /* Compressed sparse rows of a binary matrix, host memory.

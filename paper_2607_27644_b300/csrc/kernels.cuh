@@ -23,6 +23,8 @@
 // which equals the leave-one-out product of signs and minimum of magnitudes.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "philox.cuh"
@@ -138,15 +140,40 @@ __device__ __forceinline__ T draw_gamma(const DecodeParamsDev &p, uint64_t shot,
     return (T)p.gamma_min + ((T)p.gamma_max - (T)p.gamma_min) * u;
 }
 
-struct SmemPlan {               // byte offsets into dynamic shared memory
+struct SmemPlan {               // byte offsets into the per-shot state block
     int M, A, cs, sgn, ehat, best, res, syn, obsacc, total;
 };
 
-// Compressed state of one check row (16 bytes for FP32).
-template <typename T> struct CheckState {
-    T m1, m2;                   // smallest / second-smallest |mu| over the row
+// Storage precision S of the per-shot state (M, A and the check minima) and
+// the arithmetic precision C it is computed in: FP64 and FP32 store what they
+// compute; FP16 and BF16 store rounded values and compute in FP32.  FP16
+// stores saturate at +-65504 (the largest finite half).
+template <typename S> struct Prec;
+template <> struct Prec<float> {
+    using C = float;
+    static __device__ __forceinline__ C ld(float v) { return v; }
+    static __device__ __forceinline__ float st(C v) { return v; }
+};
+template <> struct Prec<double> {
+    using C = double;
+    static __device__ __forceinline__ C ld(double v) { return v; }
+    static __device__ __forceinline__ double st(C v) { return v; }
+};
+template <> struct Prec<__half> {
+    using C = float;
+    static __device__ __forceinline__ C ld(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half st(C v) { return __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f)); }
+};
+template <> struct Prec<__nv_bfloat16> {
+    using C = float;
+    static __device__ __forceinline__ C ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 st(C v) { return __float2bfloat16_rn(v); }
+};
+
+// Compressed state of one check row: 16 bytes for FP32, 8 for FP16/BF16.
+template <typename S> struct alignas(sizeof(S) >= 4 ? 16 : 8) CheckState {
+    S m1, m2;                   // smallest / second-smallest |mu| over the row
     uint32_t meta;              // argmin position in the row | parity << 31
-    uint32_t pad;
 };
 
 // Column entry: check index << 12 | position of the entry within its row.
@@ -157,18 +184,19 @@ constexpr uint32_t COL_SENTINEL = 0xffffffffu;
 // owns one 16-bit word of sign bits, bit b = sign of mu at position b*L + l.
 // The sign bit of position pos of row i therefore lives in halfword
 // i*L + pos % L, bit pos / L.
-template <typename T, int L, int NB>
-__device__ __forceinline__ void row_pass(const DevDEM &g, const T *A, CheckState<T> *cs, uint16_t *sgnh,
+template <typename S, int L, int NB>
+__device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState<S> *cs, uint16_t *sgnh,
                                          const uint32_t *syn, int warp, int nwarp, int lane)
 {
     static_assert(32 % L == 0 && NB <= 16, "row geometry");
+    using C = typename Prec<S>::C;
     constexpr int P = 32 / L;
     const unsigned FULL = 0xffffffffu;
     const int r = lane / L, l = lane % L;
-    const int C = g.C;
-    for (int base = warp * P; base < C; base += nwarp * P) {
+    const int Cn = g.C;
+    for (int base = warp * P; base < Cn; base += nwarp * P) {
         const int i = base + r;
-        const bool rowok = i < C;
+        const bool rowok = i < Cn;
         int e0 = 0, deg = 0;
         if (rowok) {
             e0 = __ldg(g.rptr + i);
@@ -180,34 +208,35 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const T *A, CheckState
             const int k = b * L + l;
             idx[b] = (k < deg) ? __ldg(g.rvar + e0 + k) : -1;
         }
-        CheckState<T> o;
-        uint32_t oldbits = 0u;
+        C om1 = (C)0, om2 = (C)0;
+        uint32_t ometa = 0u, oldbits = 0u;
         if (rowok) {
-            o = cs[i];
+            const CheckState<S> o = cs[i];
+            om1 = Prec<S>::ld(o.m1);
+            om2 = Prec<S>::ld(o.m2);
+            ometa = o.meta;
             oldbits = sgnh[i * L + l];
-        } else {
-            o.m1 = (T)0; o.m2 = (T)0; o.meta = 0u; o.pad = 0u;
         }
-        const uint32_t oarg = o.meta & 0xfffu, opar = o.meta >> 31;
-        T b1 = Num<T>::inf(), b2 = Num<T>::inf();
+        const uint32_t oarg = ometa & 0xfffu, opar = ometa >> 31;
+        C b1 = Num<C>::inf(), b2 = Num<C>::inf();
         uint32_t bi = 0xfffu, newbits = 0u;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             if (idx[b] >= 0) {
                 const uint32_t k = (uint32_t)(b * L + l);
-                const T mag = (k == oarg) ? o.m2 : o.m1;
-                const T nu_old = (((oldbits >> b) & 1u) ^ opar) ? -mag : mag;
-                const T m = A[idx[b]] - nu_old;
-                newbits |= ((m < (T)0) ? 1u : 0u) << b;
-                const T a = vabs(m);
+                const C mag = (k == oarg) ? om2 : om1;
+                const C nu_old = (((oldbits >> b) & 1u) ^ opar) ? -mag : mag;
+                const C m = Prec<S>::ld(A[idx[b]]) - nu_old;
+                newbits |= ((m < (C)0) ? 1u : 0u) << b;
+                const C a = vabs(m);
                 if (a < b1) { b2 = b1; b1 = a; bi = k; }
                 else if (a < b2) { b2 = a; }
             }
         }
 #pragma unroll
         for (int off = L / 2; off > 0; off >>= 1) {
-            const T o1 = __shfl_xor_sync(FULL, b1, off);
-            const T o2 = __shfl_xor_sync(FULL, b2, off);
+            const C o1 = __shfl_xor_sync(FULL, b1, off);
+            const C o2 = __shfl_xor_sync(FULL, b2, off);
             const uint32_t oi = __shfl_xor_sync(FULL, bi, off);
             if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin(b1, o2); b1 = o1; bi = oi; }
             else { b2 = vmin(b2, o1); }
@@ -219,35 +248,41 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const T *A, CheckState
             sgnh[i * L + l] = (uint16_t)newbits;
             if (l == 0) {
                 const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
-                CheckState<T> n;
-                n.m1 = b1;
-                n.m2 = b2;
+                CheckState<S> n;
+                n.m1 = Prec<S>::st(b1);
+                n.m2 = Prec<S>::st(b2);
                 n.meta = bi | ((par ^ sb) << 31);
-                n.pad = 0u;
                 cs[i] = n;
             }
         }
     }
 }
 
-template <typename T, int L, int NB>
+// Compressed-row Relay-BP.  S: storage precision; L, NB: row geometry; GS:
+// per-shot state in a per-block region of global memory (gstate, plan.total
+// bytes per block, L2-resident) instead of shared memory, for DEMs whose state
+// does not fit on chip.
+template <typename S, int L, int NB, bool GS>
 __global__ void __launch_bounds__(512)
 relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
                     const uint32_t *__restrict__ syn_in, uint64_t shot0, int64_t shots,
                     uint32_t *__restrict__ corr_out, uint32_t *__restrict__ pobs_out,
                     StatsDev *__restrict__ stats_out, unsigned long long *__restrict__ work,
-                    T *__restrict__ gamma_scratch, double *__restrict__ trace, int trace_iters)
+                    typename Prec<S>::C *__restrict__ gamma_scratch, double *__restrict__ trace, int trace_iters,
+                    unsigned char *__restrict__ gstate)
 {
+    using C = typename Prec<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *M = reinterpret_cast<T *>(smem + plan.M);
-    T *A = reinterpret_cast<T *>(smem + plan.A);
-    CheckState<T> *cs = reinterpret_cast<CheckState<T> *>(smem + plan.cs);
-    uint16_t *sgnh = reinterpret_cast<uint16_t *>(smem + plan.sgn);
-    uint32_t *ehat = reinterpret_cast<uint32_t *>(smem + plan.ehat);
-    uint32_t *best = reinterpret_cast<uint32_t *>(smem + plan.best);
-    uint32_t *res = reinterpret_cast<uint32_t *>(smem + plan.res);
-    uint32_t *syn = reinterpret_cast<uint32_t *>(smem + plan.syn);
-    uint32_t *obsacc = reinterpret_cast<uint32_t *>(smem + plan.obsacc);
+    unsigned char *base = GS ? gstate + (size_t)blockIdx.x * (size_t)plan.total : smem;
+    S *M = reinterpret_cast<S *>(base + plan.M);
+    S *A = reinterpret_cast<S *>(base + plan.A);
+    CheckState<S> *cs = reinterpret_cast<CheckState<S> *>(base + plan.cs);
+    uint16_t *sgnh = reinterpret_cast<uint16_t *>(base + plan.sgn);
+    uint32_t *ehat = reinterpret_cast<uint32_t *>(base + plan.ehat);
+    uint32_t *best = reinterpret_cast<uint32_t *>(base + plan.best);
+    uint32_t *res = reinterpret_cast<uint32_t *>(base + plan.res);
+    uint32_t *syn = reinterpret_cast<uint32_t *>(base + plan.syn);
+    uint32_t *obsacc = reinterpret_cast<uint32_t *>(base + plan.obsacc);
 
     __shared__ long long s_shot;
     __shared__ int s_nsol, s_have_best, s_copy;
@@ -255,11 +290,11 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = blockDim.x, nwarp = nthr >> 5;
-    const int C = g.C, V = g.V;
-    const int WC = wordsof(C), WV = wordsof(V), WK = wordsof(g.K);
+    const int Cn = g.C, V = g.V;
+    const int WC = wordsof(Cn), WV = wordsof(V), WK = wordsof(g.K);
     const int NG = WV;          // variable groups of 32 (one ELL slice each)
     const unsigned FULL = 0xffffffffu;
-    T *gam = gamma_scratch + (int64_t)blockIdx.x * V;
+    C *gam = gamma_scratch + (int64_t)blockIdx.x * V;
 
     for (;;) {
         if (tid == 0) {
@@ -275,18 +310,18 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
 
         // ---- shot start: M = L0, leg-0 strengths, zero messages ------------
         for (int j = tid; j < V; j += nthr) {
-            const T l0 = Num<T>::l0(g, j);
-            const T gm = (T)p.gamma0;
-            M[j] = l0;
+            const C l0 = Num<C>::l0(g, j);
+            const C gm = (C)p.gamma0;
+            M[j] = Prec<S>::st(l0);
             gam[j] = gm;
-            A[j] = ((T)1 - gm) * l0 + gm * l0;
+            A[j] = Prec<S>::st(((C)1 - gm) * l0 + gm * l0);
         }
-        for (int i = tid; i < C; i += nthr) {
-            CheckState<T> z;
-            z.m1 = (T)0; z.m2 = (T)0; z.meta = 0u; z.pad = 0u;
+        for (int i = tid; i < Cn; i += nthr) {
+            CheckState<S> z;
+            z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u;
             cs[i] = z;
         }
-        for (int w = tid; w < C * L; w += nthr) sgnh[w] = (uint16_t)0;
+        for (int w = tid; w < Cn * L; w += nthr) sgnh[w] = (uint16_t)0;
         for (int w = tid; w < WV; w += nthr) ehat[w] = 0u;
         for (int w = tid; w < WC; w += nthr) {
             const uint32_t sv = syn_in[sidx * WC + w];
@@ -301,19 +336,24 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
             if (leg > 0) {
                 // a6: new leg -- fresh strengths, marginals carried over
                 for (int j = tid; j < V; j += nthr) {
-                    const T l0 = Num<T>::l0(g, j);
-                    const T gn = draw_gamma<T>(p, shot, leg, j, V);
-                    T carry = (T)0;
+                    const C l0 = Num<C>::l0(g, j);
+                    const C gn = draw_gamma<C>(p, shot, leg, j, V);
+                    const C Mj = Prec<S>::ld(M[j]);
+                    C carry = (C)0;
                     if (p.carry_messages) {
-                        const T go = gam[j];
-                        carry = A[j] - (((T)1 - go) * l0 + go * M[j]);
+                        const C go = gam[j];
+                        carry = Prec<S>::ld(A[j]) - (((C)1 - go) * l0 + go * Mj);
                     }
                     gam[j] = gn;
-                    A[j] = ((T)1 - gn) * l0 + gn * M[j] + carry;
+                    A[j] = Prec<S>::st(((C)1 - gn) * l0 + gn * Mj + carry);
                 }
                 if (!p.carry_messages) {
-                    for (int i = tid; i < C; i += nthr) { cs[i].m1 = (T)0; cs[i].m2 = (T)0; cs[i].meta = 0u; }
-                    for (int w = tid; w < C * L; w += nthr) sgnh[w] = (uint16_t)0;
+                    for (int i = tid; i < Cn; i += nthr) {
+                        CheckState<S> z;
+                        z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u;
+                        cs[i] = z;
+                    }
+                    for (int w = tid; w < Cn * L; w += nthr) sgnh[w] = (uint16_t)0;
                 }
                 __syncthreads();
             }
@@ -321,26 +361,26 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
             bool conv = false;
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: check rows, L lanes per row ---------------------------
-                row_pass<T, L, NB>(g, A, cs, sgnh, syn, warp, nwarp, lane);
+                row_pass<S, L, NB>(g, A, cs, sgnh, syn, warp, nwarp, lane);
                 __syncthreads();
                 // ---- a4: variables, one lane per variable, ELL slices --------
                 for (int G = warp; G < NG; G += nwarp) {
                     const int j = G * 32 + lane;
                     const bool act = j < V;
-                    const T l0 = act ? Num<T>::l0(g, j) : (T)0;
-                    const T gm = act ? gam[j] : (T)0;
+                    const C l0 = act ? Num<C>::l0(g, j) : (C)0;
+                    const C gm = act ? gam[j] : (C)0;
                     const int D = __ldg(g.gdeg + G);
                     const uint32_t *col = g.cinfo + __ldg(g.goff + G) + lane;
-                    T S = (T)0;
+                    C Ssum = (C)0;
                     // column messages nu_ij rebuilt from the check states; four
                     // independent slots per step, the remainder one by one (D is
                     // uniform over the warp, so the split does not diverge)
-                    auto msg = [&](uint32_t c) -> T {
+                    auto msg = [&](uint32_t c) -> C {
                         const uint32_t i = c >> 12;
-                        const CheckState<T> q = cs[i];
+                        const CheckState<S> q = cs[i];
                         const uint32_t pos = c & 0xfffu;
                         const uint32_t hw = sgnh[i * L + (pos % L)];
-                        const T mag = (pos == (q.meta & 0xfffu)) ? q.m2 : q.m1;
+                        const C mag = Prec<S>::ld((pos == (q.meta & 0xfffu)) ? q.m2 : q.m1);
                         const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
                         return sb ? -mag : mag;
                     };
@@ -351,18 +391,18 @@ relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
                         for (int u = 0; u < 4; ++u) c[u] = __ldg(col + (k + u) * 32);
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (c[u] != COL_SENTINEL) S += msg(c[u]);
+                            if (c[u] != COL_SENTINEL) Ssum += msg(c[u]);
                     }
                     for (; k < D; ++k) {
                         const uint32_t c = __ldg(col + k * 32);
-                        if (c != COL_SENTINEL) S += msg(c);
+                        if (c != COL_SENTINEL) Ssum += msg(c);
                     }
                     uint32_t dec = 0u;
                     if (act) {
-                        const T Mn = ((T)1 - gm) * l0 + gm * M[j] + S;
-                        M[j] = Mn;
-                        A[j] = ((T)1 - gm) * l0 + gm * Mn + S;
-                        dec = (Mn < (T)0) ? 1u : 0u;
+                        const C Mn = ((C)1 - gm) * l0 + gm * Prec<S>::ld(M[j]) + Ssum;
+                        M[j] = Prec<S>::st(Mn);
+                        A[j] = Prec<S>::st(((C)1 - gm) * l0 + gm * Mn + Ssum);
+                        dec = (Mn < (C)0) ? 1u : 0u;
                         if (trace && iters < trace_iters)
                             trace[((int64_t)sidx * trace_iters + iters) * V + j] = (double)Mn;
                     }

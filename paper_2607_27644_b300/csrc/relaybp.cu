@@ -65,6 +65,9 @@ struct relaybp_handle {
     int64_t stage_shots = 0;
     int64_t launches = 0;
     int max_row_deg = 0;
+    // per-block decoder state in global memory, for DEMs too large for shared memory
+    unsigned char *d_gstate = nullptr;
+    size_t gstate_bytes = 0;
 };
 
 namespace {
@@ -108,7 +111,8 @@ int check_params(const relaybp_params *p)
     if (!std::isfinite(p->gamma0) || !std::isfinite(p->gamma_min) || !std::isfinite(p->gamma_max) ||
         p->gamma_min > p->gamma_max)
         return fail(RELAYBP_ERR_INVALID, "memory strengths must be finite with gamma_min <= gamma_max");
-    if (p->msg_dtype != RELAYBP_MSG_F64 && p->msg_dtype != RELAYBP_MSG_F32)
+    if (p->msg_dtype != RELAYBP_MSG_F64 && p->msg_dtype != RELAYBP_MSG_F32 && p->msg_dtype != RELAYBP_MSG_F16 &&
+        p->msg_dtype != RELAYBP_MSG_BF16)
         return fail(RELAYBP_ERR_UNSUPPORTED, "msg_dtype %d not supported", p->msg_dtype);
     if (p->reserved != 0) return fail(RELAYBP_ERR_INVALID, "reserved field must be 0");
     return 0;
@@ -132,7 +136,7 @@ RowGeom row_geom(int maxdeg)
     return {0, 0};
 }
 
-SmemPlan make_plan(const DevDEM &g, size_t esz, int L)
+SmemPlan make_plan(const DevDEM &g, size_t esz, size_t csz, int L)
 {
     SmemPlan s{};
     size_t off = 0;
@@ -144,7 +148,7 @@ SmemPlan make_plan(const DevDEM &g, size_t esz, int L)
     };
     s.M = take(esz * g.V);
     s.A = take(esz * g.V);
-    s.cs = take((esz == 8 ? sizeof(CheckState<double>) : sizeof(CheckState<float>)) * (size_t)g.C);
+    s.cs = take(csz * (size_t)g.C);
     s.sgn = take(2 * (size_t)g.C * (size_t)L);      // row_pass: one 16-bit sign word per (row, lane)
     s.ehat = take(4 * (size_t)words(g.V));
     s.best = take(4 * (size_t)words(g.V));
@@ -228,44 +232,62 @@ int launch_decode_exact(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0
     return 0;
 }
 
-template <typename T, int L, int NB>
+template <typename S, int L, int NB>
 int launch_decode_geom(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
                        uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace, int trace_iters)
 {
+    using C = typename Prec<S>::C;
     const DevDEM &g = h->dem;
-    SmemPlan plan = make_plan(g, sizeof(T), L);
+    SmemPlan plan = make_plan(g, sizeof(S), sizeof(CheckState<S>), L);
     int maxsm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (plan.total + 64 > maxsm)
-        return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes)",
-                    plan.total, maxsm);
-    auto kern = relay_decode_kernel<T, L, NB>;
-    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+    // shared-memory state when one shot's state fits, else a per-block region
+    // of global memory (one block per SM keeps the regions L2-resident)
+    const bool gs = plan.total + 1024 > maxsm;
     const int threads = block_threads(g);
-    int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan.total));
-    if (per_sm < 1) return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan.total);
-    int64_t blocks = (int64_t)per_sm * h->num_sms;
-    if (blocks > shots) blocks = shots;
+    int64_t blocks = 0, resident = 0;
+    if (!gs) {
+        auto kern = relay_decode_kernel<S, L, NB, false>;
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+        int per_sm = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan.total));
+        if (per_sm < 1)
+            return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan.total);
+        resident = (int64_t)per_sm * h->num_sms;
+    } else {
+        resident = h->num_sms;
+    }
+    blocks = std::min<int64_t>(resident, shots);
     if (blocks < 1) blocks = 1;
     // scratch: the leg's memory strengths, one row of V per block
-    if (h->gamma_blocks < blocks || h->gamma_elem != sizeof(T)) {
+    if (h->gamma_blocks < blocks || h->gamma_elem != sizeof(C)) {
         if (h->d_gamma) { cudaFree(h->d_gamma); h->d_gamma = nullptr; }
-        int64_t want = (int64_t)per_sm * h->num_sms;
-        CUDA_TRY(cudaMalloc(&h->d_gamma, (size_t)want * g.V * sizeof(T) + 16));
-        h->gamma_blocks = want;
-        h->gamma_elem = sizeof(T);
+        h->gamma_blocks = 0;
+        CUDA_TRY(cudaMalloc(&h->d_gamma, (size_t)resident * g.V * sizeof(C) + 16));
+        h->gamma_blocks = resident;
+        h->gamma_elem = sizeof(C);
+    }
+    if (gs && h->gstate_bytes < (size_t)blocks * plan.total) {
+        if (h->d_gstate) { cudaFree(h->d_gstate); h->d_gstate = nullptr; }
+        h->gstate_bytes = 0;
+        CUDA_TRY(cudaMalloc(&h->d_gstate, (size_t)resident * plan.total));
+        h->gstate_bytes = (size_t)resident * plan.total;
     }
     CUDA_TRY(cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st));
-    kern<<<(unsigned)blocks, threads, plan.total, st>>>(g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr,
-                                                       d_pobs, d_stats, h->d_work, static_cast<T *>(h->d_gamma),
-                                                       d_trace, trace_iters);
+    if (!gs)
+        relay_decode_kernel<S, L, NB, false><<<(unsigned)blocks, threads, plan.total, st>>>(
+            g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, h->d_work,
+            static_cast<C *>(h->d_gamma), d_trace, trace_iters, nullptr);
+    else
+        relay_decode_kernel<S, L, NB, true><<<(unsigned)blocks, threads, 0, st>>>(
+            g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, h->d_work,
+            static_cast<C *>(h->d_gamma), d_trace, trace_iters, h->d_gstate);
     CUDA_TRY(cudaGetLastError());
     h->launches += 1;
     return 0;
 }
 
-template <typename T>
+template <typename S>
 int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
                   uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace = nullptr,
                   int trace_iters = 0)
@@ -273,7 +295,7 @@ int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int6
     const RowGeom rg = row_geom(h->max_row_deg);
 #define RELAYBP_GEOM(LL, NN)                                                                                   \
     if (rg.L == LL && rg.NB == NN)                                                                            \
-        return launch_decode_geom<T, LL, NN>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace,    \
+        return launch_decode_geom<S, LL, NN>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace,    \
                                              trace_iters);
     RELAYBP_GEOM(4, 4)
     RELAYBP_GEOM(8, 4)
@@ -285,6 +307,23 @@ int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int6
 #undef RELAYBP_GEOM
     return fail(RELAYBP_ERR_UNSUPPORTED, "a detector touches %d faults; the decode kernel handles at most 512",
                 h->max_row_deg);
+}
+
+// Storage-precision dispatch of the compressed kernels.
+int launch_decode_dtype(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
+                        uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace, int trace_iters)
+{
+    switch (h->params.msg_dtype) {
+    case RELAYBP_MSG_F64:
+        return launch_decode<double>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace, trace_iters);
+    case RELAYBP_MSG_F16:
+        return launch_decode<__half>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace, trace_iters);
+    case RELAYBP_MSG_BF16:
+        return launch_decode<__nv_bfloat16>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace,
+                                            trace_iters);
+    default:
+        return launch_decode<float>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace, trace_iters);
+    }
 }
 
 }  // namespace
@@ -468,9 +507,8 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     if (h->params.msg_dtype == RELAYBP_MSG_F64) {
         int rc = launch_decode_exact(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st, nullptr, 0);
         if (rc <= 0) return rc;
-        return launch_decode<double>(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
     }
-    return launch_decode<float>(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+    return launch_decode_dtype(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st, nullptr, 0);
 }
 
 int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
@@ -486,9 +524,8 @@ int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     if (h->params.msg_dtype == RELAYBP_MSG_F64) {
         int rc = launch_decode_exact(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
         if (rc <= 0) return rc;
-        return launch_decode<double>(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
     }
-    return launch_decode<float>(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
+    return launch_decode_dtype(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
 }
 
 int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
@@ -574,6 +611,7 @@ int relaybp_destroy(relaybp_handle *h)
     for (void *p : h->allocs) cudaFree(p);
     cudaFree(h->d_work);
     cudaFree(h->d_gamma);
+    cudaFree(h->d_gstate);
     cudaFree(h->d_stage_syn);
     cudaFree(h->d_stage_pobs);
     cudaFree(h->d_stage_stats);
@@ -629,14 +667,15 @@ template <typename T, int L, int NB>
 int noalloc_decode_geom(relaybp_handle *h, unsigned char *scratch, const uint32_t *d_syn, uint64_t shot0,
                         int64_t shots, uint32_t *d_corr, uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st)
 {
+    using Cm = typename Prec<T>::C;
     const DevDEM &g = h->dem;
-    SmemPlan plan = make_plan(g, sizeof(T), L);
+    SmemPlan plan = make_plan(g, sizeof(T), sizeof(CheckState<T>), L);
     int maxsm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (plan.total + 64 > maxsm)
-        return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes)",
-                    plan.total, maxsm);
-    auto kern = relay_decode_kernel<T, L, NB>;
+    if (plan.total + 1024 > maxsm)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes); "
+                    "the allocation-free entry point keeps it on chip only: use relaybp_decode_batch", plan.total, maxsm);
+    auto kern = relay_decode_kernel<T, L, NB, false>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
     const int threads = block_threads(g);
     int per_sm = 0;
@@ -645,7 +684,7 @@ int noalloc_decode_geom(relaybp_handle *h, unsigned char *scratch, const uint32_
     int64_t blocks = (int64_t)per_sm * h->num_sms;
     if (blocks > shots) blocks = shots;
     // every block needs one row of V memory strengths after the counter
-    const size_t row = (size_t)g.V * sizeof(T);
+    const size_t row = (size_t)g.V * sizeof(Cm);
     const size_t need = kNoAllocCounterBytes + (size_t)blocks * row;
     if (need > kNoAllocScratchBytes)
         return fail(RELAYBP_ERR_UNSUPPORTED,
@@ -653,10 +692,10 @@ int noalloc_decode_geom(relaybp_handle *h, unsigned char *scratch, const uint32_
                     "allocation-free entry point has %zu bytes: use relaybp_decode_batch",
                     need, (long long)blocks, row, kNoAllocScratchBytes);
     unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
-    T *gam = reinterpret_cast<T *>(scratch + kNoAllocCounterBytes);
+    Cm *gam = reinterpret_cast<Cm *>(scratch + kNoAllocCounterBytes);
     CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));     // the counter must start at 0
     kern<<<(unsigned)blocks, threads, plan.total, st>>>(g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr,
-                                                       d_pobs, d_stats, work, gam, nullptr, 0);
+                                                       d_pobs, d_stats, work, gam, nullptr, 0, nullptr);
     CUDA_TRY(cudaGetLastError());
     h->launches += 1;
     return 0;
@@ -722,10 +761,18 @@ extern "C" int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d
     if (int rc = noalloc_scratch(h->device, &scratch)) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
-    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
+    switch (h->params.msg_dtype) {
+    case RELAYBP_MSG_F64: {
         int rc = noalloc_decode_exact(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
         if (rc <= 0) return rc;
         return noalloc_decode<double>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
     }
-    return noalloc_decode<float>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+    case RELAYBP_MSG_F16:
+        return noalloc_decode<__half>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+    case RELAYBP_MSG_BF16:
+        return noalloc_decode<__nv_bfloat16>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds,
+                                             st);
+    default:
+        return noalloc_decode<float>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
+    }
 }

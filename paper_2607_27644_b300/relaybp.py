@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(_HERE, "librelaybp.so")
 
 RELAYBP_MSG_F64 = 0
 RELAYBP_MSG_F32 = 1
-_DTYPES = {"f64": RELAYBP_MSG_F64, "f32": RELAYBP_MSG_F32}
+RELAYBP_MSG_F16 = 2
+RELAYBP_MSG_BF16 = 3
+_DTYPES = {"f64": RELAYBP_MSG_F64, "f32": RELAYBP_MSG_F32, "f16": RELAYBP_MSG_F16, "bf16": RELAYBP_MSG_BF16}
 
 
 class relaybp_csr(ctypes.Structure):

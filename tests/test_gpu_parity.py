@@ -184,6 +184,53 @@ def test_decode_circuit_level_fp32(circ160):
     assert np.all(rg["stats"][:, 1] <= 5)
 
 
+# Storage precision: FP16 keeps 11 significant bits (unit roundoff 4.9e-4),
+# BF16 8 (3.9e-3); arithmetic stays FP32.  The first two iterations' posteriors
+# stay within a few roundings of the FP64 oracle; after that the comparison is
+# the decoder's answer, validity and LER, as for FP32.
+@pytest.mark.parametrize("dtype,tol", [("f16", 1e-2), ("bf16", 5e-2)])
+def test_low_precision_storage_circuit_level(circ160, dtype, tol):
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype=dtype, **CIRC_KW)
+    h = _handle(circ160, pg)
+    syn, obs, _ = oracle.sample(circ160, 9, 20_000, 400)
+    W = 2
+    ro = oracle.decode(circ160, po, syn, shot0=20_000, trace_iters=W)
+    rg = gpu_decode(h, syn, shot0=20_000, trace_iters=W)
+    for s_ in range(0, 400, 40):
+        n = min(W, int(ro["stats"][s_, 3]))
+        worst, _ = _posterior_parity(ro["trace"][s_], rg["trace"][s_], n, circ160.n_loc, tol)
+        assert worst <= tol, (s_, worst)
+    _logical_parity(circ160, ro, rg, syn, obs)
+
+
+@pytest.fixture(scope="module")
+def circ320():
+    return circuit_dem("ZSZ-LP-320", 0.001, 14, "Z")
+
+
+def test_global_state_path_320(circ320):
+    """ZSZ-LP-320 (DEM 1920 x 28,992, E = 169,376) in FP32 does not fit one
+    shot's state in shared memory, so the kernel keeps it in a per-block
+    region of global memory; FP16 storage fits on chip.  Both against the
+    oracle."""
+    from gpu_util import gpu_decode, params_pair
+    kw = dict(CIRC_KW, gamma_min=-0.16, gamma_max=0.66, num_sets=200)   # Table 9 interval of ZSZ-LP-320
+    syn, obs, _ = oracle.sample(circ320, 4, 0, 48)
+    po, _ = params_pair(msg_dtype="f32", **kw)
+    ro = oracle.decode(circ320, po, syn, trace_iters=4)
+    for dtype in ("f32", "f16"):
+        _, pg = params_pair(msg_dtype=dtype, **kw)
+        h = _handle(circ320, pg)
+        rg = gpu_decode(h, syn, trace_iters=4)
+        if dtype == "f32":
+            for s_ in range(48):
+                n = min(4, int(ro["stats"][s_, 3]))
+                worst, _ = _posterior_parity(ro["trace"][s_], rg["trace"][s_], n, circ320.n_loc, 1e-4)
+                assert worst <= 1e-4
+        _logical_parity(circ320, ro, rg, syn, obs)
+
+
 def test_full_size_sampled_outputs(circ160):
     """10^6 shots sampled and decoded on the GPU in the benchmark's launch
     configuration; 24 shots spread over the batch are recomputed by the oracle

@@ -170,19 +170,9 @@ def test_dem_noiseless_limit_and_scaling():
     assert np.all((r > 1.9) & (r <= 2.0 + 1e-12))
 
 
-@pytest.mark.parametrize("row", _table("dem_sizes.txt")[:1], ids=lambda r: r[0])
+@pytest.mark.parametrize("row", _table("dem_sizes.txt"), ids=lambda r: r[0])
 def test_dem_sizes_table5(row):
-    """(N_det, N_loc) of Table 5 (ZSZ-LP-320; 390 and 550 run in the slow set)."""
-    name, rounds, ndet, nloc = row[0], *map(int, row[1:])
-    D = circuit_dem(name, 0.001, rounds, "Z")
-    assert (D.n_det, D.n_loc) == (ndet, nloc)
-
-
-@pytest.mark.slow
-@pytest.mark.parametrize("row", _table("dem_sizes.txt")[1:], ids=lambda r: r[0])
-def test_dem_sizes_table5_large(row):
-    if not os.environ.get("RUN_SLOW"):
-        pytest.skip("set RUN_SLOW=1 for the 390/550 DEM builds")
+    """(N_det, N_loc) of Table 5: 1920/28992, 2652/40326, 4180/63910."""
     name, rounds, ndet, nloc = row[0], *map(int, row[1:])
     D = circuit_dem(name, 0.001, rounds, "Z")
     assert (D.n_det, D.n_loc) == (ndet, nloc)

@@ -289,19 +289,43 @@ def _csr_from_cols(cols: list[tuple], nrows: int) -> tuple[np.ndarray, np.ndarra
     return indptr.astype(np.int32), cc.astype(np.int32)
 
 
+def _set_bits_by_fault(R: np.ndarray, nloc: int) -> tuple[np.ndarray, np.ndarray]:
+    """(fault, row) pairs of the set bits of a [rows, words] bit matrix whose bit
+    f of a row means fault f flips it, sorted by fault then row."""
+    rows, wi = np.nonzero(R)
+    if rows.size == 0:
+        return np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64)
+    bits = np.unpackbits(np.ascontiguousarray(R[rows, wi]).view(np.uint8).reshape(-1, 8), axis=1,
+                         bitorder="little")
+    k, b = np.nonzero(bits)
+    fault = wi[k].astype(np.int64) * 64 + b
+    row = rows[k].astype(np.int64)
+    keep = fault < nloc
+    fault, row = fault[keep], row[keep]
+    order = np.lexsort((row, fault))
+    return fault[order], row[order]
+
+
 def circuit_dem(code_name: str, p: float, rounds: int | None = None, basis: str = "Z",
                 chunk: int = 1 << 17) -> DEM:
-    """Circuit-level DEM of a d-round memory experiment (Sec. 6.1, App. E)."""
+    """Circuit-level DEM of a d-round memory experiment (Sec. 6.1, App. E).
+
+    Columns appear in the order of the first fault component that produces
+    them; merged probabilities accumulate in that order.
+    """
     code = load_code(code_name)
     rounds = code.d if rounds is None else rounds
     circ, info = memory_circuit(code, rounds, basis)
     nf = _count_faults(circ)
     det_rows, obs_rows = info["detectors"], info["observables"]
     n_det, n_obs = len(det_rows), len(obs_rows)
-    groups: dict[tuple, int] = {}
-    col_dets: list[tuple] = []
-    col_obs: list[tuple] = []
-    col_p: list[float] = []
+    # two independent 64-bit random keys per detector / observable: a fault's
+    # 128-bit signature is the XOR of its keys (set identity with collision
+    # probability ~ n^2 / 2^128)
+    rng = np.random.default_rng(0x5EED_DE11)
+    kd = rng.integers(0, 2 ** 63, size=(2, n_det), dtype=np.int64).astype(np.uint64) * np.uint64(2) + np.uint64(1)
+    ko = rng.integers(0, 2 ** 63, size=(2, max(1, n_obs)), dtype=np.int64).astype(np.uint64) * np.uint64(2)
+    sig_all, first_dets, first_obs, probs_all = [], [], [], []
     for f0 in range(0, nf, chunk):
         f1 = min(nf, f0 + chunk)
         rec, probs = _frame_sim(circ, p, f0, f1)
@@ -312,33 +336,53 @@ def circuit_dem(code_name: str, p: float, rounds: int | None = None, basis: str 
         for i, rows in enumerate(obs_rows):
             O[i] = np.bitwise_xor.reduce(rec[rows], axis=0)
         nloc = f1 - f0
-        Db = np.unpackbits(D.view(np.uint8), axis=1, bitorder="little")[:, :nloc]
-        Ob = np.unpackbits(O.view(np.uint8), axis=1, bitorder="little")[:, :nloc]
-        fd, dd = np.nonzero(Db.T)
-        fo, oo = np.nonzero(Ob.T)
+        fd, dd = _set_bits_by_fault(D, nloc)
+        fo, oo = _set_bits_by_fault(O, nloc)
+        sig = np.zeros((nloc, 2), dtype=np.uint64)
+        for t in range(2):
+            np.bitwise_xor.at(sig[:, t], fd, kd[t][dd])
+            if n_obs:
+                np.bitwise_xor.at(sig[:, t], fo, ko[t][oo])
+        hit = np.zeros(nloc, dtype=bool)
+        hit[fd] = True
+        hit[fo] = True
+        nz = np.nonzero(hit)[0]
         dstart = np.searchsorted(fd, np.arange(nloc + 1))
         ostart = np.searchsorted(fo, np.arange(nloc + 1))
-        for f in range(nloc):
-            ds = tuple(dd[dstart[f]:dstart[f + 1]].tolist())
-            os_ = tuple(oo[ostart[f]:ostart[f + 1]].tolist())
-            if not ds and not os_:
-                continue
-            key = (ds, os_)
-            pf = float(probs[f])
-            j = groups.get(key)
-            if j is None:
-                groups[key] = len(col_p)
-                col_dets.append(ds)
-                col_obs.append(os_)
-                col_p.append(pf)
-            else:
-                q = col_p[j]
-                col_p[j] = q + pf - 2.0 * q * pf
+        sig_all.append(sig[nz])
+        probs_all.append(probs[nz])
+        first_dets.append([(dd[dstart[f]:dstart[f + 1]], oo[ostart[f]:ostart[f + 1]]) for f in nz])
+    sig = np.concatenate(sig_all)
+    probs = np.concatenate(probs_all)
+    sets = [x for chunk_sets in first_dets for x in chunk_sets]
+    _, first, inv = np.unique(sig, axis=0, return_index=True, return_inverse=True)
+    inv = inv.reshape(-1)
+    order = np.argsort(first, kind="stable")          # groups by first occurrence
+    rank = np.empty_like(order)
+    rank[order] = np.arange(order.size)
+    col = rank[inv]
+    ncol = order.size
+    col_p = np.zeros(ncol, dtype=np.float64)
+    seen = np.zeros(ncol, dtype=bool)
+    for f in range(col.size):                         # p <- p1 + p2 - 2 p1 p2, in fault order
+        j = col[f]
+        if seen[j]:
+            q = col_p[j]
+            col_p[j] = q + probs[f] - 2.0 * q * probs[f]
+        else:
+            col_p[j] = probs[f]
+            seen[j] = True
+    reps = first[order]
+    col_dets = [tuple(sets[r][0].tolist()) for r in reps]
+    col_obs = [tuple(sets[r][1].tolist()) for r in reps]
+    for f in range(0, col.size, max(1, col.size // 2000)):   # spot-check set identity within groups
+        r = reps[col[f]]
+        if not (np.array_equal(sets[f][0], sets[r][0]) and np.array_equal(sets[f][1], sets[r][1])):
+            raise RuntimeError("signature collision while merging fault mechanisms")
     Hp, Hi = _csr_from_cols(col_dets, n_det)
     Op, Oi = _csr_from_cols(col_obs, n_obs)
-    return DEM(f"{code_name}/circuit/d{rounds}/{basis}/p{p:g}", n_det, len(col_p), n_obs,
-               Hp, Hi, Op, Oi, np.asarray(col_p, dtype=np.float64),
-               dict(code=code_name, rounds=rounds, basis=basis, p=p, n_fault_components=nf))
+    return DEM(f"{code_name}/circuit/d{rounds}/{basis}/p{p:g}", n_det, ncol, n_obs,
+               Hp, Hi, Op, Oi, col_p, dict(code=code_name, rounds=rounds, basis=basis, p=p, n_fault_components=nf))
 
 
 def code_capacity_dem(code_name: str, p: float) -> DEM:
