@@ -96,6 +96,7 @@ typedef struct {
 } relaybp_shot_stats;
 
 typedef struct relaybp_handle relaybp_handle;
+typedef struct relaybp_group relaybp_group;
 
 /* Build a decoder for one DEM on the current CUDA device.
  * H: detector x fault check matrix (C rows, V columns); every row has 0 or at
@@ -164,10 +165,11 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
  * - All calls on a device share the one array: calls whose kernels overlap on
  *   the GPU (other streams, other handles, other host threads) race and give
  *   wrong results.  Serialise them, e.g. by issuing them on one stream.
- * - A DEM whose scratch (256 bytes + one row of V message-precision values per
- *   resident thread block) exceeds 16 MiB is rejected with
- *   RELAYBP_ERR_UNSUPPORTED and a message giving both sizes; use
- *   relaybp_decode_batch for it.  (The ZSZ-LP-160 circuit DEM needs 12.3 MB.) */
+ * - A launch whose scratch (256 bytes + one row of V memory strengths, FP32
+ *   or FP64, per thread block) exceeds 16 MiB, or a DEM whose per-shot state
+ *   does not fit in shared memory, is rejected with RELAYBP_ERR_UNSUPPORTED
+ *   and a message giving the sizes; use relaybp_decode_batch for it.  (The
+ *   ZSZ-LP-160 circuit DEM in FP32 needs 12.3 MB.) */
 int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
                                  uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
                                  void *cuda_stream);
@@ -194,6 +196,29 @@ int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t
 int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const uint32_t *d_true_obs,
                            const relaybp_shot_stats *d_stats, int64_t shots, unsigned long long *d_counters,
                            void *cuda_stream);
+
+/* Batched decoding of several DEMs in one persistent launch (no counterpart
+ * in the paper, which decodes one shot at a time; its App. F notes that
+ * batched decoding is bound by device memory capacity and bandwidth).
+ *
+ * relaybp_group_create: a group of 1..16 handles built on one device with one
+ * message precision (their other parameters may differ: each DEM decodes with
+ * its own).  The group owns its own scratch; the handles must outlive it.
+ * relaybp_group_decode: decode, in ONE kernel launch, shots[d] syndromes of
+ * DEM d from d_syndromes[d] (global shot indices shot0[d]...) for every d,
+ * writing d_corrections[d], d_pred_obs[d], d_stats[d] (each array, or any of
+ * its entries, may be NULL).  Every thread block takes the next shot of any
+ * DEM from one work counter, so uneven shot counts and shots that finish
+ * early leave no SM idle until the whole batch is done.  Results equal those
+ * of relaybp_decode_batch on each DEM alone (except for FP64 DEMs small enough
+ * for its literal-order kernel, which a group decodes with the compressed
+ * FP64 kernel).  Asynchronous on the stream; one group per stream. */
+int relaybp_group_create(relaybp_handle *const *handles, int32_t n, relaybp_group **out);
+int relaybp_group_decode(relaybp_group *grp, const uint32_t *const *d_syndromes, const uint64_t *shot0,
+                         const int64_t *shots, uint32_t *const *d_corrections, uint32_t *const *d_pred_obs,
+                         relaybp_shot_stats *const *d_stats, void *cuda_stream);
+int64_t relaybp_group_launch_count(const relaybp_group *grp);
+int relaybp_group_destroy(relaybp_group *grp);
 
 /* Number of kernel launches this handle has issued since it was built. */
 int64_t relaybp_launch_count(const relaybp_handle *h);

@@ -258,55 +258,94 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
     }
 }
 
-// Compressed-row Relay-BP.  S: storage precision; L, NB: row geometry; GS:
-// per-shot state in a per-block region of global memory (gstate, plan.total
-// bytes per block, L2-resident) instead of shared memory, for DEMs whose state
-// does not fit on chip.
+// One DEM of a launch: its structure, decoder parameters, shared-state plan
+// and the batch of shots to decode with its outputs.
+struct DecodeJob {
+    DevDEM g;
+    DecodeParamsDev p;
+    SmemPlan plan;
+    const uint32_t *syn_in;     // [shots][ceil(C/32)]
+    uint64_t shot0;             // global index of the first shot (keys the draws)
+    int64_t shots;
+    uint32_t *corr_out, *pobs_out;
+    StatsDev *stats_out;
+    double *trace;
+    int trace_iters;
+};
+
+constexpr int kMaxJobs = 16;
+// Jobs of one launch; start[d] = first work index of job d (prefix sums of
+// the shot counts), start[n] = total.
+struct JobTable {
+    DecodeJob job[kMaxJobs];
+    int64_t start[kMaxJobs + 1];
+    int n;
+};
+
+// Compressed-row Relay-BP over a table of jobs (one DEM each) in one
+// persistent launch: every block takes the next work index from one device
+// counter, finds its job and decodes that shot with the job's DEM, so shots of
+// all DEMs share the SMs and a block whose shot ends early moves on at once.
+// S: storage precision; L, NB: row geometry (for the longest row of any job);
+// GS: per-shot state in a per-block region of global memory (gstate,
+// state_stride bytes per block, L2-resident) instead of shared memory.
 template <typename S, int L, int NB, bool GS>
 __global__ void __launch_bounds__(512)
-relay_decode_kernel(DevDEM g, DecodeParamsDev p, SmemPlan plan,
-                    const uint32_t *__restrict__ syn_in, uint64_t shot0, int64_t shots,
-                    uint32_t *__restrict__ corr_out, uint32_t *__restrict__ pobs_out,
-                    StatsDev *__restrict__ stats_out, unsigned long long *__restrict__ work,
-                    typename Prec<S>::C *__restrict__ gamma_scratch, double *__restrict__ trace, int trace_iters,
-                    unsigned char *__restrict__ gstate)
+relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__restrict__ work,
+                    typename Prec<S>::C *__restrict__ gamma_scratch, int vmax,
+                    unsigned char *__restrict__ gstate, size_t state_stride)
 {
     using C = typename Prec<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned char *base = GS ? gstate + (size_t)blockIdx.x * (size_t)plan.total : smem;
-    S *M = reinterpret_cast<S *>(base + plan.M);
-    S *A = reinterpret_cast<S *>(base + plan.A);
-    CheckState<S> *cs = reinterpret_cast<CheckState<S> *>(base + plan.cs);
-    uint16_t *sgnh = reinterpret_cast<uint16_t *>(base + plan.sgn);
-    uint32_t *ehat = reinterpret_cast<uint32_t *>(base + plan.ehat);
-    uint32_t *best = reinterpret_cast<uint32_t *>(base + plan.best);
-    uint32_t *res = reinterpret_cast<uint32_t *>(base + plan.res);
-    uint32_t *syn = reinterpret_cast<uint32_t *>(base + plan.syn);
-    uint32_t *obsacc = reinterpret_cast<uint32_t *>(base + plan.obsacc);
+    unsigned char *base = GS ? gstate + (size_t)blockIdx.x * state_stride : smem;
 
     __shared__ long long s_shot;
-    __shared__ int s_nsol, s_have_best, s_copy;
+    __shared__ int s_job, s_nsol, s_have_best, s_copy;
     __shared__ double s_best_w, s_w;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = blockDim.x, nwarp = nthr >> 5;
-    const int Cn = g.C, V = g.V;
-    const int WC = wordsof(Cn), WV = wordsof(V), WK = wordsof(g.K);
-    const int NG = WV;          // variable groups of 32 (one ELL slice each)
     const unsigned FULL = 0xffffffffu;
-    C *gam = gamma_scratch + (int64_t)blockIdx.x * V;
+    C *gam = gamma_scratch + (int64_t)blockIdx.x * vmax;
+    const int64_t total = tab.start[tab.n];
 
     for (;;) {
         if (tid == 0) {
-            s_shot = (long long)atomicAdd(work, 1ull);
+            const long long q = (long long)atomicAdd(work, 1ull);
+            int d = 0;
+            while (d + 1 < tab.n && q >= tab.start[d + 1]) ++d;
+            s_job = d;
+            s_shot = q;
             s_nsol = 0;
             s_have_best = 0;
             s_best_w = 0.0;
         }
         __syncthreads();
-        const long long sidx = s_shot;
-        if (sidx >= shots) break;
-        const uint64_t shot = shot0 + (uint64_t)sidx;
+        if (s_shot >= total) break;
+        const DecodeJob &J = tab.job[s_job];
+        const DevDEM &g = J.g;
+        const DecodeParamsDev &p = J.p;
+        const SmemPlan &plan = J.plan;
+        const long long sidx = s_shot - tab.start[s_job];
+        const uint64_t shot = J.shot0 + (uint64_t)sidx;
+        const uint32_t *syn_in = J.syn_in;
+        uint32_t *corr_out = J.corr_out;
+        uint32_t *pobs_out = J.pobs_out;
+        StatsDev *stats_out = J.stats_out;
+        double *trace = J.trace;
+        const int trace_iters = J.trace_iters;
+        S *M = reinterpret_cast<S *>(base + plan.M);
+        S *A = reinterpret_cast<S *>(base + plan.A);
+        CheckState<S> *cs = reinterpret_cast<CheckState<S> *>(base + plan.cs);
+        uint16_t *sgnh = reinterpret_cast<uint16_t *>(base + plan.sgn);
+        uint32_t *ehat = reinterpret_cast<uint32_t *>(base + plan.ehat);
+        uint32_t *best = reinterpret_cast<uint32_t *>(base + plan.best);
+        uint32_t *res = reinterpret_cast<uint32_t *>(base + plan.res);
+        uint32_t *syn = reinterpret_cast<uint32_t *>(base + plan.syn);
+        uint32_t *obsacc = reinterpret_cast<uint32_t *>(base + plan.obsacc);
+        const int Cn = g.C, V = g.V;
+        const int WC = wordsof(Cn), WV = wordsof(V), WK = wordsof(g.K);
+        const int NG = WV;      // variable groups of 32 (one ELL slice each)
 
         // ---- shot start: M = L0, leg-0 strengths, zero messages ------------
         for (int j = tid; j < V; j += nthr) {

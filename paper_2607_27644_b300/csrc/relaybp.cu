@@ -48,26 +48,38 @@ int words(int64_t bits) { return (int)((bits + 31) / 32); }
 
 }  // namespace
 
+// Device scratch of a launch owner (a handle or a group): the persistent
+// kernel's work counter, one row of memory strengths per resident block and,
+// for DEMs too large for shared memory, one state region per resident block.
+struct Scratch {
+    unsigned long long *work = nullptr;
+    void *gamma = nullptr;
+    size_t gamma_bytes = 0;
+    unsigned char *gstate = nullptr;
+    size_t gstate_bytes = 0;
+    bool fixed = false;             // true: never (re)allocate (allocation-free entry point)
+};
+
 struct relaybp_handle {
     int device = 0;
     int num_sms = 0;
     relaybp_params params{};
     DevDEM dem{};
     std::vector<void *> allocs;
-    // scratch
-    unsigned long long *d_work = nullptr;
-    void *d_gamma = nullptr;         // [blocks][V] of the message type
-    int64_t gamma_blocks = 0;
-    size_t gamma_elem = 0;
+    Scratch scratch;
     // host-buffer staging (relaybp_decode_host)
     uint32_t *d_stage_syn = nullptr, *d_stage_pobs = nullptr;
     StatsDev *d_stage_stats = nullptr;
     int64_t stage_shots = 0;
     int64_t launches = 0;
     int max_row_deg = 0;
-    // per-block decoder state in global memory, for DEMs too large for shared memory
-    unsigned char *d_gstate = nullptr;
-    size_t gstate_bytes = 0;
+};
+
+struct relaybp_group {
+    int device = 0;
+    std::vector<relaybp_handle *> handles;
+    Scratch scratch;
+    int64_t launches = 0;
 };
 
 namespace {
@@ -206,11 +218,57 @@ int block_threads(const DevDEM &g)
     return 512;
 }
 
+int scratch_reserve(Scratch &sc, size_t gamma_bytes, size_t gstate_bytes)
+{
+    if (!sc.work) {
+        if (sc.fixed) return fail(RELAYBP_ERR_UNSUPPORTED, "scratch has no work counter");
+        CUDA_TRY(cudaMalloc(&sc.work, 256));
+    }
+    if (sc.gamma_bytes < gamma_bytes) {
+        if (sc.fixed)
+            return fail(RELAYBP_ERR_UNSUPPORTED, "needs %zu bytes of memory-strength scratch, %zu available",
+                        gamma_bytes, sc.gamma_bytes);
+        if (sc.gamma) { cudaFree(sc.gamma); sc.gamma = nullptr; }
+        sc.gamma_bytes = 0;
+        CUDA_TRY(cudaMalloc(&sc.gamma, gamma_bytes));
+        sc.gamma_bytes = gamma_bytes;
+    }
+    if (sc.gstate_bytes < gstate_bytes) {
+        if (sc.fixed)
+            return fail(RELAYBP_ERR_UNSUPPORTED, "needs %zu bytes of off-chip decoder state, %zu available",
+                        gstate_bytes, sc.gstate_bytes);
+        if (sc.gstate) { cudaFree(sc.gstate); sc.gstate = nullptr; }
+        sc.gstate_bytes = 0;
+        CUDA_TRY(cudaMalloc(&sc.gstate, gstate_bytes));
+        sc.gstate_bytes = gstate_bytes;
+    }
+    return 0;
+}
+
+void scratch_free(Scratch &sc)
+{
+    if (sc.fixed) return;
+    cudaFree(sc.work);
+    cudaFree(sc.gamma);
+    cudaFree(sc.gstate);
+    sc = Scratch{};
+}
+
+// Inputs and outputs of one DEM in a launch.
+struct JobIO {
+    const uint32_t *syn;
+    uint64_t shot0;
+    int64_t shots;
+    uint32_t *corr, *pobs;
+    StatsDev *stats;
+    double *trace;
+    int trace_iters;
+};
+
 // FP64 in the literal evaluation order when one shot's per-edge messages fit
 // in shared memory (at most a quarter of it, so that several shots share an
 // SM); returns 1 if the DEM is too large for this kernel.
-int launch_decode_exact(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
-                        uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace, int trace_iters)
+int launch_decode_exact(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st)
 {
     const DevDEM &g = h->dem;
     ExactPlan plan = make_exact_plan(g);
@@ -223,80 +281,93 @@ int launch_decode_exact(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, relay_decode_exact_kernel, threads, plan.total));
     if (per_sm < 1) return 1;
     int64_t blocks = (int64_t)per_sm * h->num_sms;
-    if (blocks > shots) blocks = shots;
-    CUDA_TRY(cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st));
+    if (blocks > io.shots) blocks = io.shots;
+    if (int rc = scratch_reserve(sc, 0, 0)) return rc;
+    CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
     relay_decode_exact_kernel<<<(unsigned)blocks, threads, plan.total, st>>>(
-        g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, h->d_work, d_trace, trace_iters);
+        g, dev_params(h->params), plan, io.syn, io.shot0, io.shots, io.corr, io.pobs, io.stats, sc.work, io.trace,
+        io.trace_iters);
     CUDA_TRY(cudaGetLastError());
     h->launches += 1;
     return 0;
 }
 
+// One persistent launch of the compressed kernel over n jobs (DEMs).
 template <typename S, int L, int NB>
-int launch_decode_geom(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
-                       uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace, int trace_iters)
+int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, cudaStream_t st, bool on_chip_only)
 {
     using C = typename Prec<S>::C;
-    const DevDEM &g = h->dem;
-    SmemPlan plan = make_plan(g, sizeof(S), sizeof(CheckState<S>), L);
+    if (n < 1 || n > kMaxJobs) return fail(RELAYBP_ERR_INVALID, "%d DEMs in one launch (1..%d)", n, kMaxJobs);
+    const int device = hs[0]->device, num_sms = hs[0]->num_sms;
+    JobTable tab{};
+    int plan_max = 0, vmax = 0, threads = 64;
+    int64_t total = 0;
+    for (int d = 0; d < n; ++d) {
+        const relaybp_handle *h = hs[d];
+        DecodeJob &J = tab.job[d];
+        J.g = h->dem;
+        J.p = dev_params(h->params);
+        J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), L);
+        J.syn_in = io[d].syn;
+        J.shot0 = io[d].shot0;
+        J.shots = io[d].shots;
+        J.corr_out = io[d].corr;
+        J.pobs_out = io[d].pobs;
+        J.stats_out = io[d].stats;
+        J.trace = io[d].trace;
+        J.trace_iters = io[d].trace_iters;
+        tab.start[d] = total;
+        total += io[d].shots;
+        plan_max = std::max(plan_max, J.plan.total);
+        vmax = std::max(vmax, h->dem.V);
+        threads = std::max(threads, block_threads(h->dem));
+    }
+    tab.start[n] = total;
+    tab.n = n;
+    if (total == 0) return 0;
     int maxsm = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
     // shared-memory state when one shot's state fits, else a per-block region
     // of global memory (one block per SM keeps the regions L2-resident)
-    const bool gs = plan.total + 1024 > maxsm;
-    const int threads = block_threads(g);
-    int64_t blocks = 0, resident = 0;
+    const bool gs = plan_max + 1024 > maxsm;
+    if (gs && on_chip_only)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes); "
+                    "the allocation-free entry point keeps it on chip only: use relaybp_decode_batch",
+                    plan_max, maxsm);
+    int64_t resident = num_sms;
     if (!gs) {
         auto kern = relay_decode_kernel<S, L, NB, false>;
-        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan_max));
         int per_sm = 0;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan.total));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan_max));
         if (per_sm < 1)
-            return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan.total);
-        resident = (int64_t)per_sm * h->num_sms;
-    } else {
-        resident = h->num_sms;
+            return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan_max);
+        resident = (int64_t)per_sm * num_sms;
     }
-    blocks = std::min<int64_t>(resident, shots);
-    if (blocks < 1) blocks = 1;
-    // scratch: the leg's memory strengths, one row of V per block
-    if (h->gamma_blocks < blocks || h->gamma_elem != sizeof(C)) {
-        if (h->d_gamma) { cudaFree(h->d_gamma); h->d_gamma = nullptr; }
-        h->gamma_blocks = 0;
-        CUDA_TRY(cudaMalloc(&h->d_gamma, (size_t)resident * g.V * sizeof(C) + 16));
-        h->gamma_blocks = resident;
-        h->gamma_elem = sizeof(C);
-    }
-    if (gs && h->gstate_bytes < (size_t)blocks * plan.total) {
-        if (h->d_gstate) { cudaFree(h->d_gstate); h->d_gstate = nullptr; }
-        h->gstate_bytes = 0;
-        CUDA_TRY(cudaMalloc(&h->d_gstate, (size_t)resident * plan.total));
-        h->gstate_bytes = (size_t)resident * plan.total;
-    }
-    CUDA_TRY(cudaMemsetAsync(h->d_work, 0, sizeof(unsigned long long), st));
+    int64_t blocks = std::min<int64_t>(resident, total);
+    const size_t stride = ((size_t)plan_max + 255) & ~(size_t)255;
+    const size_t gamma_need = (size_t)(sc.fixed ? blocks : resident) * vmax * sizeof(C);
+    if (int rc = scratch_reserve(sc, gamma_need, gs ? (size_t)resident * stride : 0)) return rc;
+    CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
     if (!gs)
-        relay_decode_kernel<S, L, NB, false><<<(unsigned)blocks, threads, plan.total, st>>>(
-            g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, h->d_work,
-            static_cast<C *>(h->d_gamma), d_trace, trace_iters, nullptr);
+        relay_decode_kernel<S, L, NB, false><<<(unsigned)blocks, threads, plan_max, st>>>(
+            tab, sc.work, static_cast<C *>(sc.gamma), vmax, nullptr, 0);
     else
         relay_decode_kernel<S, L, NB, true><<<(unsigned)blocks, threads, 0, st>>>(
-            g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, h->d_work,
-            static_cast<C *>(h->d_gamma), d_trace, trace_iters, h->d_gstate);
+            tab, sc.work, static_cast<C *>(sc.gamma), vmax, sc.gstate, stride);
     CUDA_TRY(cudaGetLastError());
-    h->launches += 1;
     return 0;
 }
 
 template <typename S>
-int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
-                  uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace = nullptr,
-                  int trace_iters = 0)
+int launch_jobs_geom(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, cudaStream_t st,
+                     bool on_chip_only)
 {
-    const RowGeom rg = row_geom(h->max_row_deg);
+    int maxdeg = 0;
+    for (int d = 0; d < n; ++d) maxdeg = std::max(maxdeg, hs[d]->max_row_deg);
+    const RowGeom rg = row_geom(maxdeg);
 #define RELAYBP_GEOM(LL, NN)                                                                                   \
-    if (rg.L == LL && rg.NB == NN)                                                                            \
-        return launch_decode_geom<S, LL, NN>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace,    \
-                                             trace_iters);
+    if (rg.L == LL && rg.NB == NN) return launch_jobs<S, LL, NN>(hs, io, n, sc, st, on_chip_only);
     RELAYBP_GEOM(4, 4)
     RELAYBP_GEOM(8, 4)
     RELAYBP_GEOM(8, 8)
@@ -305,25 +376,31 @@ int launch_decode(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int6
     RELAYBP_GEOM(16, 16)
     RELAYBP_GEOM(32, 16)
 #undef RELAYBP_GEOM
-    return fail(RELAYBP_ERR_UNSUPPORTED, "a detector touches %d faults; the decode kernel handles at most 512",
-                h->max_row_deg);
+    return fail(RELAYBP_ERR_UNSUPPORTED, "a detector touches %d faults; the decode kernel handles at most 512", maxdeg);
 }
 
-// Storage-precision dispatch of the compressed kernels.
-int launch_decode_dtype(relaybp_handle *h, const uint32_t *d_syn, uint64_t shot0, int64_t shots, uint32_t *d_corr,
-                        uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st, double *d_trace, int trace_iters)
+// Storage-precision dispatch of the compressed kernel (all jobs share it).
+int launch_jobs_dtype(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, cudaStream_t st,
+                      bool on_chip_only = false)
 {
-    switch (h->params.msg_dtype) {
-    case RELAYBP_MSG_F64:
-        return launch_decode<double>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace, trace_iters);
-    case RELAYBP_MSG_F16:
-        return launch_decode<__half>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace, trace_iters);
-    case RELAYBP_MSG_BF16:
-        return launch_decode<__nv_bfloat16>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace,
-                                            trace_iters);
-    default:
-        return launch_decode<float>(h, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st, d_trace, trace_iters);
+    switch (hs[0]->params.msg_dtype) {
+    case RELAYBP_MSG_F64: return launch_jobs_geom<double>(hs, io, n, sc, st, on_chip_only);
+    case RELAYBP_MSG_F16: return launch_jobs_geom<__half>(hs, io, n, sc, st, on_chip_only);
+    case RELAYBP_MSG_BF16: return launch_jobs_geom<__nv_bfloat16>(hs, io, n, sc, st, on_chip_only);
+    default: return launch_jobs_geom<float>(hs, io, n, sc, st, on_chip_only);
     }
+}
+
+// Single-DEM decode: the literal-order FP64 kernel when it applies, else one job.
+int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, bool on_chip_only)
+{
+    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
+        int rc = launch_decode_exact(h, sc, io, st);
+        if (rc <= 0) return rc;
+    }
+    int rc = launch_jobs_dtype(&h, &io, 1, sc, st, on_chip_only);
+    if (rc == 0) h->launches += 1;
+    return rc;
 }
 
 }  // namespace
@@ -437,8 +514,7 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
         (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
         (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
         return bail(rc);
-    ce = cudaMalloc(&h->d_work, 64);
-    if (ce != cudaSuccess) return bail(fail(RELAYBP_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(ce)));
+    if ((rc = scratch_reserve(h->scratch, 0, 0))) return bail(rc);
     *out = h;
     return 0;
 }
@@ -502,13 +578,9 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     if (shots == 0) return 0;
     if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
     static_assert(sizeof(StatsDev) == sizeof(relaybp_shot_stats), "stats layout");
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
-    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
-        int rc = launch_decode_exact(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st, nullptr, 0);
-        if (rc <= 0) return rc;
-    }
-    return launch_decode_dtype(h, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st, nullptr, 0);
+    const JobIO io{d_syndromes, shot0, shots, d_corrections, d_pred_obs, reinterpret_cast<StatsDev *>(d_stats),
+                   nullptr, 0};
+    return decode_single(h, h->scratch, io, static_cast<cudaStream_t>(cuda_stream), false);
 }
 
 int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
@@ -519,13 +591,9 @@ int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     if (shots < 0 || trace_iters < 0) return fail(RELAYBP_ERR_INVALID, "negative size");
     if (shots == 0) return 0;
     if (!d_syndromes || (trace_iters > 0 && !d_trace)) return fail(RELAYBP_ERR_INVALID, "null pointer");
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
-    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
-        int rc = launch_decode_exact(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
-        if (rc <= 0) return rc;
-    }
-    return launch_decode_dtype(h, d_syndromes, shot0, shots, nullptr, nullptr, ds, st, d_trace, trace_iters);
+    const JobIO io{d_syndromes, shot0, shots, nullptr, nullptr, reinterpret_cast<StatsDev *>(d_stats), d_trace,
+                   trace_iters};
+    return decode_single(h, h->scratch, io, static_cast<cudaStream_t>(cuda_stream), false);
 }
 
 int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
@@ -584,6 +652,62 @@ int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const 
     return 0;
 }
 
+int relaybp_group_create(relaybp_handle *const *handles, int32_t n, relaybp_group **out)
+{
+    g_err.clear();
+    if (!out) return fail(RELAYBP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!handles || n < 1 || n > kMaxJobs) return fail(RELAYBP_ERR_INVALID, "a group holds 1..%d handles", kMaxJobs);
+    for (int32_t d = 0; d < n; ++d) {
+        if (!handles[d]) return fail(RELAYBP_ERR_INVALID, "handle %d is NULL", d);
+        if (handles[d]->device != handles[0]->device)
+            return fail(RELAYBP_ERR_INVALID, "handles of a group must share one device");
+        if (handles[d]->params.msg_dtype != handles[0]->params.msg_dtype)
+            return fail(RELAYBP_ERR_INVALID, "handles of a group must share one message precision");
+    }
+    relaybp_group *grp = new relaybp_group();
+    grp->device = handles[0]->device;
+    grp->handles.assign(handles, handles + n);
+    *out = grp;
+    return 0;
+}
+
+int relaybp_group_decode(relaybp_group *grp, const uint32_t *const *d_syndromes, const uint64_t *shot0,
+                         const int64_t *shots, uint32_t *const *d_corrections, uint32_t *const *d_pred_obs,
+                         relaybp_shot_stats *const *d_stats, void *cuda_stream)
+{
+    g_err.clear();
+    if (!grp) return fail(RELAYBP_ERR_INVALID, "group is NULL");
+    if (!d_syndromes || !shot0 || !shots) return fail(RELAYBP_ERR_INVALID, "null array");
+    const int n = (int)grp->handles.size();
+    std::vector<JobIO> io(n);
+    for (int d = 0; d < n; ++d) {
+        if (shots[d] < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count for DEM %d", d);
+        if (shots[d] > 0 && !d_syndromes[d]) return fail(RELAYBP_ERR_INVALID, "syndromes of DEM %d are NULL", d);
+        io[d] = JobIO{d_syndromes[d], shot0[d], shots[d], d_corrections ? d_corrections[d] : nullptr,
+                      d_pred_obs ? d_pred_obs[d] : nullptr,
+                      d_stats ? reinterpret_cast<StatsDev *>(d_stats[d]) : nullptr, nullptr, 0};
+    }
+    int rc = launch_jobs_dtype(grp->handles.data(), io.data(), n, grp->scratch, static_cast<cudaStream_t>(cuda_stream));
+    if (rc == 0) grp->launches += 1;
+    return rc;
+}
+
+int relaybp_group_destroy(relaybp_group *grp)
+{
+    if (!grp) return 0;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(grp->device);
+    cudaDeviceSynchronize();
+    scratch_free(grp->scratch);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete grp;
+    return 0;
+}
+
+int64_t relaybp_group_launch_count(const relaybp_group *grp) { return grp ? grp->launches : -1; }
+
 int64_t relaybp_launch_count(const relaybp_handle *h) { return h ? h->launches : -1; }
 
 int relaybp_probe_smem_read(int32_t reps, float *d_sink, double *bytes_read, void *cuda_stream)
@@ -609,9 +733,7 @@ int relaybp_destroy(relaybp_handle *h)
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     for (void *p : h->allocs) cudaFree(p);
-    cudaFree(h->d_work);
-    cudaFree(h->d_gamma);
-    cudaFree(h->d_gstate);
+    scratch_free(h->scratch);
     cudaFree(h->d_stage_syn);
     cudaFree(h->d_stage_pobs);
     cudaFree(h->d_stage_stats);
@@ -663,89 +785,6 @@ int noalloc_scratch(int device, unsigned char **out)
     return 0;
 }
 
-template <typename T, int L, int NB>
-int noalloc_decode_geom(relaybp_handle *h, unsigned char *scratch, const uint32_t *d_syn, uint64_t shot0,
-                        int64_t shots, uint32_t *d_corr, uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st)
-{
-    using Cm = typename Prec<T>::C;
-    const DevDEM &g = h->dem;
-    SmemPlan plan = make_plan(g, sizeof(T), sizeof(CheckState<T>), L);
-    int maxsm = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (plan.total + 1024 > maxsm)
-        return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes); "
-                    "the allocation-free entry point keeps it on chip only: use relaybp_decode_batch", plan.total, maxsm);
-    auto kern = relay_decode_kernel<T, L, NB, false>;
-    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
-    const int threads = block_threads(g);
-    int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan.total));
-    if (per_sm < 1) return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan.total);
-    int64_t blocks = (int64_t)per_sm * h->num_sms;
-    if (blocks > shots) blocks = shots;
-    // every block needs one row of V memory strengths after the counter
-    const size_t row = (size_t)g.V * sizeof(Cm);
-    const size_t need = kNoAllocCounterBytes + (size_t)blocks * row;
-    if (need > kNoAllocScratchBytes)
-        return fail(RELAYBP_ERR_UNSUPPORTED,
-                    "this DEM needs %zu bytes of decoder scratch (%lld blocks x %zu bytes + counter); the "
-                    "allocation-free entry point has %zu bytes: use relaybp_decode_batch",
-                    need, (long long)blocks, row, kNoAllocScratchBytes);
-    unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
-    Cm *gam = reinterpret_cast<Cm *>(scratch + kNoAllocCounterBytes);
-    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));     // the counter must start at 0
-    kern<<<(unsigned)blocks, threads, plan.total, st>>>(g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr,
-                                                       d_pobs, d_stats, work, gam, nullptr, 0, nullptr);
-    CUDA_TRY(cudaGetLastError());
-    h->launches += 1;
-    return 0;
-}
-
-template <typename T>
-int noalloc_decode(relaybp_handle *h, unsigned char *scratch, const uint32_t *d_syn, uint64_t shot0, int64_t shots,
-                   uint32_t *d_corr, uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st)
-{
-    const RowGeom rg = row_geom(h->max_row_deg);
-#define RELAYBP_NOALLOC_GEOM(LL, NN)                                                                          \
-    if (rg.L == LL && rg.NB == NN)                                                                           \
-        return noalloc_decode_geom<T, LL, NN>(h, scratch, d_syn, shot0, shots, d_corr, d_pobs, d_stats, st);
-    RELAYBP_NOALLOC_GEOM(4, 4)
-    RELAYBP_NOALLOC_GEOM(8, 4)
-    RELAYBP_NOALLOC_GEOM(8, 8)
-    RELAYBP_NOALLOC_GEOM(8, 12)
-    RELAYBP_NOALLOC_GEOM(8, 16)
-    RELAYBP_NOALLOC_GEOM(16, 16)
-    RELAYBP_NOALLOC_GEOM(32, 16)
-#undef RELAYBP_NOALLOC_GEOM
-    return fail(RELAYBP_ERR_UNSUPPORTED, "a detector touches %d faults; the decode kernel handles at most 512",
-                h->max_row_deg);
-}
-
-// FP64 literal-order kernel: only the work counter lives in the scratch.
-int noalloc_decode_exact(relaybp_handle *h, unsigned char *scratch, const uint32_t *d_syn, uint64_t shot0,
-                         int64_t shots, uint32_t *d_corr, uint32_t *d_pobs, StatsDev *d_stats, cudaStream_t st)
-{
-    const DevDEM &g = h->dem;
-    ExactPlan plan = make_exact_plan(g);
-    int maxsm = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (plan.total > maxsm / 4) return 1;
-    CUDA_TRY(cudaFuncSetAttribute(relay_decode_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
-    const int threads = g.E <= 4096 ? 128 : 256;
-    int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, relay_decode_exact_kernel, threads, plan.total));
-    if (per_sm < 1) return 1;
-    int64_t blocks = (int64_t)per_sm * h->num_sms;
-    if (blocks > shots) blocks = shots;
-    unsigned long long *work = reinterpret_cast<unsigned long long *>(scratch);
-    CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), st));
-    relay_decode_exact_kernel<<<(unsigned)blocks, threads, plan.total, st>>>(
-        g, dev_params(h->params), plan, d_syn, shot0, shots, d_corr, d_pobs, d_stats, work, nullptr, 0);
-    CUDA_TRY(cudaGetLastError());
-    h->launches += 1;
-    return 0;
-}
-
 }  // namespace
 
 extern "C" int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0,
@@ -759,20 +798,14 @@ extern "C" int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d
     if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
     unsigned char *scratch = nullptr;
     if (int rc = noalloc_scratch(h->device, &scratch)) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    StatsDev *ds = reinterpret_cast<StatsDev *>(d_stats);
-    switch (h->params.msg_dtype) {
-    case RELAYBP_MSG_F64: {
-        int rc = noalloc_decode_exact(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
-        if (rc <= 0) return rc;
-        return noalloc_decode<double>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
-    }
-    case RELAYBP_MSG_F16:
-        return noalloc_decode<__half>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
-    case RELAYBP_MSG_BF16:
-        return noalloc_decode<__nv_bfloat16>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds,
-                                             st);
-    default:
-        return noalloc_decode<float>(h, scratch, d_syndromes, shot0, shots, d_corrections, d_pred_obs, ds, st);
-    }
+    // a fixed scratch view of the static array: counter first, then the rows;
+    // it never grows, so a launch that needs more is rejected
+    Scratch sc;
+    sc.fixed = true;
+    sc.work = reinterpret_cast<unsigned long long *>(scratch);
+    sc.gamma = scratch + kNoAllocCounterBytes;
+    sc.gamma_bytes = kNoAllocScratchBytes - kNoAllocCounterBytes;
+    const JobIO io{d_syndromes, shot0, shots, d_corrections, d_pred_obs, reinterpret_cast<StatsDev *>(d_stats),
+                   nullptr, 0};
+    return decode_single(h, sc, io, static_cast<cudaStream_t>(cuda_stream), true);
 }

@@ -58,6 +58,10 @@ def _load() -> ctypes.CDLL:
         "relaybp_decode_host": ([P, P, U64, I64, P, P, P], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
+        "relaybp_group_create": ([P, I32, ctypes.POINTER(P)], ctypes.c_int),
+        "relaybp_group_decode": ([P, P, P, P, P, P, P, P], ctypes.c_int),
+        "relaybp_group_launch_count": ([P], I64),
+        "relaybp_group_destroy": ([P], ctypes.c_int),
         "relaybp_probe_smem_read": ([I32, P, P, P], ctypes.c_int),
         "relaybp_destroy": ([P], ctypes.c_int),
         "relaybp_last_error": ([], ctypes.c_char_p),
@@ -73,7 +77,8 @@ _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
-            "relaybp_probe_smem_read", "relaybp_destroy", "relaybp_last_error"]
+            "relaybp_probe_smem_read", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
+            "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
 
 
 class RelayBPError(RuntimeError):
@@ -232,6 +237,45 @@ def relaybp_probe_smem_read(reps: int, d_sink, stream=None) -> float:
     _check(_lib.relaybp_probe_smem_read(reps, _ptr(d_sink), ctypes.byref(b), _stream(stream)),
            "relaybp_probe_smem_read")
     return b.value
+
+
+@dataclass
+class Group:
+    ptr: ctypes.c_void_p
+    handles: list
+
+
+def relaybp_group_create(handles: list) -> Group:
+    arr = (ctypes.c_void_p * len(handles))(*[h.ptr.value if hasattr(h.ptr, "value") else h.ptr for h in handles])
+    out = ctypes.c_void_p()
+    _check(_lib.relaybp_group_create(arr, len(handles), ctypes.byref(out)), "relaybp_group_create")
+    return Group(out, list(handles))
+
+
+def _ptr_array(ts):
+    if ts is None:
+        return None
+    return (ctypes.c_void_p * len(ts))(*[None if t is None else t.data_ptr() for t in ts])
+
+
+def relaybp_group_decode(grp: Group, d_syndromes: list, shot0: list, shots: list, d_corrections=None,
+                         d_pred_obs=None, d_stats=None, stream=None):
+    n = len(grp.handles)
+    s0 = (ctypes.c_uint64 * n)(*shot0)
+    ns = (ctypes.c_int64 * n)(*shots)
+    _check(_lib.relaybp_group_decode(grp.ptr, _ptr_array(d_syndromes), s0, ns, _ptr_array(d_corrections),
+                                     _ptr_array(d_pred_obs), _ptr_array(d_stats), _stream(stream)),
+           "relaybp_group_decode")
+
+
+def relaybp_group_launch_count(grp: Group) -> int:
+    return int(_lib.relaybp_group_launch_count(grp.ptr))
+
+
+def relaybp_group_destroy(grp: Group):
+    if grp.ptr:
+        _check(_lib.relaybp_group_destroy(grp.ptr), "relaybp_group_destroy")
+        grp.ptr = ctypes.c_void_p()
 
 
 def relaybp_destroy(h: Handle):

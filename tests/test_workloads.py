@@ -202,3 +202,11 @@ def test_code_capacity_dem():
     D = code_capacity_dem("ZSZ-LP-160", 0.05)
     assert (D.n_det, D.n_loc, D.n_obs) == (64, 160, 32)
     assert D.n_edges == 576
+
+
+def test_multi_p_builder_matches_single():
+    from workloads.dem import circuit_dems
+    many = circuit_dems("ZSZ-LP-60", [0.001, 0.0025, 0.004], 3, "Z")
+    for D in many:
+        one = circuit_dem("ZSZ-LP-60", D.meta["p"], 3, "Z")
+        assert np.array_equal(D.H_indices, one.H_indices) and np.array_equal(D.priors, one.priors)

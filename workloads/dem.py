@@ -313,6 +313,14 @@ def circuit_dem(code_name: str, p: float, rounds: int | None = None, basis: str 
     Columns appear in the order of the first fault component that produces
     them; merged probabilities accumulate in that order.
     """
+    return circuit_dems(code_name, [p], rounds, basis, chunk)[0]
+
+
+def circuit_dems(code_name: str, ps, rounds: int | None = None, basis: str = "Z",
+                 chunk: int = 1 << 17) -> list[DEM]:
+    """circuit_dem for several noise strengths p, sharing one frame simulation
+    (the detector structure does not depend on p; only the merged
+    probabilities do)."""
     code = load_code(code_name)
     rounds = code.d if rounds is None else rounds
     circ, info = memory_circuit(code, rounds, basis)
@@ -328,7 +336,7 @@ def circuit_dem(code_name: str, p: float, rounds: int | None = None, basis: str 
     sig_all, first_dets, first_obs, probs_all = [], [], [], []
     for f0 in range(0, nf, chunk):
         f1 = min(nf, f0 + chunk)
-        rec, probs = _frame_sim(circ, p, f0, f1)
+        rec, probs = _frame_sim(circ, 1.0, f0, f1)     # unit strength: scaled per p below
         D = np.zeros((n_det, rec.shape[1]), dtype=np.uint64)
         for i, rows in enumerate(det_rows):
             D[i] = np.bitwise_xor.reduce(rec[rows], axis=0)
@@ -362,16 +370,6 @@ def circuit_dem(code_name: str, p: float, rounds: int | None = None, basis: str 
     rank[order] = np.arange(order.size)
     col = rank[inv]
     ncol = order.size
-    col_p = np.zeros(ncol, dtype=np.float64)
-    seen = np.zeros(ncol, dtype=bool)
-    for f in range(col.size):                         # p <- p1 + p2 - 2 p1 p2, in fault order
-        j = col[f]
-        if seen[j]:
-            q = col_p[j]
-            col_p[j] = q + probs[f] - 2.0 * q * probs[f]
-        else:
-            col_p[j] = probs[f]
-            seen[j] = True
     reps = first[order]
     col_dets = [tuple(sets[r][0].tolist()) for r in reps]
     col_obs = [tuple(sets[r][1].tolist()) for r in reps]
@@ -381,8 +379,24 @@ def circuit_dem(code_name: str, p: float, rounds: int | None = None, basis: str 
             raise RuntimeError("signature collision while merging fault mechanisms")
     Hp, Hi = _csr_from_cols(col_dets, n_det)
     Op, Oi = _csr_from_cols(col_obs, n_obs)
-    return DEM(f"{code_name}/circuit/d{rounds}/{basis}/p{p:g}", n_det, ncol, n_obs,
-               Hp, Hi, Op, Oi, col_p, dict(code=code_name, rounds=rounds, basis=basis, p=p, n_fault_components=nf))
+    out = []
+    for p in ps:
+        # component probabilities at strength p: p for resets and measurements,
+        # p/15 for each two-qubit Pauli (the unit-strength values times p)
+        pr = np.where(probs == 1.0, p, p / 15.0)     # unit strength marks p (1.0) or p/15 (1/15)
+        col_p = np.zeros(ncol, dtype=np.float64)
+        seen = np.zeros(ncol, dtype=bool)
+        for f in range(col.size):                     # p <- p1 + p2 - 2 p1 p2, in fault order
+            j = col[f]
+            if seen[j]:
+                q = col_p[j]
+                col_p[j] = q + pr[f] - 2.0 * q * pr[f]
+            else:
+                col_p[j] = pr[f]
+                seen[j] = True
+        out.append(DEM(f"{code_name}/circuit/d{rounds}/{basis}/p{p:g}", n_det, ncol, n_obs, Hp, Hi, Op, Oi, col_p,
+                       dict(code=code_name, rounds=rounds, basis=basis, p=p, n_fault_components=nf)))
+    return out
 
 
 def code_capacity_dem(code_name: str, p: float) -> DEM:
