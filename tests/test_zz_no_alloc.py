@@ -55,3 +55,19 @@ def test_noalloc_matches_decode_batch_twice(case):
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
     R.relaybp_destroy(h)
+
+
+def test_noalloc_rejects_state_beyond_its_limits():
+    """A DEM whose per-shot state does not fit on chip would need off-chip
+    state the allocation-free entry point does not have: a clear error."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    rng = np.random.default_rng(1)
+    C, V = 1500, 70_000
+    rows = [np.sort(rng.choice(V, 8, replace=False)) for _ in range(C)]
+    indptr = np.r_[0, np.cumsum([len(r) for r in rows])].astype(np.int32)
+    h = R.relaybp_build(indptr, np.concatenate(rows), C, V, np.full(V, 0.01), params=R.Params(num_sets=2))
+    syn = torch.zeros((4, h.wc), dtype=torch.int32, device="cuda")
+    with pytest.raises(R.RelayBPError, match="allocation-free"):
+        R.relaybp_decode_batch_noalloc(h, syn, 0, 4)
+    R.relaybp_destroy(h)
