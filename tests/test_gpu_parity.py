@@ -129,7 +129,7 @@ def _oracle_windows(dem, po, syn, shot0, eps, tol, T):
     amount in [-eps, eps], eps the unit roundoff of the arithmetic under test
     (a uniform scaling would not do: min-sum is homogeneous, so it would only
     rescale every message) -- and returns the number of leading iterations in
-    which the two stay within tol/100 of each other with equal decisions, and
+    which the two stay within tol/1000 of each other with equal decisions, and
     at least 1 (after one iteration the GPU's error is a few roundings of
     O(10) terms).  Within that window the GPU must stay within tol of the
     oracle; the margin covers the GPU's many roundings per value per
@@ -145,7 +145,7 @@ def _oracle_windows(dem, po, syn, shot0, eps, tol, T):
         w = 0
         for t in range(n):
             x, y = a["trace"][s_, t], b["trace"][s_, t]
-            if np.any((x < 0) != (y < 0)) or (np.abs(x - y) / np.maximum(1.0, np.abs(x))).max() > tol / 100:
+            if np.any((x < 0) != (y < 0)) or (np.abs(x - y) / np.maximum(1.0, np.abs(x))).max() > tol / 1000:
                 break
             w += 1
         wins.append(max(w, min(1, n)))
