@@ -55,6 +55,10 @@ def _load():
                                                ctypes.c_int32])
         _lib.oracle_relaybp_decode.restype = ctypes.c_int
         _lib.oracle_max_threads.restype = ctypes.c_int
+        _lib.oracle_learned_loss.argtypes = ([ctypes.c_int32] * 2 + [P] * 3 + [ctypes.c_int32, P, ctypes.c_int32, P,
+                                             ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64, P, P,
+                                             ctypes.c_int32])
+        _lib.oracle_learned_loss.restype = ctypes.c_int
     return _lib
 
 
@@ -156,3 +160,27 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
         bits = np.concatenate([bits, np.zeros(bits.shape[:-1] + (pad,), dtype=np.uint8)], axis=-1)
     by = np.packbits(bits, axis=-1, bitorder="little")
     return np.ascontiguousarray(by).view(np.uint32)
+
+
+def learned_loss(dem, w: np.ndarray, knots: np.ndarray, gamma_seed: int, syndromes: np.ndarray,
+                 errors: np.ndarray, shot0: int = 0, trace: bool = False, n_threads: int = 0):
+    """Per-shot loss of the learned forward (T = w.shape[0] unrolled iterations).
+
+    w: [T, E] message weights in row-major edge order; knots: [K+1] inverse CDF
+    of the memory strengths.  Returns (loss [shots], trace [shots, T, V] or None).
+    """
+    lib = _load()
+    Hp, Hi, _, _, pr = _dem_arrays(dem)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    knots = np.ascontiguousarray(knots, dtype=np.float64)
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint32)
+    err = np.ascontiguousarray(errors, dtype=np.uint32)
+    shots = syn.shape[0]
+    T, K = w.shape[0], knots.shape[0] - 1
+    loss = np.zeros(shots, dtype=np.float64)
+    tr = np.zeros((shots, T, dem.n_loc), dtype=np.float64) if trace else None
+    rc = lib.oracle_learned_loss(dem.n_det, dem.n_loc, _ptr(Hp), _ptr(Hi), _ptr(pr), T, _ptr(w), K, _ptr(knots),
+                                 gamma_seed, _ptr(syn), _ptr(err), shot0, shots, _ptr(loss), _ptr(tr), n_threads)
+    if rc != 0:
+        raise ValueError("oracle_learned_loss rejected its input")
+    return loss, tr

@@ -357,3 +357,127 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* a10: learned form (not in the paper; the design of this library)          */
+/* ------------------------------------------------------------------------- */
+/* Learned parameters:
+ *   w[t][e]  per-iteration, per-edge weights of the check-to-variable messages,
+ *            nu_e(t) = w[t-1][e] * (-1)^{s_i} prod_{f != e} sgn(mu_f) * min_{f != e} |mu_f|,
+ *            t = 1..T (iterations past T reuse w[T-1]); e in row-major edge order;
+ *   knots[0..K] nondecreasing: the inverse CDF of the memory strengths,
+ *            g(u) = knots[k] + (knots[k+1] - knots[k]) * (u*K - k), k = floor(u*K),
+ *            u the same 24-bit stream-1 draw as the plain method's legs.
+ * Training objective for one shot: T iterations of one memory-BP leg started
+ * from M = L0, nu = 0, with g_j = g(u_j) of leg 1, and
+ *   loss = sum_t sum_j BCE(M_j(t), e_j),
+ *   BCE(M, e) = e * softplus(M) + (1 - e) * softplus(-M)
+ * (the error probability of bit j is sigmoid(-M_j)).  Plain loops, FP64. */
+static double softplus(double x) { return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
+
+static double knot_gamma(const double *knots, int32_t K, double u)
+{
+    double x = u * (double)K;
+    int32_t k = (int32_t)floor(x);
+    if (k >= K) k = K - 1;
+    double f = x - (double)k;
+    return knots[k] + (knots[k + 1] - knots[k]) * f;
+}
+
+static double draw_u(uint64_t seed, uint64_t shot, int32_t leg, int32_t j, int32_t n_loc)
+{
+    uint64_t nblk = ((uint64_t)n_loc + 3) / 4;
+    uint32_t w = stream_word(seed, shot, 1u, (uint64_t)leg * nblk * 4 + (uint64_t)j);
+    return (double)(w >> 8) * (1.0 / 16777216.0);
+}
+
+/* Loss of each shot under the learned forward (trace optional: [shots][T][V]). */
+int oracle_learned_loss(int32_t n_det, int32_t n_loc, const int32_t *H_indptr, const int32_t *H_indices,
+                        const double *priors, int32_t T, const double *w, int32_t K, const double *knots,
+                        uint64_t gamma_seed, const uint32_t *syndromes, const uint32_t *errors, uint64_t shot0,
+                        int64_t shots, double *loss, double *trace, int32_t n_threads)
+{
+    if (n_det < 0 || n_loc < 0 || shots < 0 || T < 1 || K < 1) return -1;
+    const int32_t E = H_indptr[n_det];
+    int64_t wd = (n_det + 31) / 32, wv = (n_loc + 31) / 32;
+    double *L0 = malloc(sizeof(double) * (size_t)(n_loc + 1));
+    for (int32_t j = 0; j < n_loc; ++j) {
+        double p = priors[j];
+        if (!(p > 0.0 && p < 1.0)) { free(L0); return -1; }
+        L0[j] = log((1.0 - p) / p);
+    }
+    int32_t *cptr = calloc((size_t)n_loc + 1, sizeof(int32_t));
+    int32_t *cedge = malloc(sizeof(int32_t) * (size_t)(E + 1));
+    for (int32_t e = 0; e < E; ++e) cptr[H_indices[e] + 1]++;
+    for (int32_t j = 0; j < n_loc; ++j) cptr[j + 1] += cptr[j];
+    {
+        int32_t *fill = calloc((size_t)n_loc + 1, sizeof(int32_t));
+        for (int32_t i = 0; i < n_det; ++i)
+            for (int32_t e = H_indptr[i]; e < H_indptr[i + 1]; ++e) {
+                int32_t j = H_indices[e];
+                cedge[cptr[j] + fill[j]++] = e;
+            }
+        free(fill);
+    }
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel
+    {
+        double *nu = malloc(sizeof(double) * (size_t)(E + 1));
+        double *mu = malloc(sizeof(double) * (size_t)(E + 1));
+        double *M = malloc(sizeof(double) * (size_t)(n_loc + 1));
+        double *Lam = malloc(sizeof(double) * (size_t)(n_loc + 1));
+        double *gam = malloc(sizeof(double) * (size_t)(n_loc + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t s = 0; s < shots; ++s) {
+            const uint32_t *syn = syndromes + s * wd;
+            const uint32_t *err = errors + s * wv;
+            uint64_t shot = shot0 + (uint64_t)s;
+            double acc = 0.0;
+            for (int32_t j = 0; j < n_loc; ++j) {
+                M[j] = L0[j];
+                gam[j] = knot_gamma(knots, K, draw_u(gamma_seed, shot, 1, j, n_loc));
+            }
+            for (int32_t e = 0; e < E; ++e) nu[e] = 0.0;
+            for (int32_t t = 1; t <= T; ++t) {
+                const double *wt = w + (int64_t)(t - 1) * E;
+                for (int32_t j = 0; j < n_loc; ++j) Lam[j] = (1.0 - gam[j]) * L0[j] + gam[j] * M[j];
+                for (int32_t j = 0; j < n_loc; ++j)
+                    for (int32_t a = cptr[j]; a < cptr[j + 1]; ++a) {
+                        double v = Lam[j];
+                        for (int32_t b = cptr[j]; b < cptr[j + 1]; ++b)
+                            if (b != a) v += nu[cedge[b]];
+                        mu[cedge[a]] = v;
+                    }
+                for (int32_t i = 0; i < n_det; ++i) {
+                    double ssign = get_bit(syn, i) ? -1.0 : 1.0;
+                    for (int32_t e = H_indptr[i]; e < H_indptr[i + 1]; ++e) {
+                        double prod = ssign, mn = INFINITY;
+                        for (int32_t f = H_indptr[i]; f < H_indptr[i + 1]; ++f) {
+                            if (f == e) continue;
+                            prod *= sgn(mu[f]);
+                            double m = fabs(mu[f]);
+                            if (m < mn) mn = m;
+                        }
+                        nu[e] = wt[e] * prod * mn;
+                    }
+                }
+                for (int32_t j = 0; j < n_loc; ++j) {
+                    double v = Lam[j];
+                    for (int32_t a = cptr[j]; a < cptr[j + 1]; ++a) v += nu[cedge[a]];
+                    M[j] = v;
+                    int e_j = get_bit(err, j);
+                    acc += e_j ? softplus(v) : softplus(-v);
+                    if (trace) trace[((int64_t)s * T + (t - 1)) * n_loc + j] = v;
+                }
+            }
+            loss[s] = acc;
+        }
+        free(nu); free(mu); free(M); free(Lam); free(gam);
+    }
+    free(L0); free(cptr); free(cedge);
+    return 0;
+}

@@ -276,3 +276,65 @@ def test_iteration_map_amplifies_rounding():
         assert d[:3].max() < 1e-12
         grew += int(d.max() > 1e-9)
     assert grew >= 1
+
+
+# ---------------------------------------------------------------------------
+# learned form (a10): pinned to the plain method and to a closed form
+# ---------------------------------------------------------------------------
+def test_learned_forward_reduces_to_plain_memory_bp():
+    """w = 1 and constant knots g reproduce the plain oracle's leg 0 run at
+    gamma0 = g bit for bit (an empty check with syndrome 1 keeps it going)."""
+    D = circuit_dem("ZSZ-LP-60", 0.004, 3, "Z")
+    Hd = D.dense_H()
+    Hx = np.vstack([Hd, np.zeros((1, D.n_loc), dtype=np.uint8)])
+    Dx = dem_from_dense(Hx, D.priors)
+    syn, _, err = oracle.sample(D, 21, 0, 6, want_errors=True)
+    S = np.hstack([unpack_bits(syn, D.n_det), np.ones((6, 1), dtype=np.uint8)])
+    synx = pack_bits(S)
+    T, g = 7, 0.3
+    w = np.ones((T, Dx.n_edges))
+    knots = np.full(17, g)
+    loss, tr = oracle.learned_loss(Dx, w, knots, 5, synx, err, trace=True)
+    P = DecodeParams(gamma0=g, pre_iter=T, num_sets=0, max_iterations=1, stop_nconv=1)
+    r = oracle.decode(Dx, P, synx, trace_iters=T)
+    assert np.array_equal(tr, r["trace"])
+    E = unpack_bits(err, D.n_loc).astype(float)
+    sp = lambda x: np.logaddexp(0.0, x)
+    want = (E[:, None, :] * sp(tr) + (1 - E[:, None, :]) * sp(-tr)).sum(axis=(1, 2))
+    assert np.allclose(loss, want, rtol=1e-12)
+
+
+def test_learned_forward_closed_form_two_variables():
+    """One check on two variables, syndrome 1, edge weights w1(t), w2(t) and
+    memory strengths g1, g2 from the knot table:
+        nu_1(t) = -w1(t) L_2(t),  nu_2(t) = -w2(t) L_1(t),
+        L_k(t) = (1 - g_k) L0_k + g_k M_k(t-1),  M_k(0) = L0_k,
+        M_1(t) = L_1(t) - w1(t) L_2(t),  M_2(t) = L_2(t) - w2(t) L_1(t)."""
+    pa, pb = 0.1, 0.3
+    a, b = math.log((1 - pa) / pa), math.log((1 - pb) / pb)
+    H = np.array([[1, 1], [0, 0]], dtype=np.uint8)
+    D = dem_from_dense(H, [pa, pb])
+    T = 6
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.5, 1.5, (T, 2))
+    knots = np.cumsum(np.r_[-0.2, rng.uniform(0.0, 0.08, 16)])
+    seed, shot = 77, 9
+    u = []
+    for j in range(2):
+        word = oracle.philox4x32_10([1 * 1 + j // 4, shot, 0, 1], [seed, 0])[j % 4]
+        u.append((int(word) >> 8) / 2.0 ** 24)
+    g = []
+    for uj in u:
+        k = min(int(np.floor(uj * 16)), 15)
+        g.append(knots[k] + (knots[k + 1] - knots[k]) * (uj * 16 - k))
+    M = [a, b]
+    want = []
+    for t in range(T):
+        L1 = (1 - g[0]) * a + g[0] * M[0]
+        L2 = (1 - g[1]) * b + g[1] * M[1]
+        M = [L1 - w[t, 0] * L2, L2 - w[t, 1] * L1]
+        want.append(list(M))
+    syn = pack_bits(np.array([[1, 1]]))
+    err = pack_bits(np.array([[1, 0]]))
+    loss, tr = oracle.learned_loss(D, w, knots, seed, syn, err, shot0=shot, trace=True)
+    assert np.allclose(tr[0], np.array(want), rtol=1e-12, atol=1e-12)
