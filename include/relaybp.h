@@ -220,6 +220,34 @@ int relaybp_group_decode(relaybp_group *grp, const uint32_t *const *d_syndromes,
 int64_t relaybp_group_launch_count(const relaybp_group *grp);
 int relaybp_group_destroy(relaybp_group *grp);
 
+/* Learned Relay-BP training (no counterpart in the paper: the learned form
+ * of this library).  Parameters, both in the precision `precision`
+ * (RELAYBP_MSG_F32 or RELAYBP_MSG_F64), device memory:
+ *   d_w [T][E]   weight of the check-to-variable message of edge e (row-major
+ *                order of H) in iteration t+1;
+ *   d_knots [K+1], nondecreasing, 1 <= K <= 64: the memory-strength inverse
+ *                CDF g(u) = knots[k] + (knots[k+1] - knots[k]) (uK - k),
+ *                k = floor(uK), u = the leg-1 Philox stream-1 draw (key
+ *                gamma_seed) of each variable.
+ * relaybp_learned_forward runs, for each shot, T iterations of one memory-BP
+ * leg from M = L0, nu = 0 with weighted messages and these strengths, writes
+ * d_loss[s] = sum_t sum_j BCE(M_j(t), e_j) (e = d_errors, bit j in error with
+ * probability sigmoid(-M_j)) and a tape of relaybp_learned_tape_bytes bytes.
+ * relaybp_learned_backward reads the tape and ADDS scale * dLoss/dw and
+ * scale * dLoss/dknots (Loss = sum of the shots' losses) into the
+ * caller-zeroed d_grad_w [T][E] and d_grad_knots [K+1].  Gradients flow
+ * through the argmin and second-argmin of every check (sign products are
+ * piecewise constant); the summation order of the atomics is not fixed. */
+int64_t relaybp_learned_tape_bytes(const relaybp_handle *h, int32_t precision, int32_t T, int64_t shots);
+int relaybp_learned_forward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
+                            const void *d_knots, uint64_t gamma_seed, const uint32_t *d_syndromes,
+                            const uint32_t *d_errors, uint64_t shot0, int64_t shots, void *d_tape, double *d_loss,
+                            void *cuda_stream);
+int relaybp_learned_backward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
+                             const void *d_knots, uint64_t gamma_seed, const uint32_t *d_errors, uint64_t shot0,
+                             int64_t shots, const void *d_tape, double scale, void *d_grad_w, void *d_grad_knots,
+                             void *cuda_stream);
+
 /* Number of kernel launches this handle has issued since it was built. */
 int64_t relaybp_launch_count(const relaybp_handle *h);
 

@@ -59,6 +59,11 @@ def _load():
                                              ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64, P, P,
                                              ctypes.c_int32])
         _lib.oracle_learned_loss.restype = ctypes.c_int
+        _lib.oracle_relaybp_decode_learned.argtypes = ([ctypes.c_int32] * 3 + [P] * 5 +
+                                                       [ctypes.POINTER(OracleParams), ctypes.c_int32, P,
+                                                        ctypes.c_int32, P, P, ctypes.c_uint64, ctypes.c_int64,
+                                                        P, P, P, P, ctypes.c_int32, P, ctypes.c_int32])
+        _lib.oracle_relaybp_decode_learned.restype = ctypes.c_int
     return _lib
 
 
@@ -120,7 +125,7 @@ class DecodeParams:
 
 
 def decode(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0, trace_iters: int = 0,
-           n_threads: int = 0):
+           n_threads: int = 0, w: np.ndarray | None = None, knots: np.ndarray | None = None):
     """Relay-BP on every syndrome row.
 
     Returns dict(corrections, pred_obs, stats[shots,4], weights, trace or None).
@@ -133,15 +138,24 @@ def decode(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0, tra
     corr = np.zeros((shots, (dem.n_loc + 31) // 32), dtype=np.uint32)
     pobs = np.zeros((shots, max(1, (dem.n_obs + 31) // 32)), dtype=np.uint32)
     stats = np.zeros((shots, 4), dtype=np.int32)
-    w = np.zeros(shots, dtype=np.float64)
+    wts = np.zeros(shots, dtype=np.float64)
     trace = np.zeros((shots, trace_iters, dem.n_loc), dtype=np.float64) if trace_iters > 0 else None
     cp = params.c()
-    rc = lib.oracle_relaybp_decode(dem.n_det, dem.n_loc, dem.n_obs, _ptr(Hp), _ptr(Hi), _ptr(Op), _ptr(Oi), _ptr(pr),
-                                   ctypes.byref(cp), _ptr(syn), shot0, shots, _ptr(corr), _ptr(pobs), _ptr(stats),
-                                   _ptr(w), trace_iters, _ptr(trace), n_threads)
+    if w is None and knots is None:
+        rc = lib.oracle_relaybp_decode(dem.n_det, dem.n_loc, dem.n_obs, _ptr(Hp), _ptr(Hi), _ptr(Op), _ptr(Oi),
+                                       _ptr(pr), ctypes.byref(cp), _ptr(syn), shot0, shots, _ptr(corr), _ptr(pobs),
+                                       _ptr(stats), _ptr(wts), trace_iters, _ptr(trace), n_threads)
+    else:
+        lw = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        lk = None if knots is None else np.ascontiguousarray(knots, dtype=np.float64)
+        rc = lib.oracle_relaybp_decode_learned(dem.n_det, dem.n_loc, dem.n_obs, _ptr(Hp), _ptr(Hi), _ptr(Op),
+                                               _ptr(Oi), _ptr(pr), ctypes.byref(cp), 0 if lw is None else lw.shape[0],
+                                               _ptr(lw), 0 if lk is None else lk.shape[0] - 1, _ptr(lk), _ptr(syn),
+                                               shot0, shots, _ptr(corr), _ptr(pobs), _ptr(stats), _ptr(wts),
+                                               trace_iters, _ptr(trace), n_threads)
     if rc != 0:
         raise ValueError("oracle_relaybp_decode rejected its input")
-    return dict(corrections=corr, pred_obs=pobs, stats=stats, weights=w, trace=trace)
+    return dict(corrections=corr, pred_obs=pobs, stats=stats, weights=wts, trace=trace)
 
 
 def unpack_bits(words: np.ndarray, nbits: int) -> np.ndarray:

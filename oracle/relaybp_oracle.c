@@ -186,9 +186,20 @@ static double draw_gamma(const oracle_params *P, uint64_t shot, int32_t leg, int
 
 static double sgn(double v) { return v < 0.0 ? -1.0 : 1.0; }   /* sgn(0) = +1 */
 
-static void decode_one(const graph_t *g, const oracle_params *P, const uint32_t *syn, uint64_t shot,
-                       uint32_t *corr, int32_t *stats, double *weight, int trace_iters, double *trace,
-                       double *nu, double *mu, double *M, double *Lam, double *gam, uint8_t *ehat,
+/* Learned parameters of the decode (the learned form of this library, not the
+ * paper's): message weights w[T][E] indexed by the iteration within the leg
+ * (iterations past T reuse w[T-1]) and the knot inverse CDF of the memory
+ * strengths of legs >= 1.  NULL pointers give the plain method. */
+typedef struct {
+    int32_t T, K;
+    const double *w, *knots;
+} learned_t;
+
+static double knot_gamma_l(const double *knots, int32_t K, double u);
+
+static void decode_one(const graph_t *g, const oracle_params *P, const learned_t *LP, const uint32_t *syn,
+                       uint64_t shot, uint32_t *corr, int32_t *stats, double *weight, int trace_iters,
+                       double *trace, double *nu, double *mu, double *M, double *Lam, double *gam, uint8_t *ehat,
                        uint8_t *best)
 {
     const int32_t V = g->n_loc, C = g->n_det, E = g->rptr[C];
@@ -200,7 +211,14 @@ static void decode_one(const graph_t *g, const oracle_params *P, const uint32_t 
     memset(ehat, 0, (size_t)V);
     for (int32_t leg = 0; leg <= P->num_sets; ++leg) {
         legs++;
-        for (int32_t j = 0; j < V; ++j) gam[j] = (leg == 0) ? P->gamma0 : draw_gamma(P, shot, leg, j, V);
+        for (int32_t j = 0; j < V; ++j) {
+            if (leg == 0) gam[j] = P->gamma0;
+            else if (LP && LP->knots) {
+                uint64_t nblk = ((uint64_t)V + 3) / 4;
+                uint32_t wd = stream_word(P->seed, shot, 1u, (uint64_t)leg * nblk * 4 + (uint64_t)j);
+                gam[j] = knot_gamma_l(LP->knots, LP->K, (double)(wd >> 8) * (1.0 / 16777216.0));
+            } else gam[j] = draw_gamma(P, shot, leg, j, V);
+        }
         if (leg > 0 && !P->carry_messages)
             for (int32_t e = 0; e < E; ++e) nu[e] = 0.0;
         int32_t T = (leg == 0) ? P->pre_iter : P->max_iterations;
@@ -218,6 +236,7 @@ static void decode_one(const graph_t *g, const oracle_params *P, const uint32_t 
                     mu[e] = s;
                 }
             /* a3: min-sum check update, leave-one-out by direct loops */
+            const double *wt = (LP && LP->w) ? LP->w + (int64_t)((t - 1 < LP->T ? t - 1 : LP->T - 1)) * E : NULL;
             for (int32_t i = 0; i < C; ++i) {
                 double ssign = get_bit(syn, i) ? -1.0 : 1.0;
                 for (int32_t e = g->rptr[i]; e < g->rptr[i + 1]; ++e) {
@@ -228,7 +247,7 @@ static void decode_one(const graph_t *g, const oracle_params *P, const uint32_t 
                         double m = fabs(mu[f]);
                         if (m < mn) mn = m;
                     }
-                    nu[e] = prod * mn;   /* a degree-1 check sends +-inf: the bit is forced */
+                    nu[e] = wt ? wt[e] * prod * mn : prod * mn;   /* a degree-1 check sends +-inf */
                 }
             }
             /* a4 (second half): marginals and hard decisions */
@@ -278,6 +297,14 @@ static void decode_one(const graph_t *g, const oracle_params *P, const uint32_t 
  * iterations; weights: [shots] FP64 weight of the returned correction; trace
  * (optional): [shots][trace_iters][n_loc] marginals M after each iteration.
  * Returns 0, or -1 on invalid input. */
+static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
+                       const int32_t *H_indptr, const int32_t *H_indices,
+                       const int32_t *O_indptr, const int32_t *O_indices,
+                       const double *priors, const oracle_params *P, const learned_t *LP,
+                       const uint32_t *syndromes, uint64_t shot0, int64_t shots,
+                       uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
+                       int32_t trace_iters, double *trace, int32_t n_threads);
+
 int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
                           const int32_t *H_indptr, const int32_t *H_indices,
                           const int32_t *O_indptr, const int32_t *O_indices,
@@ -285,6 +312,34 @@ int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
                           const uint32_t *syndromes, uint64_t shot0, int64_t shots,
                           uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
                           int32_t trace_iters, double *trace, int32_t n_threads)
+{
+    return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, NULL, syndromes,
+                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, n_threads);
+}
+
+/* Relay-BP with learned parameters: w [T][E] (or NULL), knots [K+1] (or NULL). */
+int oracle_relaybp_decode_learned(int32_t n_det, int32_t n_loc, int32_t n_obs,
+                                  const int32_t *H_indptr, const int32_t *H_indices,
+                                  const int32_t *O_indptr, const int32_t *O_indices,
+                                  const double *priors, const oracle_params *P,
+                                  int32_t T, const double *w, int32_t K, const double *knots,
+                                  const uint32_t *syndromes, uint64_t shot0, int64_t shots,
+                                  uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
+                                  int32_t trace_iters, double *trace, int32_t n_threads)
+{
+    if ((w && T < 1) || (knots && K < 1) || (w && P->carry_messages)) return -1;
+    learned_t LP = {T, K, w, knots};
+    return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, &LP, syndromes,
+                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, n_threads);
+}
+
+static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
+                       const int32_t *H_indptr, const int32_t *H_indices,
+                       const int32_t *O_indptr, const int32_t *O_indices,
+                       const double *priors, const oracle_params *P, const learned_t *LP,
+                       const uint32_t *syndromes, uint64_t shot0, int64_t shots,
+                       uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
+                       int32_t trace_iters, double *trace, int32_t n_threads)
 {
     if (n_det < 0 || n_loc < 0 || shots < 0 || !P) return -1;
     if (P->pre_iter < 0 || P->max_iterations < 0 || P->num_sets < 0 || P->stop_nconv < 1) return -1;
@@ -330,7 +385,7 @@ int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
 #pragma omp for schedule(dynamic, 1)
         for (int64_t s = 0; s < shots; ++s) {
             uint32_t *corr = corrections + s * wv;
-            decode_one(&g, P, syndromes + s * wd, shot0 + (uint64_t)s, corr, stats + 4 * s, weights + s,
+            decode_one(&g, P, LP, syndromes + s * wd, shot0 + (uint64_t)s, corr, stats + 4 * s, weights + s,
                        trace_iters, trace ? trace + s * (int64_t)trace_iters * n_loc : NULL,
                        nu, mu, M, Lam, gam, ehat, best);
             if (pred_obs) {
@@ -481,3 +536,6 @@ int oracle_learned_loss(int32_t n_det, int32_t n_loc, const int32_t *H_indptr, c
     free(L0); free(cptr); free(cedge);
     return 0;
 }
+
+
+static double knot_gamma_l(const double *knots, int32_t K, double u) { return knot_gamma(knots, K, u); }

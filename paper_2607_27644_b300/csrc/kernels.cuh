@@ -42,6 +42,7 @@ struct DevDEM {
     const uint32_t *cinfo;      // sliced ELL: per 32-variable group, slot-major entries
     const int32_t *goff;        // [ceil(V/32)] offset of each group's slots in cinfo
     const int32_t *gdeg;        // [ceil(V/32)] slots (largest column degree) of each group
+    const uint32_t *cedge_ell;  // same slots as cinfo: row-major edge index of each entry
     const int32_t *optr;        // [V+1] column pointers into oidx
     const int32_t *oidx;        // observables flipped by each fault
     const double *L0d;          // [V] prior LLRs, FP64

@@ -18,6 +18,7 @@
 
 #include "../../include/relaybp.h"
 #include "kernels.cuh"
+#include "learned.cuh"
 
 using namespace relaybp;
 
@@ -73,6 +74,10 @@ struct relaybp_handle {
     int64_t stage_shots = 0;
     int64_t launches = 0;
     int max_row_deg = 0;
+    // learned-form training scratch: work counter and one gradient row per block
+    unsigned long long *d_lwork = nullptr;
+    void *d_lgbar = nullptr;
+    size_t lgbar_bytes = 0;
 };
 
 struct relaybp_group {
@@ -403,9 +408,193 @@ int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t 
     return rc;
 }
 
+// ---- learned form ----------------------------------------------------------
+template <typename T>
+TapePlan tape_plan(const DevDEM &g, int L)
+{
+    TapePlan tp{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        size_t at = off;
+        off += bytes;
+        return (int)at;
+    };
+    tp.rows = take(sizeof(TapeRow<T>) * (size_t)g.C);
+    tp.sgn = take(2 * (size_t)g.C * (size_t)L);
+    tp.M = take(sizeof(T) * (size_t)g.V);
+    tp.iter = (int)((off + 15) & ~size_t(15));
+    return tp;
+}
+
+template <typename T>
+LearnedSmem learned_smem(const DevDEM &g, int L, bool backward)
+{
+    LearnedSmem sp{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        size_t at = off;
+        off += bytes;
+        return (int)at;
+    };
+    sp.a = take(sizeof(T) * (size_t)g.V);
+    sp.b = take(sizeof(T) * (size_t)g.V);
+    sp.c = take(sizeof(T) * (size_t)g.V);
+    sp.d = backward ? take(sizeof(T) * (size_t)g.V) : 0;
+    sp.rows = take((backward ? sizeof(BackRow<T>) : sizeof(TapeRow<T>)) * (size_t)g.C);
+    sp.sgn = backward ? 0 : take(2 * (size_t)g.C * (size_t)L);
+    sp.syn = take(4 * (size_t)words(g.C));
+    sp.total = (int)((off + 15) & ~size_t(15));
+    return sp;
+}
+
+struct LearnedCall {
+    int precision, T, K;
+    const void *w, *knots;
+    uint64_t gamma_seed;
+    const uint32_t *syn, *err;
+    uint64_t shot0;
+    int64_t shots;
+    void *tape;
+    double *loss;
+    double scale;
+    void *grad_w, *grad_knots;
+};
+
+template <typename T, int L, int NB>
+int learned_launch(relaybp_handle *h, const LearnedCall &c, bool backward, cudaStream_t st)
+{
+    const DevDEM &g = h->dem;
+    LearnedSmem sp = learned_smem<T>(g, L, backward);
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (sp.total + 1024 > maxsm)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned %s state (%d bytes) exceeds shared memory (%d bytes)",
+                    backward ? "backward" : "forward", sp.total, maxsm);
+    LearnedDev a{};
+    a.g = g;
+    a.T = c.T;
+    a.K = c.K;
+    a.w = c.w;
+    a.knots = c.knots;
+    a.gamma_seed = c.gamma_seed;
+    a.syn = c.syn;
+    a.err = c.err;
+    a.shot0 = c.shot0;
+    a.shots = c.shots;
+    a.tape = static_cast<unsigned char *>(c.tape);
+    a.tp = tape_plan<T>(g, L);
+    a.loss = c.loss;
+    a.cedge_ell = g.cedge_ell;
+    const int threads = 512;
+    int per_sm = 0;
+    if (!backward) {
+        auto kern = learned_forward_kernel<T, L, NB>;
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sp.total));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sp.total));
+    } else {
+        auto kern = learned_backward_kernel<T, L, NB>;
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sp.total));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sp.total));
+    }
+    if (per_sm < 1) return fail(RELAYBP_ERR_UNSUPPORTED, "learned kernel cannot be resident");
+    const int64_t blocks = std::min<int64_t>((int64_t)per_sm * h->num_sms, c.shots);
+    if (!h->d_lwork) CUDA_TRY(cudaMalloc(&h->d_lwork, 256));
+    CUDA_TRY(cudaMemsetAsync(h->d_lwork, 0, sizeof(unsigned long long), st));
+    if (!backward) {
+        learned_forward_kernel<T, L, NB><<<(unsigned)blocks, threads, sp.total, st>>>(a, sp, h->d_lwork);
+    } else {
+        const size_t need = (size_t)blocks * g.V * sizeof(T);
+        if (h->lgbar_bytes < need) {
+            cudaFree(h->d_lgbar);
+            h->d_lgbar = nullptr;
+            h->lgbar_bytes = 0;
+            CUDA_TRY(cudaMalloc(&h->d_lgbar, need));
+            h->lgbar_bytes = need;
+        }
+        learned_backward_kernel<T, L, NB><<<(unsigned)blocks, threads, sp.total, st>>>(
+            a, sp, h->d_lwork, (T)c.scale, static_cast<T *>(c.grad_w), static_cast<T *>(c.grad_knots),
+            static_cast<T *>(h->d_lgbar));
+    }
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
+}
+
+template <typename T>
+int learned_dispatch(relaybp_handle *h, const LearnedCall &c, bool backward, cudaStream_t st)
+{
+    const RowGeom rg = row_geom(h->max_row_deg);
+#define RELAYBP_LGEOM(LL, NN) \
+    if (rg.L == LL && rg.NB == NN) return learned_launch<T, LL, NN>(h, c, backward, st);
+    RELAYBP_LGEOM(4, 4)
+    RELAYBP_LGEOM(8, 4)
+    RELAYBP_LGEOM(8, 8)
+    RELAYBP_LGEOM(8, 12)
+    RELAYBP_LGEOM(8, 16)
+    RELAYBP_LGEOM(16, 16)
+    RELAYBP_LGEOM(32, 16)
+#undef RELAYBP_LGEOM
+    return fail(RELAYBP_ERR_UNSUPPORTED, "a detector touches %d faults (limit 512)", h->max_row_deg);
+}
+
+int learned_check(relaybp_handle *h, const LearnedCall &c, bool backward)
+{
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (c.precision != RELAYBP_MSG_F32 && c.precision != RELAYBP_MSG_F64)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned training runs in FP32 or FP64");
+    if (c.T < 1 || c.K < 1 || c.K > 64) return fail(RELAYBP_ERR_INVALID, "need T >= 1 and 1 <= K <= 64");
+    if (c.shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (!c.w || !c.knots || !c.err || !c.tape) return fail(RELAYBP_ERR_INVALID, "null pointer");
+    if (!backward && (!c.syn || !c.loss)) return fail(RELAYBP_ERR_INVALID, "null pointer");
+    if (backward && (!c.grad_w || !c.grad_knots)) return fail(RELAYBP_ERR_INVALID, "null pointer");
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
+
+int64_t relaybp_learned_tape_bytes(const relaybp_handle *h, int32_t precision, int32_t T, int64_t shots)
+{
+    if (!h || T < 1 || shots < 0) return -1;
+    const RowGeom rg = row_geom(h->max_row_deg);
+    if (rg.L == 0) return -1;
+    const TapePlan tp = precision == RELAYBP_MSG_F64 ? tape_plan<double>(h->dem, rg.L) : tape_plan<float>(h->dem, rg.L);
+    return (int64_t)tp.iter * T * shots;
+}
+
+int relaybp_learned_forward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
+                            const void *d_knots, uint64_t gamma_seed, const uint32_t *d_syndromes,
+                            const uint32_t *d_errors, uint64_t shot0, int64_t shots, void *d_tape, double *d_loss,
+                            void *cuda_stream)
+{
+    g_err.clear();
+    LearnedCall c{precision, T, K, d_w, d_knots, gamma_seed, d_syndromes, d_errors, shot0, shots, d_tape, d_loss,
+                  0.0, nullptr, nullptr};
+    if (int rc = learned_check(h, c, false)) return rc;
+    if (shots == 0) return 0;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    return precision == RELAYBP_MSG_F64 ? learned_dispatch<double>(h, c, false, st)
+                                        : learned_dispatch<float>(h, c, false, st);
+}
+
+int relaybp_learned_backward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
+                             const void *d_knots, uint64_t gamma_seed, const uint32_t *d_errors, uint64_t shot0,
+                             int64_t shots, const void *d_tape, double scale, void *d_grad_w, void *d_grad_knots,
+                             void *cuda_stream)
+{
+    g_err.clear();
+    LearnedCall c{precision, T, K, d_w, d_knots, gamma_seed, nullptr, d_errors, shot0, shots,
+                  const_cast<void *>(d_tape), nullptr, scale, d_grad_w, d_grad_knots};
+    if (int rc = learned_check(h, c, true)) return rc;
+    if (shots == 0) return 0;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    return precision == RELAYBP_MSG_F64 ? learned_dispatch<double>(h, c, true, st)
+                                        : learned_dispatch<float>(h, c, true, st);
+}
+
 
 const char *relaybp_last_error(void) { return g_err.c_str(); }
 
@@ -470,13 +659,14 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
         gdeg[G] = D;
         goff[G + 1] = goff[G] + D * 32;
     }
-    std::vector<uint32_t> cinfo((size_t)goff[NG], COL_SENTINEL);
+    std::vector<uint32_t> cinfo((size_t)goff[NG], COL_SENTINEL), cedge_ell((size_t)goff[NG], 0u);
     for (int32_t j = 0; j < V; ++j) {
         const int32_t G = j / 32, l = j % 32;
         for (int32_t k = 0; k < cptr[j + 1] - cptr[j]; ++k) {
             const int32_t i = cchk[cptr[j] + k];
             const int32_t pos = cedge[cptr[j] + k] - rptr[i];
             cinfo[(size_t)goff[G] + (size_t)k * 32 + l] = ((uint32_t)i << 12) | (uint32_t)pos;
+            cedge_ell[(size_t)goff[G] + (size_t)k * 32 + l] = (uint32_t)cedge[cptr[j] + k];
         }
     }
     // observables per column
@@ -509,7 +699,7 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     int rc = 0;
     if ((rc = upload(h, rptr, &g.rptr)) || (rc = upload(h, rvar, &g.rvar)) || 
         (rc = upload(h, cptr, &g.cptr)) || (rc = upload(h, cchk, &g.cchk)) || 
-        (rc = upload(h, cedge, &g.cedge)) || (rc = upload(h, cinfo, &g.cinfo)) || (rc = upload(h, goff, &g.goff)) ||
+        (rc = upload(h, cedge, &g.cedge)) || (rc = upload(h, cinfo, &g.cinfo)) || (rc = upload(h, cedge_ell, &g.cedge_ell)) || (rc = upload(h, goff, &g.goff)) ||
         (rc = upload(h, gdeg, &g.gdeg)) ||
         (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
         (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
@@ -734,6 +924,8 @@ int relaybp_destroy(relaybp_handle *h)
     cudaDeviceSynchronize();
     for (void *p : h->allocs) cudaFree(p);
     scratch_free(h->scratch);
+    cudaFree(h->d_lwork);
+    cudaFree(h->d_lgbar);
     cudaFree(h->d_stage_syn);
     cudaFree(h->d_stage_pobs);
     cudaFree(h->d_stage_stats);

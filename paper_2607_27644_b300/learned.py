@@ -1,0 +1,66 @@
+"""Learned Relay-BP: trainable message weights and memory-strength distribution.
+
+Not in arXiv 2607.27644 (which decodes with plain Relay-BP).  The model:
+per-iteration, per-edge weights w[t][e] on the min-sum check-to-variable
+messages and a monotone piecewise-linear inverse CDF of the memory strength
+(K segments) in place of the uniform interval.  The loss is the summed binary
+cross-entropy of the posteriors against the sampled errors over T unrolled
+iterations of one memory-BP leg; forward and backward run in the library's
+CUDA kernels (relaybp_learned_forward / _backward), wrapped here in a
+torch.autograd.Function so torch optimisers can train the parameters.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import relaybp as R
+
+
+class LearnedLoss(torch.autograd.Function):
+    """loss = mean over shots of sum_t sum_j BCE(M_j(t), e_j)."""
+
+    @staticmethod
+    def forward(ctx, w, knots, handle, syndromes, errors, shot0: int, gamma_seed: int):
+        shots = syndromes.shape[0]
+        T = w.shape[0]
+        prec = R._prec(w.dtype)
+        tape = torch.empty(R.relaybp_learned_tape_bytes(handle, prec, T, shots), dtype=torch.uint8,
+                           device=w.device)
+        loss = torch.empty(shots, dtype=torch.float64, device=w.device)
+        R.relaybp_learned_forward(handle, w, knots, gamma_seed, syndromes, errors, shot0, shots, tape, loss)
+        ctx.save_for_backward(w, knots, errors, tape)
+        ctx.meta = (handle, shot0, gamma_seed, shots)
+        return loss.mean().to(w.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        w, knots, errors, tape = ctx.saved_tensors
+        handle, shot0, gamma_seed, shots = ctx.meta
+        gw = torch.zeros_like(w)
+        gk = torch.zeros_like(knots)
+        scale = float(grad_out.item()) / shots
+        R.relaybp_learned_backward(handle, w, knots, gamma_seed, errors, shot0, shots, tape, scale, gw, gk)
+        return gw, gk, None, None, None, None, None
+
+
+class LearnedParams(torch.nn.Module):
+    """w [T, E] initialised to 1 and knots from raw parameters kept monotone:
+    knots[0] = theta[0], knots[k+1] = knots[k] + softplus(theta[k+1]);
+    initialised to the uniform interval [gamma_min, gamma_max]."""
+
+    def __init__(self, T: int, n_edges: int, gamma_min: float, gamma_max: float, K: int = 16,
+                 dtype=torch.float32, device="cuda"):
+        super().__init__()
+        self.w = torch.nn.Parameter(torch.ones((T, n_edges), dtype=dtype, device=device))
+        step = (gamma_max - gamma_min) / K
+        inv_sp = float(torch.log(torch.expm1(torch.tensor(step, dtype=torch.float64))))
+        theta = torch.full((K + 1,), inv_sp, dtype=dtype, device=device)
+        theta[0] = gamma_min
+        self.theta = torch.nn.Parameter(theta)
+
+    def knots(self):
+        return torch.cat([self.theta[:1], self.theta[:1] + torch.cumsum(torch.nn.functional.softplus(self.theta[1:]),
+                                                                        0)])
+
+    def loss(self, handle, syndromes, errors, shot0: int, gamma_seed: int):
+        return LearnedLoss.apply(self.w, self.knots(), handle, syndromes, errors, shot0, gamma_seed)

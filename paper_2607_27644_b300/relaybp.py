@@ -58,6 +58,10 @@ def _load() -> ctypes.CDLL:
         "relaybp_decode_host": ([P, P, U64, I64, P, P, P], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
+        "relaybp_learned_tape_bytes": ([P, I32, I32, I64], I64),
+        "relaybp_learned_forward": ([P, I32, I32, P, I32, P, U64, P, P, U64, I64, P, P, P], ctypes.c_int),
+        "relaybp_learned_backward": ([P, I32, I32, P, I32, P, U64, P, U64, I64, P, ctypes.c_double, P, P, P],
+                                     ctypes.c_int),
         "relaybp_group_create": ([P, I32, ctypes.POINTER(P)], ctypes.c_int),
         "relaybp_group_decode": ([P, P, P, P, P, P, P, P], ctypes.c_int),
         "relaybp_group_launch_count": ([P], I64),
@@ -77,7 +81,8 @@ _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
-            "relaybp_probe_smem_read", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
+            "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
+            "relaybp_learned_backward", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
             "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
 
 
@@ -237,6 +242,38 @@ def relaybp_probe_smem_read(reps: int, d_sink, stream=None) -> float:
     _check(_lib.relaybp_probe_smem_read(reps, _ptr(d_sink), ctypes.byref(b), _stream(stream)),
            "relaybp_probe_smem_read")
     return b.value
+
+
+def _prec(dtype) -> int:
+    import torch
+    if dtype == torch.float64:
+        return RELAYBP_MSG_F64
+    if dtype == torch.float32:
+        return RELAYBP_MSG_F32
+    raise ValueError("learned training runs in float32 or float64")
+
+
+def relaybp_learned_tape_bytes(h: Handle, precision: int, T: int, shots: int) -> int:
+    n = int(_lib.relaybp_learned_tape_bytes(h.ptr, precision, T, shots))
+    if n < 0:
+        raise RelayBPError("relaybp_learned_tape_bytes: invalid arguments")
+    return n
+
+
+def relaybp_learned_forward(h: Handle, w, knots, gamma_seed: int, d_syndromes, d_errors, shot0: int, shots: int,
+                            d_tape, d_loss, stream=None):
+    T, K = w.shape[0], knots.shape[0] - 1
+    _check(_lib.relaybp_learned_forward(h.ptr, _prec(w.dtype), T, _ptr(w), K, _ptr(knots), gamma_seed,
+                                        _ptr(d_syndromes), _ptr(d_errors), shot0, shots, _ptr(d_tape), _ptr(d_loss),
+                                        _stream(stream)), "relaybp_learned_forward")
+
+
+def relaybp_learned_backward(h: Handle, w, knots, gamma_seed: int, d_errors, shot0: int, shots: int, d_tape,
+                             scale: float, d_grad_w, d_grad_knots, stream=None):
+    T, K = w.shape[0], knots.shape[0] - 1
+    _check(_lib.relaybp_learned_backward(h.ptr, _prec(w.dtype), T, _ptr(w), K, _ptr(knots), gamma_seed,
+                                         _ptr(d_errors), shot0, shots, _ptr(d_tape), scale, _ptr(d_grad_w),
+                                         _ptr(d_grad_knots), _stream(stream)), "relaybp_learned_backward")
 
 
 @dataclass

@@ -1,0 +1,131 @@
+"""Learned form: GPU forward loss and backward gradients against the FP64
+oracle -- the loss directly, the gradients by central finite differences of
+the oracle's forward (coordinates where a min/argmin kink lies within the
+step, seen as FD(h) != FD(h/2), are excluded)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import unpack_bits
+from workloads.dem import circuit_dem
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(dem, T, seed, dtype):
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.6, 1.4, (T, dem.n_edges))
+    knots = np.cumsum(np.r_[-0.2, rng.uniform(0.02, 0.07, 16)])
+    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", num_sets=1))
+    return R, h, w, knots
+
+
+def _gpu_loss_grad(R, h, w, knots, syn, err, shot0, dtype, gseed):
+    import torch
+    tw = torch.tensor(w, dtype=dtype, device="cuda")
+    tk = torch.tensor(knots, dtype=dtype, device="cuda")
+    ts = torch.from_numpy(syn.view(np.int32)).cuda()
+    te = torch.from_numpy(err.view(np.int32)).cuda()
+    shots = syn.shape[0]
+    prec = R._prec(dtype)
+    tape = torch.empty(R.relaybp_learned_tape_bytes(h, prec, w.shape[0], shots), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(shots, dtype=torch.float64, device="cuda")
+    R.relaybp_learned_forward(h, tw, tk, gseed, ts, te, shot0, shots, tape, loss)
+    gw = torch.zeros_like(tw)
+    gk = torch.zeros_like(tk)
+    R.relaybp_learned_backward(h, tw, tk, gseed, te, shot0, shots, tape, 1.0, gw, gk)
+    torch.cuda.synchronize()
+    return loss.cpu().numpy(), gw.cpu().numpy().astype(np.float64), gk.cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def small_dem():
+    return circuit_dem("ZSZ-LP-60", 0.004, 2, "Z")
+
+
+def test_forward_loss_matches_oracle(small_dem):
+    import torch
+    dem = small_dem
+    for dtype, T, tol in ((torch.float64, 8, 1e-10), (torch.float32, 3, 1e-4)):
+        R, h, w, knots = _setup(dem, T, 1, dtype)
+        syn, _, err = oracle.sample(dem, 3, 100, 24, want_errors=True)
+        lo, _ = oracle.learned_loss(dem, w, knots, 9, syn, err, shot0=100)
+        lg, _, _ = _gpu_loss_grad(R, h, w, knots, syn, err, 100, dtype, 9)
+        assert np.allclose(lg, lo, rtol=tol, atol=tol), (dtype, np.abs(lg - lo).max())
+        R.relaybp_destroy(h)
+
+
+def test_gradients_match_finite_differences(small_dem):
+    import torch
+    dem = small_dem
+    T = 6
+    R, h, w, knots = _setup(dem, T, 2, torch.float64)
+    syn, _, err = oracle.sample(dem, 4, 0, 16, want_errors=True)
+    _, gw, gk = _gpu_loss_grad(R, h, w, knots, syn, err, 0, torch.float64, 11)
+
+    def L(wv, kv):
+        return oracle.learned_loss(dem, wv, kv, 11, syn, err)[0].sum()
+
+    def fd(fun, x, idx, hh):
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += hh
+        xm[idx] -= hh
+        return (fun(xp) - fun(xm)) / (2 * hh)
+
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(40):
+        t, e = int(rng.integers(T)), int(rng.integers(dem.n_edges))
+        f1 = fd(lambda x: L(x, knots), w, (t, e), 1e-6)
+        f2 = fd(lambda x: L(x, knots), w, (t, e), 5e-7)
+        if abs(f1 - f2) > 1e-6 * max(1.0, abs(f1)):
+            continue
+        assert abs(gw[t, e] - f1) <= 1e-5 * max(1.0, abs(f1)), (t, e, gw[t, e], f1)
+        checked += 1
+    assert checked >= 30
+    kchecked = 0
+    for k in range(knots.size):
+        f1 = fd(lambda x: L(w, x), knots, k, 1e-7)
+        f2 = fd(lambda x: L(w, x), knots, k, 5e-8)
+        if abs(f1 - f2) > 1e-5 * max(1.0, abs(f1)):
+            continue
+        assert abs(gk[k] - f1) <= 1e-4 * max(1.0, abs(f1)), (k, gk[k], f1)
+        kchecked += 1
+    assert kchecked >= 12
+    R.relaybp_destroy(h)
+
+
+def test_training_reduces_loss():
+    """A short Adam run on self-sampled shots lowers the loss of a held-out batch."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from paper_2607_27644_b300.learned import LearnedParams
+    dem = circuit_dem("ZSZ-LP-160", 0.002, 10, "Z")
+    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", num_sets=1))
+    T, B = 10, 256
+    model = LearnedParams(T, dem.n_edges, -0.15, 0.61)
+    opt = torch.optim.Adam(model.parameters(), lr=0.01)
+
+    def batch(shot0):
+        syn = torch.zeros((B, h.wc), dtype=torch.int32, device="cuda")
+        err = torch.zeros((B, h.wv), dtype=torch.int32, device="cuda")
+        R.relaybp_sample(h, 4, shot0, B, syn, None, err)
+        return syn, err
+
+    vs, ve = batch(10**9)
+    with torch.no_grad():
+        before = float(model.loss(h, vs, ve, 10**9, 77))
+    for step in range(40):
+        s, e = batch(step * B)
+        opt.zero_grad()
+        loss = model.loss(h, s, e, step * B, 77)
+        loss.backward()
+        opt.step()
+    with torch.no_grad():
+        after = float(model.loss(h, vs, ve, 10**9, 77))
+    assert after < before
+    k = model.knots().detach().cpu().numpy()
+    assert np.all(np.diff(k) >= 0)
+    R.relaybp_destroy(h)

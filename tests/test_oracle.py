@@ -338,3 +338,34 @@ def test_learned_forward_closed_form_two_variables():
     err = pack_bits(np.array([[1, 0]]))
     loss, tr = oracle.learned_loss(D, w, knots, seed, syn, err, shot0=shot, trace=True)
     assert np.allclose(tr[0], np.array(want), rtol=1e-12, atol=1e-12)
+
+
+def test_learned_decode_leg0_matches_training_forward():
+    """Leg 0 of the learned decode (weights by iteration, gamma0 = g) equals the
+    training forward with constant knots g, which is pinned above."""
+    D = circuit_dem("ZSZ-LP-60", 0.004, 3, "Z")
+    Hx = np.vstack([D.dense_H(), np.zeros((1, D.n_loc), dtype=np.uint8)])
+    Dx = dem_from_dense(Hx, D.priors)
+    syn, _, err = oracle.sample(D, 22, 0, 5, want_errors=True)
+    synx = pack_bits(np.hstack([unpack_bits(syn, D.n_det), np.ones((5, 1), dtype=np.uint8)]))
+    T, g = 6, 0.2
+    w = np.random.default_rng(8).uniform(0.7, 1.3, (T, Dx.n_edges))
+    _, tr = oracle.learned_loss(Dx, w, np.full(17, g), 5, synx, err, trace=True)
+    P = DecodeParams(gamma0=g, pre_iter=T, num_sets=0, max_iterations=1, stop_nconv=1)
+    r = oracle.decode(Dx, P, synx, trace_iters=T, w=w, knots=np.full(17, 0.4))
+    assert np.array_equal(tr, r["trace"])
+
+
+def test_learned_decode_unit_weights_is_plain():
+    D = circuit_dem("ZSZ-LP-60", 0.004, 3, "Z")
+    syn, _, _ = oracle.sample(D, 23, 0, 40)
+    P = DecodeParams(num_sets=8, seed=3)
+    a = oracle.decode(D, P, syn)
+    b = oracle.decode(D, P, syn, w=np.ones((5, D.n_edges)))
+    assert np.array_equal(a["corrections"], b["corrections"]) and np.array_equal(a["stats"], b["stats"])
+    Hd = D.dense_H().astype(np.int64)
+    c = oracle.decode(D, P, syn, w=np.random.default_rng(2).uniform(0.8, 1.0, (5, D.n_edges)),
+                      knots=np.linspace(-0.1, 0.5, 17))
+    eh = unpack_bits(c["corrections"], D.n_loc).astype(np.int64)
+    conv = c["stats"][:, 0] == 1
+    assert np.array_equal((eh[conv] @ Hd.T) % 2, unpack_bits(syn, D.n_det)[conv])
