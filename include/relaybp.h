@@ -113,6 +113,16 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
 /* Replace the decoder parameters of an existing handle (validated as above). */
 int relaybp_set_params(relaybp_handle *h, const relaybp_params *params);
 
+/* Attach learned parameters to a handle for decoding (the learned form of
+ * this library; no counterpart in the paper).  d_w [T][E] FP32 message weights
+ * indexed by the iteration within each leg (iterations past T use the last),
+ * d_knots [K+1] FP32 nondecreasing memory-strength inverse CDF for legs >= 1
+ * (same meaning as in relaybp_learned_forward; u from stream 1 of the leg).
+ * Either may be NULL (NULL and NULL restore the plain method).  Device
+ * pointers stay owned by the caller and must outlive the decodes that use
+ * them.  Needs msg_dtype F32, F16 or BF16 and carry_messages = 0. */
+int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const float *d_knots, int32_t K);
+
 /* Query sizes: n_det (C), n_loc (V), n_obs (K), n_edges (nnz of H). */
 int relaybp_sizes(const relaybp_handle *h, int32_t *n_det, int32_t *n_loc, int32_t *n_obs, int64_t *n_edges);
 

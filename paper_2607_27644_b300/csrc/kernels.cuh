@@ -55,6 +55,12 @@ struct DecodeParamsDev {
     int32_t pre_iter, num_sets, max_iterations, stop_nconv;
     int32_t stop_all, carry_messages;
     uint64_t seed;
+    // learned form (NULL: plain method): message weights [lT][E] indexed by
+    // the iteration within the leg (past lT: the last), memory-strength
+    // inverse-CDF knots [lK+1] for legs >= 1
+    const float *lw;
+    const float *lknots;
+    int32_t lT, lK;
 };
 
 struct StatsDev {               // mirrors relaybp_shot_stats
@@ -185,9 +191,9 @@ constexpr uint32_t COL_SENTINEL = 0xffffffffu;
 // owns one 16-bit word of sign bits, bit b = sign of mu at position b*L + l.
 // The sign bit of position pos of row i therefore lives in halfword
 // i*L + pos % L, bit pos / L.
-template <typename S, int L, int NB>
+template <typename S, int L, int NB, bool LW>
 __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState<S> *cs, uint16_t *sgnh,
-                                         const uint32_t *syn, int warp, int nwarp, int lane)
+                                         const uint32_t *syn, int warp, int nwarp, int lane, const float *wprev)
 {
     static_assert(32 % L == 0 && NB <= 16, "row geometry");
     using C = typename Prec<S>::C;
@@ -225,7 +231,8 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
         for (int b = 0; b < NB; ++b) {
             if (idx[b] >= 0) {
                 const uint32_t k = (uint32_t)(b * L + l);
-                const C mag = (k == oarg) ? om2 : om1;
+                C mag = (k == oarg) ? om2 : om1;
+                if (LW) mag *= (C)__ldg(wprev + e0 + (int)k);
                 const C nu_old = (((oldbits >> b) & 1u) ^ opar) ? -mag : mag;
                 const C m = Prec<S>::ld(A[idx[b]]) - nu_old;
                 newbits |= ((m < (C)0) ? 1u : 0u) << b;
@@ -290,7 +297,7 @@ struct JobTable {
 // S: storage precision; L, NB: row geometry (for the longest row of any job);
 // GS: per-shot state in a per-block region of global memory (gstate,
 // state_stride bytes per block, L2-resident) instead of shared memory.
-template <typename S, int L, int NB, bool GS>
+template <typename S, int L, int NB, bool GS, bool LW>
 __global__ void __launch_bounds__(512)
 relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__restrict__ work,
                     typename Prec<S>::C *__restrict__ gamma_scratch, int vmax,
@@ -377,7 +384,19 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                 // a6: new leg -- fresh strengths, marginals carried over
                 for (int j = tid; j < V; j += nthr) {
                     const C l0 = Num<C>::l0(g, j);
-                    const C gn = draw_gamma<C>(p, shot, leg, j, V);
+                    C gn;
+                    if (LW && p.lknots) {
+                        const uint32_t nblk = (uint32_t)((V + 3) / 4);
+                        const uint4 rr = philox_block(p.seed, shot, 1u, (uint32_t)leg * nblk + (uint32_t)(j >> 2));
+                        const C u = (C)(uint4_word(rr, j & 3) >> 8) * (C)(1.0 / 16777216.0);
+                        const C x = u * (C)p.lK;
+                        int kk = (int)floor((double)x);
+                        if (kk >= p.lK) kk = p.lK - 1;
+                        const C lo = (C)__ldg(p.lknots + kk), hi = (C)__ldg(p.lknots + kk + 1);
+                        gn = lo + (hi - lo) * (x - (C)kk);
+                    } else {
+                        gn = draw_gamma<C>(p, shot, leg, j, V);
+                    }
                     const C Mj = Prec<S>::ld(M[j]);
                     C carry = (C)0;
                     if (p.carry_messages) {
@@ -401,7 +420,13 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             bool conv = false;
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: check rows, L lanes per row ---------------------------
-                row_pass<S, L, NB>(g, A, cs, sgnh, syn, warp, nwarp, lane);
+                const float *wprev = nullptr, *wcur = nullptr;
+                if (LW && p.lw) {
+                    wprev = p.lw + (int64_t)min(t > 0 ? t - 1 : 0, p.lT - 1) * g.E;
+                    wcur = p.lw + (int64_t)min(t, p.lT - 1) * g.E;
+                }
+                if (LW && p.lw) row_pass<S, L, NB, true>(g, A, cs, sgnh, syn, warp, nwarp, lane, wprev);
+                else row_pass<S, L, NB, false>(g, A, cs, sgnh, syn, warp, nwarp, lane, nullptr);
                 __syncthreads();
                 // ---- a4: variables, one lane per variable, ELL slices --------
                 for (int G = warp; G < NG; G += nwarp) {
@@ -411,16 +436,18 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     const C gm = act ? gam[j] : (C)0;
                     const int D = __ldg(g.gdeg + G);
                     const uint32_t *col = g.cinfo + __ldg(g.goff + G) + lane;
+                    const uint32_t *cel = g.cedge_ell + __ldg(g.goff + G) + lane;
                     C Ssum = (C)0;
                     // column messages nu_ij rebuilt from the check states; four
                     // independent slots per step, the remainder one by one (D is
                     // uniform over the warp, so the split does not diverge)
-                    auto msg = [&](uint32_t c) -> C {
+                    auto msg = [&](uint32_t c, int slot) -> C {
                         const uint32_t i = c >> 12;
                         const CheckState<S> q = cs[i];
                         const uint32_t pos = c & 0xfffu;
                         const uint32_t hw = sgnh[i * L + (pos % L)];
-                        const C mag = Prec<S>::ld((pos == (q.meta & 0xfffu)) ? q.m2 : q.m1);
+                        C mag = Prec<S>::ld((pos == (q.meta & 0xfffu)) ? q.m2 : q.m1);
+                        if (LW && wcur) mag *= (C)__ldg(wcur + __ldg(cel + slot * 32));
                         const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
                         return sb ? -mag : mag;
                     };
@@ -431,11 +458,11 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                         for (int u = 0; u < 4; ++u) c[u] = __ldg(col + (k + u) * 32);
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (c[u] != COL_SENTINEL) Ssum += msg(c[u]);
+                            if (c[u] != COL_SENTINEL) Ssum += msg(c[u], k + u);
                     }
                     for (; k < D; ++k) {
                         const uint32_t c = __ldg(col + k * 32);
-                        if (c != COL_SENTINEL) Ssum += msg(c);
+                        if (c != COL_SENTINEL) Ssum += msg(c, k);
                     }
                     uint32_t dec = 0u;
                     if (act) {

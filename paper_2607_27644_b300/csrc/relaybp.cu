@@ -75,6 +75,8 @@ struct relaybp_handle {
     int64_t launches = 0;
     int max_row_deg = 0;
     // learned-form training scratch: work counter and one gradient row per block
+    const float *lw = nullptr, *lknots = nullptr;     // learned inference parameters (caller-owned)
+    int lT = 0, lK = 0;
     unsigned long long *d_lwork = nullptr;
     void *d_lgbar = nullptr;
     size_t lgbar_bytes = 0;
@@ -305,6 +307,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
     if (n < 1 || n > kMaxJobs) return fail(RELAYBP_ERR_INVALID, "%d DEMs in one launch (1..%d)", n, kMaxJobs);
     const int device = hs[0]->device, num_sms = hs[0]->num_sms;
     JobTable tab{};
+    bool learned = false;
     int plan_max = 0, vmax = 0, threads = 64;
     int64_t total = 0;
     for (int d = 0; d < n; ++d) {
@@ -312,6 +315,11 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         DecodeJob &J = tab.job[d];
         J.g = h->dem;
         J.p = dev_params(h->params);
+        J.p.lw = h->lw;
+        J.p.lknots = h->lknots;
+        J.p.lT = h->lT;
+        J.p.lK = h->lK;
+        if (h->lw || h->lknots) learned = true;
         J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), L);
         J.syn_in = io[d].syn;
         J.shot0 = io[d].shot0;
@@ -341,7 +349,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
                     plan_max, maxsm);
     int64_t resident = num_sms;
     if (!gs) {
-        auto kern = relay_decode_kernel<S, L, NB, false>;
+        auto kern = learned ? relay_decode_kernel<S, L, NB, false, true> : relay_decode_kernel<S, L, NB, false, false>;
         CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan_max));
         int per_sm = 0;
         CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan_max));
@@ -354,11 +362,17 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
     const size_t gamma_need = (size_t)(sc.fixed ? blocks : resident) * vmax * sizeof(C);
     if (int rc = scratch_reserve(sc, gamma_need, gs ? (size_t)resident * stride : 0)) return rc;
     CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
-    if (!gs)
-        relay_decode_kernel<S, L, NB, false><<<(unsigned)blocks, threads, plan_max, st>>>(
+    if (!gs && !learned)
+        relay_decode_kernel<S, L, NB, false, false><<<(unsigned)blocks, threads, plan_max, st>>>(
             tab, sc.work, static_cast<C *>(sc.gamma), vmax, nullptr, 0);
+    else if (!gs)
+        relay_decode_kernel<S, L, NB, false, true><<<(unsigned)blocks, threads, plan_max, st>>>(
+            tab, sc.work, static_cast<C *>(sc.gamma), vmax, nullptr, 0);
+    else if (!learned)
+        relay_decode_kernel<S, L, NB, true, false><<<(unsigned)blocks, threads, 0, st>>>(
+            tab, sc.work, static_cast<C *>(sc.gamma), vmax, sc.gstate, stride);
     else
-        relay_decode_kernel<S, L, NB, true><<<(unsigned)blocks, threads, 0, st>>>(
+        relay_decode_kernel<S, L, NB, true, true><<<(unsigned)blocks, threads, 0, st>>>(
             tab, sc.work, static_cast<C *>(sc.gamma), vmax, sc.gstate, stride);
     CUDA_TRY(cudaGetLastError());
     return 0;
@@ -399,7 +413,7 @@ int launch_jobs_dtype(relaybp_handle *const *hs, const JobIO *io, int n, Scratch
 // Single-DEM decode: the literal-order FP64 kernel when it applies, else one job.
 int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, bool on_chip_only)
 {
-    if (h->params.msg_dtype == RELAYBP_MSG_F64) {
+    if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots) {
         int rc = launch_decode_exact(h, sc, io, st);
         if (rc <= 0) return rc;
     }
@@ -716,6 +730,23 @@ int relaybp_set_params(relaybp_handle *h, const relaybp_params *params)
     if (int rc = check_params(params)) return rc;
     if (int rc = check_legs(params, h->dem.V)) return rc;
     h->params = *params;
+    return 0;
+}
+
+int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const float *d_knots, int32_t K)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if ((d_w && T < 1) || (d_knots && (K < 1 || K > 64)))
+        return fail(RELAYBP_ERR_INVALID, "need T >= 1 with weights and 1 <= K <= 64 with knots");
+    if ((d_w || d_knots) && h->params.msg_dtype == RELAYBP_MSG_F64)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned decoding runs with FP32 arithmetic (msg_dtype F32/F16/BF16)");
+    if (d_w && h->params.carry_messages)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned weights with carry_messages are not supported");
+    h->lw = d_w;
+    h->lT = d_w ? T : 0;
+    h->lknots = d_knots;
+    h->lK = d_knots ? K : 0;
     return 0;
 }
 

@@ -50,6 +50,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_build": ([ctypes.POINTER(relaybp_csr), P, ctypes.POINTER(relaybp_csr),
                            ctypes.POINTER(relaybp_params), ctypes.POINTER(P)], ctypes.c_int),
         "relaybp_set_params": ([P, ctypes.POINTER(relaybp_params)], ctypes.c_int),
+        "relaybp_set_learned": ([P, P, I32, P, I32], ctypes.c_int),
         "relaybp_sizes": ([P, P, P, P, P], ctypes.c_int),
         "relaybp_sample": ([P, U64, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_batch": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
@@ -79,7 +80,7 @@ def _load() -> ctypes.CDLL:
 
 _lib = _load()
 
-EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
+EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
@@ -192,6 +193,15 @@ def relaybp_sizes(h: Handle) -> tuple[int, int, int, int]:
 def relaybp_set_params(h: Handle, params: Params):
     cp = params.c()
     _check(_lib.relaybp_set_params(h.ptr, ctypes.byref(cp)), "relaybp_set_params")
+
+
+def relaybp_set_learned(h: Handle, d_w=None, d_knots=None):
+    """Attach FP32 learned weights [T, E] and knots [K+1] (device tensors the
+    caller keeps alive); None, None restores the plain method."""
+    T = 0 if d_w is None else d_w.shape[0]
+    K = 0 if d_knots is None else d_knots.shape[0] - 1
+    _check(_lib.relaybp_set_learned(h.ptr, _ptr(d_w), T, _ptr(d_knots), K), "relaybp_set_learned")
+    h._keep = [d_w, d_knots]
 
 
 def relaybp_sample(h: Handle, seed: int, shot0: int, shots: int, d_syndromes, d_obs=None, d_errors=None,

@@ -129,3 +129,49 @@ def test_training_reduces_loss():
     k = model.knots().detach().cpu().numpy()
     assert np.all(np.diff(k) >= 0)
     R.relaybp_destroy(h)
+
+
+def test_learned_decode_unit_weights_equal_plain():
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode
+    dem = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+    p = R.Params(msg_dtype="f32", num_sets=100, gamma_min=-0.15, gamma_max=0.61, seed=3)
+    h = R.relaybp_build_dem(dem, p)
+    syn, _, _ = oracle.sample(dem, 5, 0, 600)
+    plain = gpu_decode(h, syn)
+    w = torch.ones((7, dem.n_edges), dtype=torch.float32, device="cuda")
+    R.relaybp_set_learned(h, w, None)
+    ones = gpu_decode(h, syn)
+    for k in ("corrections", "pred_obs", "stats", "weights"):
+        assert np.array_equal(plain[k], ones[k]), k
+    R.relaybp_destroy(h)
+
+
+def test_learned_decode_matches_oracle():
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode
+    dem = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+    kw = dict(num_sets=100, gamma_min=-0.15, gamma_max=0.61, seed=4)
+    rng = np.random.default_rng(6)
+    T = 8
+    w = rng.uniform(0.75, 1.0, (T, dem.n_edges))
+    knots = np.cumsum(np.r_[-0.15, rng.uniform(0.02, 0.07, 16)])
+    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **kw))
+    tw = torch.tensor(w, dtype=torch.float32, device="cuda")
+    tk = torch.tensor(knots, dtype=torch.float32, device="cuda")
+    R.relaybp_set_learned(h, tw, tk)
+    syn, obs, _ = oracle.sample(dem, 6, 0, 300)
+    rg = gpu_decode(h, syn)
+    ro = oracle.decode(dem, oracle.DecodeParams(**kw), syn, w=w.astype(np.float32).astype(np.float64),
+                       knots=knots.astype(np.float32).astype(np.float64))
+    Hd = dem.dense_H().astype(np.int64)
+    S = unpack_bits(syn, dem.n_det)
+    for r in (ro, rg):
+        eh = unpack_bits(r["corrections"], dem.n_loc).astype(np.int64)
+        conv = r["stats"][:, 0] == 1
+        assert np.array_equal((eh[conv] @ Hd.T) % 2, S[conv])
+    same = np.all(ro["pred_obs"][:, :rg["pred_obs"].shape[1]] == rg["pred_obs"], axis=1)
+    assert (~same).sum() <= 0
+    R.relaybp_destroy(h)
