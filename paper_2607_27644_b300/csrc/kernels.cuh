@@ -122,6 +122,19 @@ __global__ void sample_kernel(DevDEM g, uint64_t seed, uint64_t shot0, int64_t s
 // ---------------------------------------------------------------------------
 // a3-a8: Relay-BP, one thread block per shot, persistent over the batch.
 // ---------------------------------------------------------------------------
+// Explicitly rounded products and sums: no FMA contraction, so every kernel
+// variant (plain or learned, shared or global state, any launch) evaluates
+// the memory term and the weighted messages with identical rounding.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+// memory-biased prior (1 - g) L0 + g M
+template <typename C> __device__ __forceinline__ C memprior(C g, C l0, C m)
+{
+    return add_rn(mul_rn(add_rn((C)1, -g), l0), mul_rn(g, m));
+}
+
 template <typename T> __device__ __forceinline__ T vmin(T a, T b) { return b < a ? b : a; }
 template <typename T> __device__ __forceinline__ T vabs(T a) { return a < (T)0 ? -a : a; }
 
@@ -232,9 +245,9 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             if (idx[b] >= 0) {
                 const uint32_t k = (uint32_t)(b * L + l);
                 C mag = (k == oarg) ? om2 : om1;
-                if (LW) mag *= (C)__ldg(wprev + e0 + (int)k);
+                if (LW) mag = mul_rn(mag, (C)__ldg(wprev + e0 + (int)k));
                 const C nu_old = (((oldbits >> b) & 1u) ^ opar) ? -mag : mag;
-                const C m = Prec<S>::ld(A[idx[b]]) - nu_old;
+                const C m = add_rn(Prec<S>::ld(A[idx[b]]), -nu_old);
                 newbits |= ((m < (C)0) ? 1u : 0u) << b;
                 const C a = vabs(m);
                 if (a < b1) { b2 = b1; b1 = a; bi = k; }
@@ -361,7 +374,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             const C gm = (C)p.gamma0;
             M[j] = Prec<S>::st(l0);
             gam[j] = gm;
-            A[j] = Prec<S>::st(((C)1 - gm) * l0 + gm * l0);
+            A[j] = Prec<S>::st(memprior<C>(gm, l0, l0));
         }
         for (int i = tid; i < Cn; i += nthr) {
             CheckState<S> z;
@@ -401,10 +414,10 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     C carry = (C)0;
                     if (p.carry_messages) {
                         const C go = gam[j];
-                        carry = Prec<S>::ld(A[j]) - (((C)1 - go) * l0 + go * Mj);
+                        carry = add_rn(Prec<S>::ld(A[j]), -memprior<C>(go, l0, Mj));
                     }
                     gam[j] = gn;
-                    A[j] = Prec<S>::st(((C)1 - gn) * l0 + gn * Mj + carry);
+                    A[j] = Prec<S>::st(add_rn(memprior<C>(gn, l0, Mj), carry));
                 }
                 if (!p.carry_messages) {
                     for (int i = tid; i < Cn; i += nthr) {
@@ -447,7 +460,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                         const uint32_t pos = c & 0xfffu;
                         const uint32_t hw = sgnh[i * L + (pos % L)];
                         C mag = Prec<S>::ld((pos == (q.meta & 0xfffu)) ? q.m2 : q.m1);
-                        if (LW && wcur) mag *= (C)__ldg(wcur + __ldg(cel + slot * 32));
+                        if (LW && wcur) mag = mul_rn(mag, (C)__ldg(wcur + __ldg(cel + slot * 32)));
                         const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
                         return sb ? -mag : mag;
                     };
@@ -458,17 +471,17 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                         for (int u = 0; u < 4; ++u) c[u] = __ldg(col + (k + u) * 32);
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (c[u] != COL_SENTINEL) Ssum += msg(c[u], k + u);
+                            if (c[u] != COL_SENTINEL) Ssum = add_rn(Ssum, msg(c[u], k + u));
                     }
                     for (; k < D; ++k) {
                         const uint32_t c = __ldg(col + k * 32);
-                        if (c != COL_SENTINEL) Ssum += msg(c, k);
+                        if (c != COL_SENTINEL) Ssum = add_rn(Ssum, msg(c, k));
                     }
                     uint32_t dec = 0u;
                     if (act) {
-                        const C Mn = ((C)1 - gm) * l0 + gm * Prec<S>::ld(M[j]) + Ssum;
+                        const C Mn = add_rn(memprior<C>(gm, l0, Prec<S>::ld(M[j])), Ssum);
                         M[j] = Prec<S>::st(Mn);
-                        A[j] = Prec<S>::st(((C)1 - gm) * l0 + gm * Mn + Ssum);
+                        A[j] = Prec<S>::st(add_rn(memprior<C>(gm, l0, Mn), Ssum));
                         dec = (Mn < (C)0) ? 1u : 0u;
                         if (trace && iters < trace_iters)
                             trace[((int64_t)sidx * trace_iters + iters) * V + j] = (double)Mn;
