@@ -46,8 +46,10 @@ def _args():
     ap.add_argument("--cpu-sample", type=int, default=96, help="shots of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="zsz160", choices=["zsz160", "mixed"],
-                    help="zsz160: the headline workload; mixed: nine DEMs in one persistent launch")
+    ap.add_argument("--workload", default="zsz160", choices=["zsz160", "mixed", "learned"],
+                    help="zsz160: the headline workload; mixed: nine DEMs in one persistent launch; "
+                         "learned: train, then learned vs plain Relay-BP at equal LER")
+    ap.add_argument("--train-steps", type=int, default=300, help="learned: Adam steps of 512 shots at p=0.2%%")
     ap.add_argument("--mixed-base", type=int, default=2000, help="mixed: shots per unit of the 2:5:10 mix")
     ap.add_argument("--msg", default="f16", choices=["f16", "bf16", "f32"], help="mixed: message storage")
     return ap.parse_args()
@@ -416,12 +418,132 @@ def run_mixed(a):
         R.relaybp_destroy(h)
 
 
+def run_learned(a):
+    """Learned Relay-BP (trained on self-sampled shots at p = 0.2%) against
+    plain Relay-BP (paper settings, FP32) on the same fresh shots at p = 0.1%.
+
+    Learned decoder: BF16 messages, learned message weights (T = 30) and
+    memory-strength distribution, stop after the first solution; shots it
+    leaves unconverged are re-decoded by plain Relay-BP (the fallback).  An
+    ablation runs plain Relay-BP with the same stop-after-one rule."""
+    import numpy as np
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from paper_2607_27644_b300.learned import LearnedParams
+    from paper_2607_27644_b300.stats import agree_within
+    from workloads.dem import circuit_dems
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    d_inf, d_train = circuit_dems(WORKLOAD["code"], [0.001, 0.002], WORKLOAD["rounds"], WORKLOAD["basis"])
+    E = d_inf.n_edges
+    T, BT = 30, 512
+    # ---- training (untimed) ---------------------------------------------------
+    ht = R.relaybp_build_dem(d_train, R.Params(msg_dtype="f32", **DECODER))
+    model = LearnedParams(T, E, DECODER["gamma_min"], DECODER["gamma_max"], device=dev)
+    opt = torch.optim.Adam(model.parameters(), lr=3e-3)
+    syn_t = torch.empty((BT, ht.wc), dtype=torch.int32, device=dev)
+    err_t = torch.empty((BT, ht.wv), dtype=torch.int32, device=dev)
+    t0 = time.perf_counter()
+    hist = []
+    for k in range(a.train_steps):
+        R.relaybp_sample(ht, 4, k * BT, BT, syn_t, None, err_t)
+        opt.zero_grad()
+        loss = model.loss(ht, syn_t, err_t, k * BT, 0x5EED)
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            model.w.clamp_(0.0, 2.0)
+        if k % max(1, a.train_steps // 10) == 0 or k == a.train_steps - 1:
+            hist.append(round(float(loss), 3))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    w = model.w.detach().float().contiguous()
+    knots = model.knots().detach().float().contiguous()
+    # ---- decoders ----------------------------------------------------------------
+    learned_params = dict(DECODER, stop_nconv=1)
+    hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="bf16", **learned_params))
+    R.relaybp_set_learned(hl, w, knots)
+    hp = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **DECODER))
+    ha = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1)))
+    hf = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, seed=DECODER["seed"] + 1)))
+    B, K, W = a.batch, a.steps, a.warmup
+    st = torch.cuda.Stream(device=dev)
+    syn = torch.empty((B, hp.wc), dtype=torch.int32, device=dev)
+    obs = torch.empty((B, hp.wk), dtype=torch.int32, device=dev)
+    pobs = torch.empty((B, hp.wk), dtype=torch.int32, device=dev)
+    stats = torch.empty((B, 6), dtype=torch.int32, device=dev)
+
+    def run(kind, k, counters):
+        s0 = 5 * 10**8 + k * B
+        R.relaybp_sample(hp, SAMPLE_SEED, s0, B, syn, obs, None, st)
+        h = {"plain": hp, "learned": hl, "ablation": ha}[kind]
+        R.relaybp_decode_batch(h, syn, s0, B, None, pobs, stats, st)
+        nfb = 0
+        if kind == "learned":
+            idx = torch.nonzero(stats[:, 0] == 0).flatten()
+            nfb = int(idx.numel())
+            if nfb:
+                sf = syn.index_select(0, idx).contiguous()
+                pf = torch.empty((nfb, hp.wk), dtype=torch.int32, device=dev)
+                stf = torch.empty((nfb, 6), dtype=torch.int32, device=dev)
+                R.relaybp_decode_batch(hf, sf, s0, nfb, None, pf, stf, st)
+                pobs.index_copy_(0, idx, pf)
+                stats.index_copy_(0, idx, stf)
+        R.relaybp_count_failures(hp, pobs, obs, stats, B, counters, st)
+        it = int(stats[:, 3].sum())
+        return nfb, it
+
+    out = {}
+    with torch.cuda.stream(st):
+        for kind in ("plain", "learned", "ablation"):
+            cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+            for w_ in range(W):
+                run(kind, K + w_, cnt)
+            torch.cuda.synchronize()
+            cnt.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fb = iters = 0
+            with ClockSampler(local) as clk:
+                e0.record(st)
+                for k in range(K):
+                    f, i = run(kind, k, cnt)
+                    fb += f
+                    iters += i
+                e1.record(st)
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            c = cnt.cpu().tolist()
+            out[kind] = {"shots_per_s": B * K / (ms / 1e3), "ms_per_step": ms / K, "shots": c[0], "failures": c[3],
+                         "nonconverged": c[1], "logical": c[2], "block_ler": c[3] / max(1, c[0]),
+                         "mean_iterations": iters / (B * K), "fallback_shots": fb, "clocks": clk.summary()}
+    lp, ll = out["plain"], out["learned"]
+    equal = agree_within(ll["failures"], ll["shots"], lp["failures"], lp["shots"])
+    line = {"metric": METRIC, "value": ll["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": ll["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEMs",
+            "config": {"workload": "learned vs plain Relay-BP, ZSZ-LP-160 d=10, inference p=0.001, training p=0.002",
+                       "train": {"steps": a.train_steps, "batch": BT, "unrolled_iterations": T, "optimizer": "Adam 3e-3",
+                                 "seconds": train_s, "loss_history": hist},
+                       "learned_decoder": "BF16 messages, learned weights + knots, stop_nconv=1, plain fallback",
+                       "plain_decoder": "FP32, paper settings (stop_nconv=5)", "shots_per_step": B},
+            "plain": lp, "learned": ll, "ablation_plain_stop1": out["ablation"],
+            "speedup_vs_plain": ll["shots_per_s"] / lp["shots_per_s"], "equal_ler_2sigma": bool(equal),
+            "clocks": ll["clocks"]}
+    print(json.dumps(line), flush=True)
+    for x in (ht, hl, hp, ha, hf):
+        R.relaybp_destroy(x)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "mixed":
         run_mixed(a)
+    elif a.workload == "learned":
+        run_learned(a)
     else:
         run_ours(a)
 
