@@ -461,63 +461,75 @@ def run_learned(a):
     train_s = time.perf_counter() - t0
     w = model.w.detach().float().contiguous()
     knots = model.knots().detach().float().contiguous()
-    # ---- decoders ----------------------------------------------------------------
+    # ---- decoders: two streams, one handle set per stream ------------------------
+    NS, FCAP = 2, 32
     learned_params = dict(DECODER, stop_nconv=1)
-    hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="bf16", **learned_params))
-    R.relaybp_set_learned(hl, w, knots)
-    hp = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **DECODER))
-    ha = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1)))
-    hf = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, seed=DECODER["seed"] + 1)))
     B, K, W = a.batch, a.steps, a.warmup
-    st = torch.cuda.Stream(device=dev)
-    syn = torch.empty((B, hp.wc), dtype=torch.int32, device=dev)
-    obs = torch.empty((B, hp.wk), dtype=torch.int32, device=dev)
-    pobs = torch.empty((B, hp.wk), dtype=torch.int32, device=dev)
-    stats = torch.empty((B, 6), dtype=torch.int32, device=dev)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
+    H = []
+    for q in range(NS):
+        hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="bf16", **learned_params))
+        R.relaybp_set_learned(hl, w, knots)
+        H.append({"learned": hl,
+                  "plain": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **DECODER)),
+                  "ablation": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1))),
+                  "fallback": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32",
+                                                                  **dict(DECODER, seed=DECODER["seed"] + 1)))})
+    hp = H[0]["plain"]
+    bufs = [dict(syn=torch.empty((B, hp.wc), dtype=torch.int32, device=dev),
+                 obs=torch.empty((B, hp.wk), dtype=torch.int32, device=dev),
+                 pobs=torch.empty((B, hp.wk), dtype=torch.int32, device=dev),
+                 stats=torch.empty((B, 6), dtype=torch.int32, device=dev),
+                 fp=torch.empty((FCAP, hp.wk), dtype=torch.int32, device=dev),
+                 fs=torch.empty((FCAP, 6), dtype=torch.int32, device=dev)) for _ in range(NS)]
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
 
-    def run(kind, k, counters):
+    def step(kind, k, cnt, it):
+        q = k % NS
+        st_, b_, h_ = streams[q], bufs[q], H[q]
         s0 = 5 * 10**8 + k * B
-        R.relaybp_sample(hp, SAMPLE_SEED, s0, B, syn, obs, None, st)
-        h = {"plain": hp, "learned": hl, "ablation": ha}[kind]
-        R.relaybp_decode_batch(h, syn, s0, B, None, pobs, stats, st)
-        nfb = 0
-        if kind == "learned":
-            idx = torch.nonzero(stats[:, 0] == 0).flatten()
-            nfb = int(idx.numel())
-            if nfb:
-                sf = syn.index_select(0, idx).contiguous()
-                pf = torch.empty((nfb, hp.wk), dtype=torch.int32, device=dev)
-                stf = torch.empty((nfb, 6), dtype=torch.int32, device=dev)
-                R.relaybp_decode_batch(hf, sf, s0, nfb, None, pf, stf, st)
-                pobs.index_copy_(0, idx, pf)
-                stats.index_copy_(0, idx, stf)
-        R.relaybp_count_failures(hp, pobs, obs, stats, B, counters, st)
-        it = int(stats[:, 3].sum())
-        return nfb, it
+        with torch.cuda.stream(st_):
+            flush.fill_(k)
+            R.relaybp_sample(h_["plain"], SAMPLE_SEED, s0, B, b_["syn"], b_["obs"], None, st_)
+            R.relaybp_decode_batch(h_[kind], b_["syn"], s0, B, None, b_["pobs"], b_["stats"], st_)
+            if kind == "learned":
+                # fallback without a host round trip: the FCAP lowest-ranked shots
+                # (unconverged first) are re-decoded by plain Relay-BP and kept
+                # where the learned decoder did not converge
+                fidx = torch.argsort(b_["stats"][:, 0], stable=True)[:FCAP]
+                sf = b_["syn"].index_select(0, fidx).contiguous()
+                R.relaybp_decode_batch(h_["fallback"], sf, s0, FCAP, None, b_["fp"], b_["fs"], st_)
+                keep = (b_["stats"].index_select(0, fidx)[:, 0] == 0)
+                b_["pobs"].index_copy_(0, fidx, torch.where(keep[:, None], b_["fp"], b_["pobs"].index_select(0, fidx)))
+                b_["stats"].index_copy_(0, fidx, torch.where(keep[:, None], b_["fs"], b_["stats"].index_select(0, fidx)))
+            R.relaybp_count_failures(h_["plain"], b_["pobs"], b_["obs"], b_["stats"], B, cnt, st_)
+            it.add_(b_["stats"][:, 3].sum())
 
     out = {}
-    with torch.cuda.stream(st):
-        for kind in ("plain", "learned", "ablation"):
-            cnt = torch.zeros(4, dtype=torch.int64, device=dev)
-            for w_ in range(W):
-                run(kind, K + w_, cnt)
+    for kind in ("plain", "learned", "ablation"):
+        cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+        it = torch.zeros(1, dtype=torch.int64, device=dev)
+        for w_ in range(W):
+            step(kind, K + w_, cnt, it)
+        torch.cuda.synchronize()
+        cnt.zero_()
+        it.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(streams[0])
+            for s_ in streams[1:]:
+                s_.wait_stream(streams[0])
+            for k in range(K):
+                step(kind, k, cnt, it)
+            for s_ in streams[1:]:
+                streams[0].wait_stream(s_)
+            e1.record(streams[0])
             torch.cuda.synchronize()
-            cnt.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            fb = iters = 0
-            with ClockSampler(local) as clk:
-                e0.record(st)
-                for k in range(K):
-                    f, i = run(kind, k, cnt)
-                    fb += f
-                    iters += i
-                e1.record(st)
-                torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            c = cnt.cpu().tolist()
-            out[kind] = {"shots_per_s": B * K / (ms / 1e3), "ms_per_step": ms / K, "shots": c[0], "failures": c[3],
-                         "nonconverged": c[1], "logical": c[2], "block_ler": c[3] / max(1, c[0]),
-                         "mean_iterations": iters / (B * K), "fallback_shots": fb, "clocks": clk.summary()}
+        ms = e0.elapsed_time(e1)
+        c = cnt.cpu().tolist()
+        out[kind] = {"shots_per_s": B * K / (ms / 1e3), "ms_per_step": ms / K, "shots": c[0], "failures": c[3],
+                     "nonconverged": c[1], "logical": c[2], "block_ler": c[3] / max(1, c[0]),
+                     "mean_iterations": float(it.item()) / (B * K), "clocks": clk.summary()}
     lp, ll = out["plain"], out["learned"]
     equal = agree_within(ll["failures"], ll["shots"], lp["failures"], lp["shots"])
     line = {"metric": METRIC, "value": ll["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": K, "warmup": W,
@@ -526,14 +538,18 @@ def run_learned(a):
             "config": {"workload": "learned vs plain Relay-BP, ZSZ-LP-160 d=10, inference p=0.001, training p=0.002",
                        "train": {"steps": a.train_steps, "batch": BT, "unrolled_iterations": T, "optimizer": "Adam 3e-3",
                                  "seconds": train_s, "loss_history": hist},
-                       "learned_decoder": "BF16 messages, learned weights + knots, stop_nconv=1, plain fallback",
+                       "learned_decoder": "BF16 messages, learned weights + knots, stop_nconv=1, plain fallback "
+                                          "(32 lowest-ranked shots per step re-decoded, kept where unconverged)",
+                       "pipeline": "2 streams, steps alternate, L2 flushed before every step",
                        "plain_decoder": "FP32, paper settings (stop_nconv=5)", "shots_per_step": B},
             "plain": lp, "learned": ll, "ablation_plain_stop1": out["ablation"],
             "speedup_vs_plain": ll["shots_per_s"] / lp["shots_per_s"], "equal_ler_2sigma": bool(equal),
             "clocks": ll["clocks"]}
     print(json.dumps(line), flush=True)
-    for x in (ht, hl, hp, ha, hf):
-        R.relaybp_destroy(x)
+    R.relaybp_destroy(ht)
+    for hh in H:
+        for x in hh.values():
+            R.relaybp_destroy(x)
 
 
 def main():

@@ -207,6 +207,18 @@ int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const 
                            const relaybp_shot_stats *d_stats, int64_t shots, unsigned long long *d_counters,
                            void *cuda_stream);
 
+/* Autotuner (launch shape only; no counterpart in the paper): times the
+ * compressed decode kernel on d_syndromes for every valid row geometry (L
+ * lanes per check row x NB positions per lane, L*NB >= the longest row) and
+ * block size (256, 512 threads), and keeps the fastest in the handle for
+ * later single-DEM decodes.  Synchronises the stream.  Results of a decode do
+ * not depend on the launch shape (per-shot arithmetic is identical), only
+ * its speed.  Outputs (each may be NULL): the chosen L, NB, threads and its
+ * time in ms.  RELAYBP_ERR_UNSUPPORTED for DEMs decoded by the literal-order
+ * FP64 kernel, which has no shape to tune. */
+int relaybp_autotune(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots, int32_t *out_L,
+                     int32_t *out_NB, int32_t *out_threads, float *out_ms, void *cuda_stream);
+
 /* Batched decoding of several DEMs in one persistent launch (no counterpart
  * in the paper, which decodes one shot at a time; its App. F notes that
  * batched decoding is bound by device memory capacity and bandwidth).

@@ -75,6 +75,7 @@ struct relaybp_handle {
     int64_t launches = 0;
     int max_row_deg = 0;
     // learned-form training scratch: work counter and one gradient row per block
+    int tuned_L = 0, tuned_NB = 0, tuned_threads = 0; // autotuned launch shape (0: heuristic)
     const float *lw = nullptr, *lknots = nullptr;     // learned inference parameters (caller-owned)
     int lT = 0, lK = 0;
     unsigned long long *d_lwork = nullptr;
@@ -333,7 +334,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         total += io[d].shots;
         plan_max = std::max(plan_max, J.plan.total);
         vmax = std::max(vmax, h->dem.V);
-        threads = std::max(threads, block_threads(h->dem));
+        threads = std::max(threads, h->tuned_threads > 0 ? h->tuned_threads : block_threads(h->dem));
     }
     tab.start[n] = total;
     tab.n = n;
@@ -384,7 +385,9 @@ int launch_jobs_geom(relaybp_handle *const *hs, const JobIO *io, int n, Scratch 
 {
     int maxdeg = 0;
     for (int d = 0; d < n; ++d) maxdeg = std::max(maxdeg, hs[d]->max_row_deg);
-    const RowGeom rg = row_geom(maxdeg);
+    RowGeom rg = row_geom(maxdeg);
+    if (n == 1 && hs[0]->tuned_L > 0 && hs[0]->tuned_L * hs[0]->tuned_NB >= maxdeg)
+        rg = RowGeom{hs[0]->tuned_L, hs[0]->tuned_NB};
 #define RELAYBP_GEOM(LL, NN)                                                                                   \
     if (rg.L == LL && rg.NB == NN) return launch_jobs<S, LL, NN>(hs, io, n, sc, st, on_chip_only);
     RELAYBP_GEOM(4, 4)
@@ -870,6 +873,64 @@ int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const 
                                                                 words(h->dem.K), d_counters);
     CUDA_TRY(cudaGetLastError());
     h->launches += 1;
+    return 0;
+}
+
+int relaybp_autotune(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots, int32_t *out_L,
+                     int32_t *out_NB, int32_t *out_threads, float *out_ms, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 1 || !d_syndromes) return fail(RELAYBP_ERR_INVALID, "need at least one syndrome");
+    if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots) {
+        ExactPlan ep = make_exact_plan(h->dem);
+        int maxsm = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+        if (ep.total <= maxsm / 4) return fail(RELAYBP_ERR_UNSUPPORTED, "the literal-order FP64 kernel has no shape to tune");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const RowGeom opts[] = {{4, 4}, {8, 4}, {8, 8}, {8, 12}, {8, 16}, {16, 16}, {32, 16}};
+    const int thr[] = {256, 512};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int sL = h->tuned_L, sNB = h->tuned_NB, sT = h->tuned_threads;
+    float best = 0.f;
+    int bL = 0, bNB = 0, bT = 0;
+    const JobIO io{d_syndromes, shot0, shots, nullptr, nullptr, nullptr, nullptr, 0};
+    for (const RowGeom &o : opts) {
+        if (o.L * o.NB < h->max_row_deg || o.L * o.NB > 4 * std::max(32, h->max_row_deg)) continue;
+        for (int tc : thr) {
+            h->tuned_L = o.L;
+            h->tuned_NB = o.NB;
+            h->tuned_threads = tc;
+            int rc = launch_jobs_dtype(&h, &io, 1, h->scratch, st);             // warm-up (also sizes scratch)
+            if (rc == 0) {
+                cudaEventRecord(e0, st);
+                rc = launch_jobs_dtype(&h, &io, 1, h->scratch, st);
+                cudaEventRecord(e1, st);
+            }
+            if (rc != 0) continue;
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (bL == 0 || ms < best) { best = ms; bL = o.L; bNB = o.NB; bT = tc; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bL == 0) {
+        h->tuned_L = sL; h->tuned_NB = sNB; h->tuned_threads = sT;
+        return fail(RELAYBP_ERR_UNSUPPORTED, "no launch shape ran");
+    }
+    h->tuned_L = bL;
+    h->tuned_NB = bNB;
+    h->tuned_threads = bT;
+    g_err.clear();
+    if (out_L) *out_L = bL;
+    if (out_NB) *out_NB = bNB;
+    if (out_threads) *out_threads = bT;
+    if (out_ms) *out_ms = best;
     return 0;
 }
 

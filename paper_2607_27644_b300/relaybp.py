@@ -63,6 +63,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_learned_forward": ([P, I32, I32, P, I32, P, U64, P, P, U64, I64, P, P, P], ctypes.c_int),
         "relaybp_learned_backward": ([P, I32, I32, P, I32, P, U64, P, U64, I64, P, ctypes.c_double, P, P, P],
                                      ctypes.c_int),
+        "relaybp_autotune": ([P, P, U64, I64, P, P, P, P, P], ctypes.c_int),
         "relaybp_group_create": ([P, I32, ctypes.POINTER(P)], ctypes.c_int),
         "relaybp_group_decode": ([P, P, P, P, P, P, P, P], ctypes.c_int),
         "relaybp_group_launch_count": ([P], I64),
@@ -83,7 +84,7 @@ _lib = _load()
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
-            "relaybp_learned_backward", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
+            "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
             "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
 
 
@@ -284,6 +285,13 @@ def relaybp_learned_backward(h: Handle, w, knots, gamma_seed: int, d_errors, sho
     _check(_lib.relaybp_learned_backward(h.ptr, _prec(w.dtype), T, _ptr(w), K, _ptr(knots), gamma_seed,
                                          _ptr(d_errors), shot0, shots, _ptr(d_tape), scale, _ptr(d_grad_w),
                                          _ptr(d_grad_knots), _stream(stream)), "relaybp_learned_backward")
+
+
+def relaybp_autotune(h: Handle, d_syndromes, shot0: int, shots: int, stream=None) -> dict:
+    L, NB, T, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(_lib.relaybp_autotune(h.ptr, _ptr(d_syndromes), shot0, shots, ctypes.byref(L), ctypes.byref(NB),
+                                 ctypes.byref(T), ctypes.byref(ms), _stream(stream)), "relaybp_autotune")
+    return dict(L=L.value, NB=NB.value, threads=T.value, ms=ms.value)
 
 
 @dataclass

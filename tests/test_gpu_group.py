@@ -75,3 +75,21 @@ def test_group_mixed_codes_fp16_off_chip_state():
             r1 = oracle.decode(dem, po, syn[s_:s_ + 1], shot0=1000 * i + int(s_))
             agree += int(np.array_equal(r1["pred_obs"][0, :pobs.shape[1]], pobs[s_].view(np.uint32)))
         assert agree >= len(idx) - 1
+
+
+def test_autotune_keeps_results():
+    """The autotuner only changes the launch shape: decodes before and after
+    tuning agree bit for bit."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    dem = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", num_sets=100, gamma_min=-0.15, gamma_max=0.61, seed=3))
+    syn = torch.zeros((2000, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 8, 0, 2000, syn)
+    before = _single(R, h, syn, 0)
+    shape = R.relaybp_autotune(h, syn, 0, 2000)
+    assert shape["L"] * shape["NB"] >= 92 and shape["threads"] in (256, 512) and shape["ms"] > 0
+    after = _single(R, h, syn, 0)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    R.relaybp_destroy(h)
