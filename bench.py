@@ -50,8 +50,10 @@ def _args():
                     help="zsz160: the headline workload; mixed: nine DEMs in one persistent launch; "
                          "learned: train, then learned vs plain Relay-BP at equal LER")
     ap.add_argument("--train-steps", type=int, default=300, help="learned: Adam steps of 512 shots at p=0.2%%")
+    ap.add_argument("--learned-msg", default="bf16", choices=["bf16", "f16", "f32"], help="learned: message storage")
     ap.add_argument("--mixed-base", type=int, default=2000, help="mixed: shots per unit of the 2:5:10 mix")
-    ap.add_argument("--msg", default="f16", choices=["f16", "bf16", "f32"], help="mixed: message storage")
+    ap.add_argument("--msg", default=None, choices=["f16", "bf16", "f32"],
+                    help="message storage (default: f32 for zsz160, f16 for mixed)")
     return ap.parse_args()
 
 
@@ -185,7 +187,8 @@ def run_ours(a):
     # relay legs overlaps the next batch instead of idling the GPU at the end of
     # its launch.  (Each handle owns its work counter, so launches may overlap.)
     NS = 2
-    hs = [R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **DECODER)) for _ in range(NS)]
+    msg = a.msg or "f32"
+    hs = [R.relaybp_build_dem(dem, R.Params(msg_dtype=msg, **DECODER)) for _ in range(NS)]
     h = hs[0]
     B, K, W = a.batch, a.steps, a.warmup
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
@@ -291,15 +294,15 @@ def run_ours(a):
     iters_rank = int(iters_total.item())
     wall_s = ms / 1e3
     E, V, C = dem.n_edges, dem.n_loc, dem.n_det
-    b_m = 4
+    b_m = {"f32": 4, "f16": 2, "bf16": 2}[msg]
     bytes_per_iter = 4 * b_m * E + 16 * V + (V + C) / 8.0
     dec_avg_s = sum(dec_ms) / len(dec_ms) / 1e3
     achieved = (iters_rank / K) * bytes_per_iter / dec_avg_s / 1e9
     edge_updates = iters_rank * E / wall_s
     roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
             "traffic": None,
-            "kernel": "relay_decode_kernel<float>",
-            "algorithmic_bytes": "per shot-iteration 4*b_m*E + 16*V + (V+C)/8 (b_m=4)",
+            "kernel": f"relay_decode_kernel<{msg}>",
+            "algorithmic_bytes": f"per shot-iteration 4*b_m*E + 16*V + (V+C)/8 (b_m={b_m})",
             "peak_source": "measured live: conflict-free 16-B shared-memory loads on all SMs (relaybp_probe_smem_read)",
             "edge_updates_per_s_wall": edge_updates, "decode_ms_per_launch": dec_avg_s * 1e3,
             "achieved_wall": iters_rank * bytes_per_iter / wall_s / 1e9,
@@ -309,7 +312,7 @@ def run_ours(a):
     c = cnt.cpu().tolist()
     line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEM (no dataset)",
+            "dtype": msg, "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEM (no dataset)",
             "config": _config(dem, B, K, world), "clocks": clk.summary(), "gpu_launches": launches * world,
             "roofline": roof, "e2e": e2e,
             "ler": {"shots": c[0], "failures": c[3], "nonconverged": c[1], "logical": c[2],
@@ -349,7 +352,8 @@ def run_mixed(a):
         for d in circuit_dems(code, MIXED_P, rounds, "Z"):
             dems.append(d)
             params.append(dict(DECODER, gamma_min=gmin, gamma_max=gmax))
-    hs = [R.relaybp_build_dem(d, R.Params(msg_dtype=a.msg, **pp)) for d, pp in zip(dems, params)]
+    mmsg = a.msg or "f16"
+    hs = [R.relaybp_build_dem(d, R.Params(msg_dtype=mmsg, **pp)) for d, pp in zip(dems, params)]
     grp = R.relaybp_group_create(hs)
     n = len(hs)
     shots = [MIXED_RATIO[i % 3] * a.mixed_base for i in range(n)]
@@ -405,7 +409,7 @@ def run_mixed(a):
                         "logical": int(c[i, 2]), "block_ler": f / max(1, c[i, 0])})
     line = {"metric": "decoded shots/s, nine ZSZ-LP DEMs in one persistent launch", "value": total / (ms / 1e3),
             "unit": "shots/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": a.msg,
+            "scaling": "weak", "vs_baseline": None, "dtype": mmsg,
             "data": "synthetic: Philox-sampled faults of the Table 5 circuit DEMs",
             "config": {"workload": "ZSZ-LP-320/390/550 (d=14/16/18) x p in {0.001,0.002,0.003}, Z-memory, "
                                    "one group launch per step, CUDA-graph replay",
@@ -441,25 +445,41 @@ def run_learned(a):
     T, BT = 30, 512
     # ---- training (untimed) ---------------------------------------------------
     ht = R.relaybp_build_dem(d_train, R.Params(msg_dtype="f32", **DECODER))
-    model = LearnedParams(T, E, DECODER["gamma_min"], DECODER["gamma_max"], device=dev)
-    opt = torch.optim.Adam(model.parameters(), lr=3e-3)
+    row_of = np.repeat(np.arange(d_inf.n_det), np.diff(d_inf.H_indptr))
+    model = LearnedParams(T, E, DECODER["gamma_min"], DECODER["gamma_max"], device=dev, row_of_edge=row_of,
+                          n_rows=d_inf.n_det)
+    opt = torch.optim.Adam(model.parameters(), lr=1e-3)
     syn_t = torch.empty((BT, ht.wc), dtype=torch.int32, device=dev)
     err_t = torch.empty((BT, ht.wv), dtype=torch.int32, device=dev)
+    syn_v = torch.empty((2 * BT, ht.wc), dtype=torch.int32, device=dev)
+    err_v = torch.empty((2 * BT, ht.wv), dtype=torch.int32, device=dev)
+    R.relaybp_sample(ht, 4, 9 * 10**8, 2 * BT, syn_v, None, err_v)     # held-out shots
     t0 = time.perf_counter()
-    hist = []
+    hist, best, best_state = [], float("inf"), None
+
+    def held_out():
+        with torch.no_grad():
+            return float(model.loss(ht, syn_v, err_v, 9 * 10**8, 0x5EED))
+
     for k in range(a.train_steps):
         R.relaybp_sample(ht, 4, k * BT, BT, syn_t, None, err_t)
         opt.zero_grad()
         loss = model.loss(ht, syn_t, err_t, k * BT, 0x5EED)
         loss.backward()
+        torch.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
         opt.step()
         with torch.no_grad():
             model.w.clamp_(0.0, 2.0)
-        if k % max(1, a.train_steps // 10) == 0 or k == a.train_steps - 1:
-            hist.append(round(float(loss), 3))
+        if k % 25 == 0 or k == a.train_steps - 1:
+            v = held_out()
+            hist.append(round(v, 3))
+            if v < best:
+                best = v
+                best_state = {n: t.detach().clone() for n, t in model.state_dict().items()}
+    model.load_state_dict(best_state)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    w = model.w.detach().float().contiguous()
+    wrow = model.w.detach().float().contiguous()
     knots = model.knots().detach().float().contiguous()
     # ---- decoders: two streams, one handle set per stream ------------------------
     NS, FCAP = 2, 32
@@ -468,8 +488,8 @@ def run_learned(a):
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     H = []
     for q in range(NS):
-        hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="bf16", **learned_params))
-        R.relaybp_set_learned(hl, w, knots)
+        hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype=a.learned_msg, **learned_params))
+        R.relaybp_set_learned_rows(hl, wrow, knots)
         H.append({"learned": hl,
                   "plain": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **DECODER)),
                   "ablation": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1))),
@@ -534,11 +554,13 @@ def run_learned(a):
     equal = agree_within(ll["failures"], ll["shots"], lp["failures"], lp["shots"])
     line = {"metric": METRIC, "value": ll["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": K, "warmup": W,
             "ms_per_step": ll["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16", "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEMs",
+            "dtype": a.learned_msg, "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEMs",
             "config": {"workload": "learned vs plain Relay-BP, ZSZ-LP-160 d=10, inference p=0.001, training p=0.002",
-                       "train": {"steps": a.train_steps, "batch": BT, "unrolled_iterations": T, "optimizer": "Adam 3e-3",
-                                 "seconds": train_s, "loss_history": hist},
-                       "learned_decoder": "BF16 messages, learned weights + knots, stop_nconv=1, plain fallback "
+                       "train": {"steps": a.train_steps, "batch": BT, "unrolled_iterations": T,
+                                 "optimizer": "Adam 1e-3, grad-norm clip 1, weights in [0, 2], best held-out kept",
+                                 "weights": "tied per check row and iteration", "seconds": train_s,
+                                 "held_out_loss_every_25_steps": hist},
+                       "learned_decoder": f"{a.learned_msg} messages, learned weights + knots, stop_nconv=1, plain fallback "
                                           "(32 lowest-ranked shots per step re-decoded, kept where unconverged)",
                        "pipeline": "2 streams, steps alternate, L2 flushed before every step",
                        "plain_decoder": "FP32, paper settings (stop_nconv=5)", "shots_per_step": B},

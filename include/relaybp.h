@@ -123,6 +123,13 @@ int relaybp_set_params(relaybp_handle *h, const relaybp_params *params);
  * them.  Needs msg_dtype F32, F16 or BF16 and carry_messages = 0. */
 int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const float *d_knots, int32_t K);
 
+/* Same with weights tied per check row: d_wrow [T][C], the weight of every
+ * message check i sends in iteration t+1 of a leg (the per-edge weights with
+ * w[t][e] = d_wrow[t][row of e]).  The weight travels in the row's compressed
+ * state, so decoding costs one multiply per message and no extra loads.
+ * Replaces any per-edge weights. */
+int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, const float *d_knots, int32_t K);
+
 /* Query sizes: n_det (C), n_loc (V), n_obs (K), n_edges (nnz of H). */
 int relaybp_sizes(const relaybp_handle *h, int32_t *n_det, int32_t *n_loc, int32_t *n_obs, int64_t *n_edges);
 

@@ -61,6 +61,7 @@ struct DecodeParamsDev {
     const float *lw;
     const float *lknots;
     int32_t lT, lK;
+    const float *lwrow;         // learned weights tied per check row: [lT][C] (NULL: none)
 };
 
 struct StatsDev {               // mirrors relaybp_shot_stats
@@ -191,9 +192,10 @@ template <> struct Prec<__nv_bfloat16> {
 };
 
 // Compressed state of one check row: 16 bytes for FP32, 8 for FP16/BF16.
-template <typename S> struct alignas(sizeof(S) >= 4 ? 16 : 8) CheckState {
+template <typename S> struct alignas(16) CheckState {
     S m1, m2;                   // smallest / second-smallest |mu| over the row
     uint32_t meta;              // argmin position in the row | parity << 31
+    float wt;                   // learned weight shared by the row's messages (1 if none)
 };
 
 // Column entry: check index << 12 | position of the entry within its row.
@@ -206,7 +208,8 @@ constexpr uint32_t COL_SENTINEL = 0xffffffffu;
 // i*L + pos % L, bit pos / L.
 template <typename S, int L, int NB, bool LW>
 __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState<S> *cs, uint16_t *sgnh,
-                                         const uint32_t *syn, int warp, int nwarp, int lane, const float *wprev)
+                                         const uint32_t *syn, int warp, int nwarp, int lane, const float *wprev,
+                                         const float *wrow_new)
 {
     static_assert(32 % L == 0 && NB <= 16, "row geometry");
     using C = typename Prec<S>::C;
@@ -234,6 +237,10 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             const CheckState<S> o = cs[i];
             om1 = Prec<S>::ld(o.m1);
             om2 = Prec<S>::ld(o.m2);
+            if (LW) {                       // row-tied weight of the old messages
+                om1 = mul_rn(om1, (C)o.wt);
+                om2 = mul_rn(om2, (C)o.wt);
+            }
             ometa = o.meta;
             oldbits = sgnh[i * L + l];
         }
@@ -245,7 +252,7 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             if (idx[b] >= 0) {
                 const uint32_t k = (uint32_t)(b * L + l);
                 C mag = (k == oarg) ? om2 : om1;
-                if (LW) mag = mul_rn(mag, (C)__ldg(wprev + e0 + (int)k));
+                if (LW && wprev) mag = mul_rn(mag, (C)__ldg(wprev + e0 + (int)k));
                 const C nu_old = (((oldbits >> b) & 1u) ^ opar) ? -mag : mag;
                 const C m = add_rn(Prec<S>::ld(A[idx[b]]), -nu_old);
                 newbits |= ((m < (C)0) ? 1u : 0u) << b;
@@ -273,6 +280,7 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
                 n.m1 = Prec<S>::st(b1);
                 n.m2 = Prec<S>::st(b2);
                 n.meta = bi | ((par ^ sb) << 31);
+                n.wt = (LW && wrow_new) ? __ldg(wrow_new + i) : 1.0f;
                 cs[i] = n;
             }
         }
@@ -378,7 +386,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         }
         for (int i = tid; i < Cn; i += nthr) {
             CheckState<S> z;
-            z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u;
+            z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u; z.wt = 1.0f;
             cs[i] = z;
         }
         for (int w = tid; w < Cn * L; w += nthr) sgnh[w] = (uint16_t)0;
@@ -422,7 +430,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                 if (!p.carry_messages) {
                     for (int i = tid; i < Cn; i += nthr) {
                         CheckState<S> z;
-                        z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u;
+                        z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u; z.wt = 1.0f;
                         cs[i] = z;
                     }
                     for (int w = tid; w < Cn * L; w += nthr) sgnh[w] = (uint16_t)0;
@@ -433,13 +441,14 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             bool conv = false;
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: check rows, L lanes per row ---------------------------
-                const float *wprev = nullptr, *wcur = nullptr;
+                const float *wprev = nullptr, *wcur = nullptr, *wrow = nullptr;
                 if (LW && p.lw) {
                     wprev = p.lw + (int64_t)min(t > 0 ? t - 1 : 0, p.lT - 1) * g.E;
                     wcur = p.lw + (int64_t)min(t, p.lT - 1) * g.E;
                 }
-                if (LW && p.lw) row_pass<S, L, NB, true>(g, A, cs, sgnh, syn, warp, nwarp, lane, wprev);
-                else row_pass<S, L, NB, false>(g, A, cs, sgnh, syn, warp, nwarp, lane, nullptr);
+                if (LW && p.lwrow) wrow = p.lwrow + (int64_t)min(t, p.lT - 1) * g.C;
+                if (LW) row_pass<S, L, NB, true>(g, A, cs, sgnh, syn, warp, nwarp, lane, wprev, wrow);
+                else row_pass<S, L, NB, false>(g, A, cs, sgnh, syn, warp, nwarp, lane, nullptr, nullptr);
                 __syncthreads();
                 // ---- a4: variables, one lane per variable, ELL slices --------
                 for (int G = warp; G < NG; G += nwarp) {
@@ -460,6 +469,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                         const uint32_t pos = c & 0xfffu;
                         const uint32_t hw = sgnh[i * L + (pos % L)];
                         C mag = Prec<S>::ld((pos == (q.meta & 0xfffu)) ? q.m2 : q.m1);
+                        if (LW) mag = mul_rn(mag, (C)q.wt);
                         if (LW && wcur) mag = mul_rn(mag, (C)__ldg(wcur + __ldg(cel + slot * 32)));
                         const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
                         return sb ? -mag : mag;

@@ -77,6 +77,7 @@ struct relaybp_handle {
     // learned-form training scratch: work counter and one gradient row per block
     int tuned_L = 0, tuned_NB = 0, tuned_threads = 0; // autotuned launch shape (0: heuristic)
     const float *lw = nullptr, *lknots = nullptr;     // learned inference parameters (caller-owned)
+    const float *lwrow = nullptr;                     // row-tied learned weights [lT][C]
     int lT = 0, lK = 0;
     unsigned long long *d_lwork = nullptr;
     void *d_lgbar = nullptr;
@@ -320,7 +321,8 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         J.p.lknots = h->lknots;
         J.p.lT = h->lT;
         J.p.lK = h->lK;
-        if (h->lw || h->lknots) learned = true;
+        J.p.lwrow = h->lwrow;
+        if (h->lw || h->lknots || h->lwrow) learned = true;
         J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), L);
         J.syn_in = io[d].syn;
         J.shot0 = io[d].shot0;
@@ -416,7 +418,7 @@ int launch_jobs_dtype(relaybp_handle *const *hs, const JobIO *io, int n, Scratch
 // Single-DEM decode: the literal-order FP64 kernel when it applies, else one job.
 int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, bool on_chip_only)
 {
-    if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots) {
+    if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots && !h->lwrow) {
         int rc = launch_decode_exact(h, sc, io, st);
         if (rc <= 0) return rc;
     }
@@ -747,7 +749,26 @@ int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const fl
     if (d_w && h->params.carry_messages)
         return fail(RELAYBP_ERR_UNSUPPORTED, "learned weights with carry_messages are not supported");
     h->lw = d_w;
+    h->lwrow = nullptr;
     h->lT = d_w ? T : 0;
+    h->lknots = d_knots;
+    h->lK = d_knots ? K : 0;
+    return 0;
+}
+
+int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, const float *d_knots, int32_t K)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if ((d_wrow && T < 1) || (d_knots && (K < 1 || K > 64)))
+        return fail(RELAYBP_ERR_INVALID, "need T >= 1 with weights and 1 <= K <= 64 with knots");
+    if ((d_wrow || d_knots) && h->params.msg_dtype == RELAYBP_MSG_F64)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned decoding runs with FP32 arithmetic (msg_dtype F32/F16/BF16)");
+    if (d_wrow && h->params.carry_messages)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned weights with carry_messages are not supported");
+    h->lw = nullptr;
+    h->lwrow = d_wrow;
+    h->lT = d_wrow ? T : 0;
     h->lknots = d_knots;
     h->lK = d_knots ? K : 0;
     return 0;

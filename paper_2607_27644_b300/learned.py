@@ -44,14 +44,23 @@ class LearnedLoss(torch.autograd.Function):
 
 
 class LearnedParams(torch.nn.Module):
-    """w [T, E] initialised to 1 and knots from raw parameters kept monotone:
-    knots[0] = theta[0], knots[k+1] = knots[k] + softplus(theta[k+1]);
-    initialised to the uniform interval [gamma_min, gamma_max]."""
+    """Message weights initialised to 1 and knots from raw parameters kept
+    monotone: knots[0] = theta[0], knots[k+1] = knots[k] + softplus(theta[k+1]);
+    initialised to the uniform interval [gamma_min, gamma_max].
+
+    Weights are per edge ([T, E]) or, with row_of_edge given, tied per check
+    row ([T, C], expanded to edges for the loss) -- the form the decode kernel
+    applies at no extra memory traffic (relaybp_set_learned_rows)."""
 
     def __init__(self, T: int, n_edges: int, gamma_min: float, gamma_max: float, K: int = 16,
-                 dtype=torch.float32, device="cuda"):
+                 dtype=torch.float32, device="cuda", row_of_edge=None, n_rows: int = 0):
         super().__init__()
-        self.w = torch.nn.Parameter(torch.ones((T, n_edges), dtype=dtype, device=device))
+        self.row_of_edge = None
+        if row_of_edge is not None:
+            self.row_of_edge = torch.as_tensor(row_of_edge, dtype=torch.long, device=device)
+            self.w = torch.nn.Parameter(torch.ones((T, n_rows), dtype=dtype, device=device))
+        else:
+            self.w = torch.nn.Parameter(torch.ones((T, n_edges), dtype=dtype, device=device))
         step = (gamma_max - gamma_min) / K
         inv_sp = float(torch.log(torch.expm1(torch.tensor(step, dtype=torch.float64))))
         theta = torch.full((K + 1,), inv_sp, dtype=dtype, device=device)
@@ -62,5 +71,9 @@ class LearnedParams(torch.nn.Module):
         return torch.cat([self.theta[:1], self.theta[:1] + torch.cumsum(torch.nn.functional.softplus(self.theta[1:]),
                                                                         0)])
 
+    def edge_weights(self):
+        return self.w if self.row_of_edge is None else self.w.index_select(1, self.row_of_edge)
+
     def loss(self, handle, syndromes, errors, shot0: int, gamma_seed: int):
-        return LearnedLoss.apply(self.w, self.knots(), handle, syndromes, errors, shot0, gamma_seed)
+        return LearnedLoss.apply(self.edge_weights().contiguous(), self.knots(), handle, syndromes, errors, shot0,
+                                 gamma_seed)

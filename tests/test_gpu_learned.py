@@ -175,3 +175,30 @@ def test_learned_decode_matches_oracle():
     same = np.all(ro["pred_obs"][:, :rg["pred_obs"].shape[1]] == rg["pred_obs"], axis=1)
     assert (~same).sum() <= 0
     R.relaybp_destroy(h)
+
+
+def test_row_tied_weights_equal_expanded_per_edge_weights():
+    """Tied weights travel in the check state; decoding equals the per-edge
+    path with the same weights expanded over each row, bit for bit."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode
+    dem = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+    kw = dict(num_sets=50, gamma_min=-0.15, gamma_max=0.61, seed=9, stop_nconv=2)
+    T = 6
+    rng = np.random.default_rng(10)
+    wrow = rng.uniform(0.7, 1.0, (T, dem.n_det)).astype(np.float32)
+    row_of = np.repeat(np.arange(dem.n_det), np.diff(dem.H_indptr))
+    wedge = wrow[:, row_of].copy()
+    knots = np.cumsum(np.r_[-0.15, rng.uniform(0.02, 0.07, 16)]).astype(np.float32)
+    syn, _, _ = oracle.sample(dem, 12, 0, 500)
+    ha = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **kw))
+    hb = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **kw))
+    tk = torch.tensor(knots, device="cuda")
+    R.relaybp_set_learned(ha, torch.tensor(wedge, device="cuda"), tk)
+    R.relaybp_set_learned_rows(hb, torch.tensor(wrow, device="cuda"), tk)
+    a, b = gpu_decode(ha, syn), gpu_decode(hb, syn)
+    for k in ("corrections", "pred_obs", "stats", "weights"):
+        assert np.array_equal(a[k], b[k]), k
+    R.relaybp_destroy(ha)
+    R.relaybp_destroy(hb)
