@@ -482,8 +482,11 @@ def run_learned(a):
     wrow = model.w.detach().float().contiguous()
     knots = model.knots().detach().float().contiguous()
     # ---- decoders: two streams, one handle set per stream ------------------------
-    NS, FCAP = 2, 32
-    learned_params = dict(DECODER, stop_nconv=1)
+    # the learned decoder runs a short relay (50 legs): a shot it cannot settle
+    # leaves after ~3k iterations and the plain decoder (paper settings) takes
+    # it over, so a hard shot pays one full-length relay, not two
+    NS, FCAP = 3, 32
+    learned_params = dict(DECODER, stop_nconv=1, num_sets=50)
     B, K, W = a.batch, a.steps, a.warmup
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     H = []
@@ -560,9 +563,9 @@ def run_learned(a):
                                  "optimizer": "Adam 1e-3, grad-norm clip 1, weights in [0, 2], best held-out kept",
                                  "weights": "tied per check row and iteration", "seconds": train_s,
                                  "held_out_loss_every_25_steps": hist},
-                       "learned_decoder": f"{a.learned_msg} messages, learned weights + knots, stop_nconv=1, plain fallback "
+                       "learned_decoder": f"{a.learned_msg} messages, learned weights + knots, stop_nconv=1, 50 legs, plain fallback "
                                           "(32 lowest-ranked shots per step re-decoded, kept where unconverged)",
-                       "pipeline": "2 streams, steps alternate, L2 flushed before every step",
+                       "pipeline": "3 streams, steps rotate, L2 flushed before every step",
                        "plain_decoder": "FP32, paper settings (stop_nconv=5)", "shots_per_step": B},
             "plain": lp, "learned": ll, "ablation_plain_stop1": out["ablation"],
             "speedup_vs_plain": ll["shots_per_s"] / lp["shots_per_s"], "equal_ler_2sigma": bool(equal),
