@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--cpu-sample", type=int, default=96, help="shots of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--streams", type=int, default=3, help="zsz160: streams (handle sets) the steps rotate over")
     ap.add_argument("--workload", default="zsz160", choices=["zsz160", "mixed", "learned"],
                     help="zsz160: the headline workload; mixed: nine DEMs in one persistent launch; "
                          "learned: train, then learned vs plain Relay-BP at equal LER")
@@ -69,13 +70,13 @@ def _dem():
     return circuit_dem(WORKLOAD["code"], WORKLOAD["p"], WORKLOAD["rounds"], WORKLOAD["basis"])
 
 
-def _config(dem, batch, steps, world, extra=None):
+def _config(dem, batch, steps, world, extra=None, streams=3):
     c = {"workload": f"{WORKLOAD['code']} circuit-level Z-memory, d={WORKLOAD['rounds']}, p={WORKLOAD['p']}, "
                      f"DEM {dem.n_det}x{dem.n_loc} (E={dem.n_edges}), plain Relay-BP",
          "decoder": dict(DECODER), "shots_per_step_per_gpu": batch, "steps": steps,
          "shots_total": batch * steps * world,
          "l2": "flushed before every step on that step's stream (256 MiB write)",
-         "parallelism": f"replicas x{world} (shot ranges); 2 streams x 1 handle each, steps alternate"}
+         "parallelism": f"replicas x{world} (shot ranges); steps rotate over {streams} streams, one handle each"}
     if extra:
         c.update(extra)
     return c
@@ -183,10 +184,11 @@ def run_ours(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dem = _dem()
-    # Two handles on two streams, alternating steps: the rare shot that runs all
-    # relay legs overlaps the next batch instead of idling the GPU at the end of
-    # its launch.  (Each handle owns its work counter, so launches may overlap.)
-    NS = 2
+    # Handles on several streams, steps rotating over them: the rare shot that
+    # runs all relay legs overlaps the next batches instead of idling the GPU at
+    # the end of its launch.  (Each handle owns its work counter, so launches
+    # may overlap.)
+    NS = max(1, a.streams)
     msg = a.msg or "f32"
     hs = [R.relaybp_build_dem(dem, R.Params(msg_dtype=msg, **DECODER)) for _ in range(NS)]
     h = hs[0]
@@ -313,7 +315,7 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": msg, "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEM (no dataset)",
-            "config": _config(dem, B, K, world), "clocks": clk.summary(), "gpu_launches": launches * world,
+            "config": _config(dem, B, K, world, streams=NS), "clocks": clk.summary(), "gpu_launches": launches * world,
             "roofline": roof, "e2e": e2e,
             "ler": {"shots": c[0], "failures": c[3], "nonconverged": c[1], "logical": c[2],
                     "block_ler": c[3] / max(1, c[0])}}
