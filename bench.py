@@ -429,9 +429,10 @@ def run_learned(a):
     plain Relay-BP (paper settings, FP32) on the same fresh shots at p = 0.1%.
 
     Learned decoder: BF16 messages, learned message weights (T = 30) and
-    memory-strength distribution, stop after the first solution; shots it
-    leaves unconverged are re-decoded by plain Relay-BP (the fallback).  An
-    ablation runs plain Relay-BP with the same stop-after-one rule."""
+    memory-strength distribution in legs 0..49, plain legs after that in the
+    same launch (the fallback for shots the learned legs leave unconverged),
+    stop after the first solution.  An ablation runs plain Relay-BP with the
+    same stop-after-one rule."""
     import numpy as np
     import torch
     from paper_2607_27644_b300 import relaybp as R
@@ -483,30 +484,27 @@ def run_learned(a):
     train_s = time.perf_counter() - t0
     wrow = model.w.detach().float().contiguous()
     knots = model.knots().detach().float().contiguous()
-    # ---- decoders: two streams, one handle set per stream ------------------------
-    # the learned decoder runs a short relay (50 legs): a shot it cannot settle
-    # leaves after ~3k iterations and the plain decoder (paper settings) takes
-    # it over, so a hard shot pays one full-length relay, not two
-    NS, FCAP = 3, 32
-    learned_params = dict(DECODER, stop_nconv=1, num_sets=50)
+    # ---- decoders: one handle set per stream ------------------------------------
+    # learned parameters for legs 0..49, then plain legs (unit weights, uniform
+    # gamma) up to the paper's 1000 in the same launch: the plain fallback for
+    # the shots the learned legs do not settle; stop after the first solution
+    NS, LEGS = 3, 50
+    learned_params = dict(DECODER, stop_nconv=1)
     B, K, W = a.batch, a.steps, a.warmup
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     H = []
     for q in range(NS):
         hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype=a.learned_msg, **learned_params))
         R.relaybp_set_learned_rows(hl, wrow, knots)
+        R.relaybp_set_learned_legs(hl, LEGS)
         H.append({"learned": hl,
                   "plain": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **DECODER)),
-                  "ablation": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1))),
-                  "fallback": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32",
-                                                                  **dict(DECODER, seed=DECODER["seed"] + 1)))})
+                  "ablation": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1)))})
     hp = H[0]["plain"]
     bufs = [dict(syn=torch.empty((B, hp.wc), dtype=torch.int32, device=dev),
                  obs=torch.empty((B, hp.wk), dtype=torch.int32, device=dev),
                  pobs=torch.empty((B, hp.wk), dtype=torch.int32, device=dev),
-                 stats=torch.empty((B, 6), dtype=torch.int32, device=dev),
-                 fp=torch.empty((FCAP, hp.wk), dtype=torch.int32, device=dev),
-                 fs=torch.empty((FCAP, 6), dtype=torch.int32, device=dev)) for _ in range(NS)]
+                 stats=torch.empty((B, 6), dtype=torch.int32, device=dev)) for _ in range(NS)]
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
 
     def step(kind, k, cnt, it):
@@ -517,16 +515,6 @@ def run_learned(a):
             flush.fill_(k)
             R.relaybp_sample(h_["plain"], SAMPLE_SEED, s0, B, b_["syn"], b_["obs"], None, st_)
             R.relaybp_decode_batch(h_[kind], b_["syn"], s0, B, None, b_["pobs"], b_["stats"], st_)
-            if kind == "learned":
-                # fallback without a host round trip: the FCAP lowest-ranked shots
-                # (unconverged first) are re-decoded by plain Relay-BP and kept
-                # where the learned decoder did not converge
-                fidx = torch.argsort(b_["stats"][:, 0], stable=True)[:FCAP]
-                sf = b_["syn"].index_select(0, fidx).contiguous()
-                R.relaybp_decode_batch(h_["fallback"], sf, s0, FCAP, None, b_["fp"], b_["fs"], st_)
-                keep = (b_["stats"].index_select(0, fidx)[:, 0] == 0)
-                b_["pobs"].index_copy_(0, fidx, torch.where(keep[:, None], b_["fp"], b_["pobs"].index_select(0, fidx)))
-                b_["stats"].index_copy_(0, fidx, torch.where(keep[:, None], b_["fs"], b_["stats"].index_select(0, fidx)))
             R.relaybp_count_failures(h_["plain"], b_["pobs"], b_["obs"], b_["stats"], B, cnt, st_)
             it.add_(b_["stats"][:, 3].sum())
 
@@ -565,8 +553,8 @@ def run_learned(a):
                                  "optimizer": "Adam 1e-3, grad-norm clip 1, weights in [0, 2], best held-out kept",
                                  "weights": "tied per check row and iteration", "seconds": train_s,
                                  "held_out_loss_every_25_steps": hist},
-                       "learned_decoder": f"{a.learned_msg} messages, learned weights + knots, stop_nconv=1, 50 legs, plain fallback "
-                                          "(32 lowest-ranked shots per step re-decoded, kept where unconverged)",
+                       "learned_decoder": f"{a.learned_msg} messages, learned weights + knots in legs 0-49, plain legs "
+                                          "after (in-kernel fallback), stop_nconv=1",
                        "pipeline": "3 streams, steps rotate, L2 flushed before every step",
                        "plain_decoder": "FP32, paper settings (stop_nconv=5)", "shots_per_step": B},
             "plain": lp, "learned": ll, "ablation_plain_stop1": out["ablation"],

@@ -130,6 +130,12 @@ int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const fl
  * Replaces any per-edge weights. */
 int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, const float *d_knots, int32_t K);
 
+/* Learned parameters apply to legs 0 .. legs-1 only; later legs run the plain
+ * method (unit weights, gamma ~ U[gamma_min, gamma_max]) in the same launch --
+ * the plain fallback for shots the learned legs do not settle.  legs = -1: all
+ * legs (the default); below -1: RELAYBP_ERR_INVALID, setting unchanged. */
+int relaybp_set_learned_legs(relaybp_handle *h, int32_t legs);
+
 /* Query sizes: n_det (C), n_loc (V), n_obs (K), n_edges (nnz of H). */
 int relaybp_sizes(const relaybp_handle *h, int32_t *n_det, int32_t *n_loc, int32_t *n_obs, int64_t *n_edges);
 

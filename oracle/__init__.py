@@ -61,7 +61,8 @@ def _load():
         _lib.oracle_learned_loss.restype = ctypes.c_int
         _lib.oracle_relaybp_decode_learned.argtypes = ([ctypes.c_int32] * 3 + [P] * 5 +
                                                        [ctypes.POINTER(OracleParams), ctypes.c_int32, P,
-                                                        ctypes.c_int32, P, P, ctypes.c_uint64, ctypes.c_int64,
+                                                        ctypes.c_int32, P, ctypes.c_int32, P, ctypes.c_uint64,
+                                                        ctypes.c_int64,
                                                         P, P, P, P, ctypes.c_int32, P, ctypes.c_int32])
         _lib.oracle_relaybp_decode_learned.restype = ctypes.c_int
     return _lib
@@ -125,7 +126,8 @@ class DecodeParams:
 
 
 def decode(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0, trace_iters: int = 0,
-           n_threads: int = 0, w: np.ndarray | None = None, knots: np.ndarray | None = None):
+           n_threads: int = 0, w: np.ndarray | None = None, knots: np.ndarray | None = None,
+           learned_legs: int = -1):
     """Relay-BP on every syndrome row.
 
     Returns dict(corrections, pred_obs, stats[shots,4], weights, trace or None).
@@ -150,7 +152,8 @@ def decode(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0, tra
         lk = None if knots is None else np.ascontiguousarray(knots, dtype=np.float64)
         rc = lib.oracle_relaybp_decode_learned(dem.n_det, dem.n_loc, dem.n_obs, _ptr(Hp), _ptr(Hi), _ptr(Op),
                                                _ptr(Oi), _ptr(pr), ctypes.byref(cp), 0 if lw is None else lw.shape[0],
-                                               _ptr(lw), 0 if lk is None else lk.shape[0] - 1, _ptr(lk), _ptr(syn),
+                                               _ptr(lw), 0 if lk is None else lk.shape[0] - 1, _ptr(lk),
+                                               learned_legs, _ptr(syn),
                                                shot0, shots, _ptr(corr), _ptr(pobs), _ptr(stats), _ptr(wts),
                                                trace_iters, _ptr(trace), n_threads)
     if rc != 0:

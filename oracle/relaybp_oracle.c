@@ -193,6 +193,7 @@ static double sgn(double v) { return v < 0.0 ? -1.0 : 1.0; }   /* sgn(0) = +1 */
 typedef struct {
     int32_t T, K;
     const double *w, *knots;
+    int32_t legs;               /* legs < legs use the learned parameters (< 0: every leg) */
 } learned_t;
 
 static double knot_gamma_l(const double *knots, int32_t K, double u);
@@ -211,9 +212,10 @@ static void decode_one(const graph_t *g, const oracle_params *P, const learned_t
     memset(ehat, 0, (size_t)V);
     for (int32_t leg = 0; leg <= P->num_sets; ++leg) {
         legs++;
+        const int lleg = LP && (LP->legs < 0 || leg < LP->legs);
         for (int32_t j = 0; j < V; ++j) {
             if (leg == 0) gam[j] = P->gamma0;
-            else if (LP && LP->knots) {
+            else if (lleg && LP->knots) {
                 uint64_t nblk = ((uint64_t)V + 3) / 4;
                 uint32_t wd = stream_word(P->seed, shot, 1u, (uint64_t)leg * nblk * 4 + (uint64_t)j);
                 gam[j] = knot_gamma_l(LP->knots, LP->K, (double)(wd >> 8) * (1.0 / 16777216.0));
@@ -236,7 +238,7 @@ static void decode_one(const graph_t *g, const oracle_params *P, const learned_t
                     mu[e] = s;
                 }
             /* a3: min-sum check update, leave-one-out by direct loops */
-            const double *wt = (LP && LP->w) ? LP->w + (int64_t)((t - 1 < LP->T ? t - 1 : LP->T - 1)) * E : NULL;
+            const double *wt = (lleg && LP->w) ? LP->w + (int64_t)((t - 1 < LP->T ? t - 1 : LP->T - 1)) * E : NULL;
             for (int32_t i = 0; i < C; ++i) {
                 double ssign = get_bit(syn, i) ? -1.0 : 1.0;
                 for (int32_t e = g->rptr[i]; e < g->rptr[i + 1]; ++e) {
@@ -322,13 +324,13 @@ int oracle_relaybp_decode_learned(int32_t n_det, int32_t n_loc, int32_t n_obs,
                                   const int32_t *H_indptr, const int32_t *H_indices,
                                   const int32_t *O_indptr, const int32_t *O_indices,
                                   const double *priors, const oracle_params *P,
-                                  int32_t T, const double *w, int32_t K, const double *knots,
+                                  int32_t T, const double *w, int32_t K, const double *knots, int32_t legs,
                                   const uint32_t *syndromes, uint64_t shot0, int64_t shots,
                                   uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
                                   int32_t trace_iters, double *trace, int32_t n_threads)
 {
     if ((w && T < 1) || (knots && K < 1) || (w && P->carry_messages)) return -1;
-    learned_t LP = {T, K, w, knots};
+    learned_t LP = {T, K, w, knots, legs};
     return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, &LP, syndromes,
                        shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, n_threads);
 }

@@ -62,6 +62,7 @@ struct DecodeParamsDev {
     const float *lknots;
     int32_t lT, lK;
     const float *lwrow;         // learned weights tied per check row: [lT][C] (NULL: none)
+    int32_t llegs;              // legs < llegs use the learned parameters (< 0: every leg)
 };
 
 struct StatsDev {               // mirrors relaybp_shot_stats
@@ -401,12 +402,13 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         int legs = 0, iters = 0;
         for (int leg = 0; leg <= p.num_sets; ++leg) {
             ++legs;
+            const bool lleg = LW && (p.llegs < 0 || leg < p.llegs);   // learned parameters in this leg
             if (leg > 0) {
                 // a6: new leg -- fresh strengths, marginals carried over
                 for (int j = tid; j < V; j += nthr) {
                     const C l0 = Num<C>::l0(g, j);
                     C gn;
-                    if (LW && p.lknots) {
+                    if (lleg && p.lknots) {
                         const uint32_t nblk = (uint32_t)((V + 3) / 4);
                         const uint4 rr = philox_block(p.seed, shot, 1u, (uint32_t)leg * nblk + (uint32_t)(j >> 2));
                         const C u = (C)(uint4_word(rr, j & 3) >> 8) * (C)(1.0 / 16777216.0);
@@ -442,11 +444,11 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: check rows, L lanes per row ---------------------------
                 const float *wprev = nullptr, *wcur = nullptr, *wrow = nullptr;
-                if (LW && p.lw) {
+                if (lleg && p.lw) {
                     wprev = p.lw + (int64_t)min(t > 0 ? t - 1 : 0, p.lT - 1) * g.E;
                     wcur = p.lw + (int64_t)min(t, p.lT - 1) * g.E;
                 }
-                if (LW && p.lwrow) wrow = p.lwrow + (int64_t)min(t, p.lT - 1) * g.C;
+                if (lleg && p.lwrow) wrow = p.lwrow + (int64_t)min(t, p.lT - 1) * g.C;
                 if (LW) row_pass<S, L, NB, true>(g, A, cs, sgnh, syn, warp, nwarp, lane, wprev, wrow);
                 else row_pass<S, L, NB, false>(g, A, cs, sgnh, syn, warp, nwarp, lane, nullptr, nullptr);
                 __syncthreads();

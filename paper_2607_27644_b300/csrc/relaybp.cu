@@ -79,6 +79,7 @@ struct relaybp_handle {
     const float *lw = nullptr, *lknots = nullptr;     // learned inference parameters (caller-owned)
     const float *lwrow = nullptr;                     // row-tied learned weights [lT][C]
     int lT = 0, lK = 0;
+    int llegs = -1;                                   // legs using the learned parameters (< 0: all)
     unsigned long long *d_lwork = nullptr;
     void *d_lgbar = nullptr;
     size_t lgbar_bytes = 0;
@@ -322,6 +323,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         J.p.lT = h->lT;
         J.p.lK = h->lK;
         J.p.lwrow = h->lwrow;
+        J.p.llegs = h->llegs;
         if (h->lw || h->lknots || h->lwrow) learned = true;
         J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), L);
         J.syn_in = io[d].syn;
@@ -771,6 +773,15 @@ int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, 
     h->lT = d_wrow ? T : 0;
     h->lknots = d_knots;
     h->lK = d_knots ? K : 0;
+    return 0;
+}
+
+int relaybp_set_learned_legs(relaybp_handle *h, int32_t legs)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (legs < -1) return fail(RELAYBP_ERR_INVALID, "learned legs must be >= -1");
+    h->llegs = legs;
     return 0;
 }
 

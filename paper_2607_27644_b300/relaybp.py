@@ -52,6 +52,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_set_params": ([P, ctypes.POINTER(relaybp_params)], ctypes.c_int),
         "relaybp_set_learned": ([P, P, I32, P, I32], ctypes.c_int),
         "relaybp_set_learned_rows": ([P, P, I32, P, I32], ctypes.c_int),
+        "relaybp_set_learned_legs": ([P, I32], ctypes.c_int),
         "relaybp_sizes": ([P, P, P, P, P], ctypes.c_int),
         "relaybp_sample": ([P, U64, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_batch": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
@@ -82,7 +83,8 @@ def _load() -> ctypes.CDLL:
 
 _lib = _load()
 
-EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
+EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows",
+            "relaybp_set_learned_legs", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
@@ -213,6 +215,10 @@ def relaybp_set_learned_rows(h: Handle, d_wrow=None, d_knots=None):
     K = 0 if d_knots is None else d_knots.shape[0] - 1
     _check(_lib.relaybp_set_learned_rows(h.ptr, _ptr(d_wrow), T, _ptr(d_knots), K), "relaybp_set_learned_rows")
     h._keep = [d_wrow, d_knots]
+
+
+def relaybp_set_learned_legs(h: Handle, legs: int):
+    _check(_lib.relaybp_set_learned_legs(h.ptr, legs), "relaybp_set_learned_legs")
 
 
 def relaybp_sample(h: Handle, seed: int, shot0: int, shots: int, d_syndromes, d_obs=None, d_errors=None,

@@ -202,3 +202,44 @@ def test_row_tied_weights_equal_expanded_per_edge_weights():
         assert np.array_equal(a[k], b[k]), k
     R.relaybp_destroy(ha)
     R.relaybp_destroy(hb)
+
+
+def test_learned_legs_cutoff_matches_oracle():
+    """Learned parameters in legs 0..n-1 and plain legs after: a cutoff of 0
+    is the plain decoder bit for bit; a cutoff of 2 agrees with the oracle's
+    decode under the same cutoff."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode
+    dem = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+    kw = dict(num_sets=60, gamma_min=-0.15, gamma_max=0.61, seed=21, stop_nconv=1)
+    rng = np.random.default_rng(22)
+    T = 8
+    w = rng.uniform(0.75, 1.0, (T, dem.n_edges)).astype(np.float32)
+    knots = np.cumsum(np.r_[-0.15, rng.uniform(0.02, 0.07, 16)]).astype(np.float32)
+    syn, _, _ = oracle.sample(dem, 23, 0, 400)
+    hp = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **kw))
+    hl = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **kw))
+    R.relaybp_set_learned(hl, torch.tensor(w, device="cuda"), torch.tensor(knots, device="cuda"))
+    R.relaybp_set_learned_legs(hl, 0)
+    a, b = gpu_decode(hp, syn), gpu_decode(hl, syn)
+    for k in ("corrections", "pred_obs", "stats", "weights"):
+        assert np.array_equal(a[k], b[k]), k
+    R.relaybp_set_learned_legs(hl, 2)
+    rg = gpu_decode(hl, syn)
+    ro = oracle.decode(dem, oracle.DecodeParams(**kw), syn, w=w.astype(np.float64), knots=knots.astype(np.float64),
+                       learned_legs=2)
+    Hd = dem.dense_H().astype(np.int64)
+    S = unpack_bits(syn, dem.n_det)
+    for r in (ro, rg):
+        eh = unpack_bits(r["corrections"], dem.n_loc).astype(np.int64)
+        conv = r["stats"][:, 0] == 1
+        assert np.array_equal((eh[conv] @ Hd.T) % 2, S[conv])
+    same = np.all(ro["pred_obs"][:, :rg["pred_obs"].shape[1]] == rg["pred_obs"], axis=1)
+    assert (~same).sum() <= 1
+    # legs past the cutoff ran for shots the learned legs left unsettled
+    assert (rg["stats"][:, 2] > 2).any()
+    with pytest.raises(RuntimeError):
+        R.relaybp_set_learned_legs(hl, -2)
+    R.relaybp_destroy(hp)
+    R.relaybp_destroy(hl)

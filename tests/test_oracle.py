@@ -369,3 +369,22 @@ def test_learned_decode_unit_weights_is_plain():
     eh = unpack_bits(c["corrections"], D.n_loc).astype(np.int64)
     conv = c["stats"][:, 0] == 1
     assert np.array_equal((eh[conv] @ Hd.T) % 2, unpack_bits(syn, D.n_det)[conv])
+
+
+def test_learned_legs_cutoff():
+    """learned_legs = 0 is the plain method exactly; a cutoff of 2 agrees with
+    the fully learned decode on shots settled in legs 0 and 1."""
+    D = circuit_dem("ZSZ-LP-60", 0.004, 3, "Z")
+    syn, _, _ = oracle.sample(D, 31, 0, 60)
+    P = DecodeParams(num_sets=10, stop_nconv=2, seed=4)
+    rng = np.random.default_rng(12)
+    w = rng.uniform(0.7, 1.0, (5, D.n_edges))
+    kn = np.linspace(-0.1, 0.5, 17)
+    plain = oracle.decode(D, P, syn)
+    cut0 = oracle.decode(D, P, syn, w=w, knots=kn, learned_legs=0)
+    assert np.array_equal(plain["corrections"], cut0["corrections"]) and np.array_equal(plain["stats"], cut0["stats"])
+    full = oracle.decode(D, P, syn, w=w, knots=kn)
+    cut2 = oracle.decode(D, P, syn, w=w, knots=kn, learned_legs=2)
+    early = full["stats"][:, 2] <= 2
+    assert early.any()
+    assert np.array_equal(full["corrections"][early], cut2["corrections"][early])
