@@ -211,7 +211,7 @@ def test_learned_legs_cutoff_matches_oracle():
     import torch
     from paper_2607_27644_b300 import relaybp as R
     from gpu_util import gpu_decode
-    dem = circuit_dem("ZSZ-LP-160", 0.001, 10, "Z")
+    dem = circuit_dem("ZSZ-LP-160", 0.002, 10, "Z")   # about 8% of shots run past leg 1
     kw = dict(num_sets=60, gamma_min=-0.15, gamma_max=0.61, seed=21, stop_nconv=1)
     rng = np.random.default_rng(22)
     T = 8
