@@ -11,15 +11,16 @@
 // include/relaybp.h.
 //
 // Layout of one shot's decoder state in shared memory (per thread block):
-//   M[V], A[V]        marginal M_j(t) and A_j = L_j(t+1) + sum_i nu_ij(t)
-//   cs[C]             per check row: smallest and second-smallest |mu|, the
-//                     argmin's position in the row | parity << 31 (parity =
-//                     s_i xor the row's mu sign bits), first sign-bit index
-//   sgnh[C*L]         sign bit of mu for every edge, one 16-bit word per
-//                     (row, lane) of the row pass -- see row_pass()
+//   A[V+1], M[V]      A_j = L_j(t+1) + sum_i nu_ij(t) (A[V] = +inf: the dummy
+//                     variable of padded row slots) and the marginal M_j(t)
+//   cs[C+1]           per check row: +-smallest and +-second-smallest |mu|
+//                     (signed by the row parity = s_i xor the row's mu sign
+//                     bits) and the argmin's column code; row C is an empty
+//                     dummy check that padded column slots name
+//   sgw[(C+1)*rw]     sign bit of mu for every edge, by position in the row
 //   ehat[WV], best[WV], res[WC], syn[WC], obsacc[WK]   bit vectors
 // With this compressed check state a message is rebuilt on demand:
-//   nu_ij = (-1)^(parity_i xor sign_e) * (e == argmin_i ? m2_i : m1_i),
+//   nu_ij = (-1)^sign_e * (e == argmin_i ? m2_i : m1_i),
 // which equals the leave-one-out product of signs and minimum of magnitudes.
 #pragma once
 #include <cstdint>
@@ -48,7 +49,18 @@ struct DevDEM {
     const double *L0d;          // [V] prior LLRs, FP64
     const float *L0f;           // [V] prior LLRs rounded to FP32
     const uint32_t *thr;        // [V] floor(p_j 2^32)
+    // branch-free layout of the decode kernel
+    const int32_t *rslot;       // [round_up(C, 32)][kRowStride] row variables, padded with V
+    const uint32_t *ecode;      // sliced ELL (goff / gdeg): column code i << lg_rsp | position, padded
+                                // with the empty dummy check C (code C << lg_rsp)
+    int32_t lg_rsp;             // log2 of the positions per row in the sign words (>= 5)
+    int32_t rw;                 // sign words per row, 2^lg_rsp / 32
 };
+
+constexpr int kRowStride = 512;     // row slots in rslot (the widest row geometry)
+// Column entry of the learned kernels: check index << 12 | position of the
+// entry within its row; padding is COL_SENTINEL.
+constexpr uint32_t COL_SENTINEL = 0xffffffffu;
 
 struct DecodeParamsDev {
     double gamma0, gamma_min, gamma_max;
@@ -162,8 +174,8 @@ __device__ __forceinline__ T draw_gamma(const DecodeParamsDev &p, uint64_t shot,
     return (T)p.gamma_min + ((T)p.gamma_max - (T)p.gamma_min) * u;
 }
 
-struct SmemPlan {               // byte offsets into the per-shot state block
-    int M, A, cs, sgn, ehat, best, res, syn, obsacc, total;
+struct SmemPlan {               // byte offsets into the per-shot state block (A first, at 0)
+    int A, M, cs, sgn, ehat, best, res, syn, obsacc, total;
 };
 
 // Storage precision S of the per-shot state (M, A and the check minima) and
@@ -175,112 +187,145 @@ template <> struct Prec<float> {
     using C = float;
     static __device__ __forceinline__ C ld(float v) { return v; }
     static __device__ __forceinline__ float st(C v) { return v; }
+    static __device__ __forceinline__ float pinf() { return __int_as_float(0x7f800000); }
 };
 template <> struct Prec<double> {
     using C = double;
     static __device__ __forceinline__ C ld(double v) { return v; }
     static __device__ __forceinline__ double st(C v) { return v; }
+    static __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
 };
 template <> struct Prec<__half> {
     using C = float;
     static __device__ __forceinline__ C ld(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half st(C v) { return __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f)); }
+    static __device__ __forceinline__ __half pinf() { return __ushort_as_half((unsigned short)0x7c00u); }
 };
 template <> struct Prec<__nv_bfloat16> {
     using C = float;
     static __device__ __forceinline__ C ld(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 st(C v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 pinf() { return __ushort_as_bfloat16((unsigned short)0x7f80u); }
 };
 
-// Compressed state of one check row: 16 bytes for FP32, 8 for FP16/BF16.
+// Compressed state of one check row.  m1 / m2 carry the row's parity as their
+// sign (parity = s_i xor the row's mu sign bits); meta is the column code
+// (i << lg_rsp | position) of the argmin, so a column entry is the argmin iff
+// its code equals meta.
 template <typename S> struct alignas(16) CheckState {
-    S m1, m2;                   // smallest / second-smallest |mu| over the row
-    uint32_t meta;              // argmin position in the row | parity << 31
+    S m1, m2;                   // +-smallest / +-second-smallest |mu| over the row
+    uint32_t meta;              // column code of the argmin
     float wt;                   // learned weight shared by the row's messages (1 if none)
 };
 
-// Column entry: check index << 12 | position of the entry within its row.
-constexpr uint32_t COL_SENTINEL = 0xffffffffu;
+// Flip the sign of v when bit 31 of s is set (exact: sign-magnitude).
+__device__ __forceinline__ float xsign(float v, uint32_t s) { return __int_as_float(__float_as_int(v) ^ (int)s); }
+__device__ __forceinline__ double xsign(double v, uint32_t s)
+{
+    return __hiloint2double(__double2hiint(v) ^ (int)s, __double2loint(v));
+}
+__device__ __forceinline__ float vmin2(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin2(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vmax2(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax2(double a, double b) { return fmax(a, b); }
 
-// Row pass geometry: L lanes share a row (32 / L rows per warp step); lane l
-// of a row handles positions l, l + L, l + 2L, ... (at most NB of them) and
-// owns one 16-bit word of sign bits, bit b = sign of mu at position b*L + l.
-// The sign bit of position pos of row i therefore lives in halfword
-// i*L + pos % L, bit pos / L.
+// Row pass geometry: L lanes share a row (P = 32 / L rows per warp step); lane
+// l of a row handles positions l, l + L, l + 2L, ... (NB of them).  Padded
+// row slots (rslot, stride kRowStride) name the dummy variable V, whose A is
+// +inf: such a slot yields |mu| = +inf and a clear sign bit, so it changes
+// neither minimum nor parity and needs no test.
+// Sign words: one row's signs of mu are rw = 2^lg_rsp / 32 words, the sign at
+// position p in bit 31 - p % 32 of word p / 32 (reversed, so that a funnel
+// shift by the column code brings it to bit 31).  The P rows of a warp step
+// gather their bits from one ballot per slot.
 template <typename S, int L, int NB, bool LW>
-__device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState<S> *cs, uint16_t *sgnh,
+__device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState<S> *cs, uint32_t *sgw,
                                          const uint32_t *syn, int warp, int nwarp, int lane, const float *wprev,
                                          const float *wrow_new)
 {
     static_assert(32 % L == 0 && NB <= 16, "row geometry");
     using C = typename Prec<S>::C;
-    constexpr int P = 32 / L;
+    constexpr int P = 32 / L;                   // rows per warp step = slots per sign word
+    constexpr int NW = (NB + P - 1) / P;        // sign words spanned by the L * NB positions
+    constexpr uint32_t GM = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
     const unsigned FULL = 0xffffffffu;
     const int r = lane / L, l = lane % L;
-    const int Cn = g.C;
+    const int Cn = g.C, RW = g.rw, lg = g.lg_rsp;
     for (int base = warp * P; base < Cn; base += nwarp * P) {
         const int i = base + r;
-        const bool rowok = i < Cn;
-        int e0 = 0, deg = 0;
-        if (rowok) {
-            e0 = __ldg(g.rptr + i);
-            deg = __ldg(g.rptr + i + 1) - e0;
-        }
+        const int il = min(i, Cn);              // rows past the end read the empty dummy row C
+        const int32_t *rs = g.rslot + (size_t)i * kRowStride + l;
         int idx[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const int k = b * L + l;
-            idx[b] = (k < deg) ? __ldg(g.rvar + e0 + k) : -1;
+        for (int b = 0; b < NB; ++b) idx[b] = __ldg(rs + b * L);
+        const CheckState<S> o = cs[il];
+        C om1 = Prec<S>::ld(o.m1), om2 = Prec<S>::ld(o.m2);
+        if (LW) {                               // row-tied weight of the old messages
+            om1 = mul_rn(om1, (C)o.wt);
+            om2 = mul_rn(om2, (C)o.wt);
         }
-        C om1 = (C)0, om2 = (C)0;
-        uint32_t ometa = 0u, oldbits = 0u;
-        if (rowok) {
-            const CheckState<S> o = cs[i];
-            om1 = Prec<S>::ld(o.m1);
-            om2 = Prec<S>::ld(o.m2);
-            if (LW) {                       // row-tied weight of the old messages
-                om1 = mul_rn(om1, (C)o.wt);
-                om2 = mul_rn(om2, (C)o.wt);
-            }
-            ometa = o.meta;
-            oldbits = sgnh[i * L + l];
+        // slot b holds the argmin iff q == b * L
+        const int q = (int)o.meta - (il << lg) - l;
+        uint32_t W[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t x = (w < RW) ? sgw[il * RW + w] : 0u;
+            W[w] = __funnelshift_l(x, x, l);
         }
-        const uint32_t oarg = ometa & 0xfffu, opar = ometa >> 31;
+        int e0 = 0, deg = 0;
+        if (LW && wprev) {
+            e0 = __ldg(g.rptr + il);
+            deg = (i < Cn) ? __ldg(g.rptr + il + 1) - e0 : 0;
+        }
         C b1 = Num<C>::inf(), b2 = Num<C>::inf();
-        uint32_t bi = 0xfffu, newbits = 0u;
+        int bi = 0;
+        uint32_t bal[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            if (idx[b] >= 0) {
-                const uint32_t k = (uint32_t)(b * L + l);
-                C mag = (k == oarg) ? om2 : om1;
-                if (LW && wprev) mag = mul_rn(mag, (C)__ldg(wprev + e0 + (int)k));
-                const C nu_old = (((oldbits >> b) & 1u) ^ opar) ? -mag : mag;
-                const C m = add_rn(Prec<S>::ld(A[idx[b]]), -nu_old);
-                newbits |= ((m < (C)0) ? 1u : 0u) << b;
-                const C a = vabs(m);
-                if (a < b1) { b2 = b1; b1 = a; bi = k; }
-                else if (a < b2) { b2 = a; }
+            C mag = (q == b * L) ? om2 : om1;
+            if (LW && wprev) {
+                const int pos = b * L + l;
+                mag = mul_rn(mag, (C)((pos < deg) ? __ldg(wprev + e0 + pos) : 1.0f));
             }
+            const uint32_t sb = (W[b / P] << ((b % P) * L)) & 0x80000000u;
+            const C m = add_rn(Prec<S>::ld(A[idx[b]]), -xsign(mag, sb));
+            bal[b] = __ballot_sync(FULL, m < (C)0);
+            const C a = vabs(m);
+            b2 = vmin2(b2, vmax2(b1, a));
+            bi = (a < b1) ? b * L + l : bi;
+            b1 = vmin2(b1, a);
         }
 #pragma unroll
         for (int off = L / 2; off > 0; off >>= 1) {
             const C o1 = __shfl_xor_sync(FULL, b1, off);
             const C o2 = __shfl_xor_sync(FULL, b2, off);
-            const uint32_t oi = __shfl_xor_sync(FULL, bi, off);
+            const int oi = __shfl_xor_sync(FULL, bi, off);
             if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin(b1, o2); b1 = o1; bi = oi; }
             else { b2 = vmin(b2, o1); }
         }
-        const uint32_t lp = __ballot_sync(FULL, (__popc(newbits) & 1) != 0);
-        const uint32_t gm = (L == 32) ? FULL : (((1u << L) - 1u) << (r * L));
-        const uint32_t par = (uint32_t)(__popc(lp & gm) & 1);
-        if (rowok) {
-            sgnh[i * L + l] = (uint16_t)newbits;
+        uint32_t X = 0u;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) X ^= bal[b];
+        const uint32_t par = (uint32_t)(__popc((X >> (r * L)) & GM) & 1);
+        // sign word w of row r: slots wP .. wP + P - 1, L bits each
+        uint32_t mine = 0u;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            uint32_t word = 0u;
+#pragma unroll
+            for (int t = 0; t < P; ++t)
+                if (w * P + t < NB) word |= ((bal[w * P + t] >> (r * L)) & GM) << (t * L);
+            mine = (l == w) ? word : mine;
+        }
+        if (i < Cn) {
+            if (l < NW && l < RW) sgw[i * RW + l] = __brev(mine);
             if (l == 0) {
                 const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
+                const bool neg = (par ^ sb) != 0u;
                 CheckState<S> n;
-                n.m1 = Prec<S>::st(b1);
-                n.m2 = Prec<S>::st(b2);
-                n.meta = bi | ((par ^ sb) << 31);
+                n.m1 = Prec<S>::st(neg ? -b1 : b1);
+                n.m2 = Prec<S>::st(neg ? -b2 : b2);
+                n.meta = ((uint32_t)i << lg) + (uint32_t)bi;
                 n.wt = (LW && wrow_new) ? __ldg(wrow_new + i) : 1.0f;
                 cs[i] = n;
             }
@@ -365,9 +410,9 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         double *trace = J.trace;
         const int trace_iters = J.trace_iters;
         S *M = reinterpret_cast<S *>(base + plan.M);
-        S *A = reinterpret_cast<S *>(base + plan.A);
+        S *A = reinterpret_cast<S *>(base);     // plan.A == 0: gathers need no base offset
         CheckState<S> *cs = reinterpret_cast<CheckState<S> *>(base + plan.cs);
-        uint16_t *sgnh = reinterpret_cast<uint16_t *>(base + plan.sgn);
+        uint32_t *sgw = reinterpret_cast<uint32_t *>(base + plan.sgn);
         uint32_t *ehat = reinterpret_cast<uint32_t *>(base + plan.ehat);
         uint32_t *best = reinterpret_cast<uint32_t *>(base + plan.best);
         uint32_t *res = reinterpret_cast<uint32_t *>(base + plan.res);
@@ -376,6 +421,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         const int Cn = g.C, V = g.V;
         const int WC = wordsof(Cn), WV = wordsof(V), WK = wordsof(g.K);
         const int NG = WV;      // variable groups of 32 (one ELL slice each)
+        const int lg = g.lg_rsp, NSW = (Cn + 1) * g.rw;
 
         // ---- shot start: M = L0, leg-0 strengths, zero messages ------------
         for (int j = tid; j < V; j += nthr) {
@@ -385,12 +431,13 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             gam[j] = gm;
             A[j] = Prec<S>::st(memprior<C>(gm, l0, l0));
         }
-        for (int i = tid; i < Cn; i += nthr) {
+        if (tid == 0) A[V] = Prec<S>::pinf();               // the dummy variable of padded row slots (+inf)
+        for (int i = tid; i <= Cn; i += nthr) {             // row C: the empty dummy check
             CheckState<S> z;
             z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u; z.wt = 1.0f;
             cs[i] = z;
         }
-        for (int w = tid; w < Cn * L; w += nthr) sgnh[w] = (uint16_t)0;
+        for (int w = tid; w < NSW; w += nthr) sgw[w] = 0u;
         for (int w = tid; w < WV; w += nthr) ehat[w] = 0u;
         for (int w = tid; w < WC; w += nthr) {
             const uint32_t sv = syn_in[sidx * WC + w];
@@ -435,7 +482,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                         z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u; z.wt = 1.0f;
                         cs[i] = z;
                     }
-                    for (int w = tid; w < Cn * L; w += nthr) sgnh[w] = (uint16_t)0;
+                    for (int w = tid; w < Cn * g.rw; w += nthr) sgw[w] = 0u;
                 }
                 __syncthreads();
             }
@@ -449,8 +496,8 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     wcur = p.lw + (int64_t)min(t, p.lT - 1) * g.E;
                 }
                 if (lleg && p.lwrow) wrow = p.lwrow + (int64_t)min(t, p.lT - 1) * g.C;
-                if (LW) row_pass<S, L, NB, true>(g, A, cs, sgnh, syn, warp, nwarp, lane, wprev, wrow);
-                else row_pass<S, L, NB, false>(g, A, cs, sgnh, syn, warp, nwarp, lane, nullptr, nullptr);
+                if (LW) row_pass<S, L, NB, true>(g, A, cs, sgw, syn, warp, nwarp, lane, wprev, wrow);
+                else row_pass<S, L, NB, false>(g, A, cs, sgw, syn, warp, nwarp, lane, nullptr, nullptr);
                 __syncthreads();
                 // ---- a4: variables, one lane per variable, ELL slices --------
                 for (int G = warp; G < NG; G += nwarp) {
@@ -459,22 +506,21 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     const C l0 = act ? Num<C>::l0(g, j) : (C)0;
                     const C gm = act ? gam[j] : (C)0;
                     const int D = __ldg(g.gdeg + G);
-                    const uint32_t *col = g.cinfo + __ldg(g.goff + G) + lane;
-                    const uint32_t *cel = g.cedge_ell + __ldg(g.goff + G) + lane;
+                    const int go = __ldg(g.goff + G);
+                    const uint32_t *col = g.ecode + go + lane;
+                    const uint32_t *cel = g.cedge_ell + go + lane;
                     C Ssum = (C)0;
-                    // column messages nu_ij rebuilt from the check states; four
+                    // column messages nu_ij rebuilt from the check states; padded
+                    // slots name the dummy check C, whose message is +0.  Four
                     // independent slots per step, the remainder one by one (D is
                     // uniform over the warp, so the split does not diverge)
-                    auto msg = [&](uint32_t c, int slot) -> C {
-                        const uint32_t i = c >> 12;
-                        const CheckState<S> q = cs[i];
-                        const uint32_t pos = c & 0xfffu;
-                        const uint32_t hw = sgnh[i * L + (pos % L)];
-                        C mag = Prec<S>::ld((pos == (q.meta & 0xfffu)) ? q.m2 : q.m1);
+                    auto msg = [&](uint32_t e, int slot) -> C {
+                        const CheckState<S> q = cs[e >> lg];
+                        const uint32_t hw = sgw[e >> 5];
+                        C mag = Prec<S>::ld((e == q.meta) ? q.m2 : q.m1);
                         if (LW) mag = mul_rn(mag, (C)q.wt);
                         if (LW && wcur) mag = mul_rn(mag, (C)__ldg(wcur + __ldg(cel + slot * 32)));
-                        const uint32_t sb = ((hw >> (pos / L)) & 1u) ^ (q.meta >> 31);
-                        return sb ? -mag : mag;
+                        return xsign(mag, __funnelshift_l(hw, hw, e) & 0x80000000u);
                     };
                     int k = 0;
                     for (; k + 4 <= D; k += 4) {
@@ -482,13 +528,9 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
 #pragma unroll
                         for (int u = 0; u < 4; ++u) c[u] = __ldg(col + (k + u) * 32);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (c[u] != COL_SENTINEL) Ssum = add_rn(Ssum, msg(c[u], k + u));
+                        for (int u = 0; u < 4; ++u) Ssum = add_rn(Ssum, msg(c[u], k + u));
                     }
-                    for (; k < D; ++k) {
-                        const uint32_t c = __ldg(col + k * 32);
-                        if (c != COL_SENTINEL) Ssum = add_rn(Ssum, msg(c, k));
-                    }
+                    for (; k < D; ++k) Ssum = add_rn(Ssum, msg(__ldg(col + k * 32), k));
                     uint32_t dec = 0u;
                     if (act) {
                         const C Mn = add_rn(memprior<C>(gm, l0, Prec<S>::ld(M[j])), Ssum);
@@ -505,9 +547,8 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     // a5: residual r = s + H e^ kept incrementally
                     if (((old ^ nw) >> lane) & 1u) {
                         for (int k = 0; k < D; ++k) {
-                            const uint32_t cc = __ldg(col + k * 32);
-                            if (cc == COL_SENTINEL) break;
-                            const uint32_t i = cc >> 12;
+                            const uint32_t i = __ldg(col + k * 32) >> lg;
+                            if (i >= (uint32_t)Cn) break;          // padding (the dummy check)
                             atomicXor(res + (i >> 5), 1u << (i & 31));
                         }
                     }

@@ -168,10 +168,10 @@ SmemPlan make_plan(const DevDEM &g, size_t esz, size_t csz, int L)
         off += bytes;
         return (int)at;
     };
+    s.A = take(esz * ((size_t)g.V + 1));            // first: the row pass gathers A[j] at offset 0
     s.M = take(esz * g.V);
-    s.A = take(esz * g.V);
-    s.cs = take(csz * (size_t)g.C);
-    s.sgn = take(2 * (size_t)g.C * (size_t)L);      // row_pass: one 16-bit sign word per (row, lane)
+    s.cs = take(csz * ((size_t)g.C + 1));           // + the empty dummy check
+    s.sgn = take(4 * ((size_t)g.C + 1) * (size_t)g.rw);
     s.ehat = take(4 * (size_t)words(g.V));
     s.best = take(4 * (size_t)words(g.V));
     s.res = take(4 * (size_t)words(g.C));
@@ -315,6 +315,9 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
     int64_t total = 0;
     for (int d = 0; d < n; ++d) {
         const relaybp_handle *h = hs[d];
+        if (!h->dem.rslot)
+            return fail(RELAYBP_ERR_UNSUPPORTED, "DEM %d: rows of %d entries exceed the decode kernel's %d", d,
+                        h->max_row_deg, kRowStride);
         DecodeJob &J = tab.job[d];
         J.g = h->dem;
         J.p = dev_params(h->params);
@@ -690,6 +693,28 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
             cedge_ell[(size_t)goff[G] + (size_t)k * 32 + l] = (uint32_t)cedge[cptr[j] + k];
         }
     }
+    // branch-free layout of the decode kernel: padded rows (dummy variable V)
+    // and column codes i << lg_rsp | position (dummy check C)
+    int32_t maxdeg = 0;
+    for (int32_t i = 0; i < C; ++i) maxdeg = std::max(maxdeg, rptr[i + 1] - rptr[i]);
+    int32_t lg_rsp = 5;
+    while ((1 << lg_rsp) < maxdeg) ++lg_rsp;
+    std::vector<int32_t> rslot;
+    std::vector<uint32_t> ecode((size_t)goff[NG], (uint32_t)C << lg_rsp);
+    if (maxdeg <= kRowStride && ((uint64_t)C + 1) << lg_rsp <= 0xffffffffull) {
+        const int32_t CP = (C + 31) / 32 * 32;
+        rslot.assign((size_t)std::max(CP, 32) * kRowStride, V);
+        for (int32_t i = 0; i < C; ++i)
+            for (int32_t e = rptr[i]; e < rptr[i + 1]; ++e) rslot[(size_t)i * kRowStride + (e - rptr[i])] = rvar[e];
+        for (int32_t j = 0; j < V; ++j) {
+            const int32_t G = j / 32, l = j % 32;
+            for (int32_t k = 0; k < cptr[j + 1] - cptr[j]; ++k) {
+                const int32_t i = cchk[cptr[j] + k];
+                const int32_t pos = cedge[cptr[j] + k] - rptr[i];
+                ecode[(size_t)goff[G] + (size_t)k * 32 + l] = ((uint32_t)i << lg_rsp) | (uint32_t)pos;
+            }
+        }
+    }
     // observables per column
     std::vector<int32_t> optr(V + 1, 0), oidx;
     if (obs) {
@@ -717,11 +742,14 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     for (int32_t i = 0; i < C; ++i) h->max_row_deg = std::max(h->max_row_deg, rptr[i + 1] - rptr[i]);
     DevDEM &g = h->dem;
     g.C = C; g.V = V; g.K = K; g.E = E;
+    g.lg_rsp = lg_rsp;
+    g.rw = 1 << (lg_rsp - 5);
     int rc = 0;
     if ((rc = upload(h, rptr, &g.rptr)) || (rc = upload(h, rvar, &g.rvar)) || 
         (rc = upload(h, cptr, &g.cptr)) || (rc = upload(h, cchk, &g.cchk)) || 
         (rc = upload(h, cedge, &g.cedge)) || (rc = upload(h, cinfo, &g.cinfo)) || (rc = upload(h, cedge_ell, &g.cedge_ell)) || (rc = upload(h, goff, &g.goff)) ||
-        (rc = upload(h, gdeg, &g.gdeg)) ||
+        (rc = upload(h, gdeg, &g.gdeg)) || (rc = upload(h, ecode, &g.ecode)) ||
+        (!rslot.empty() && (rc = upload(h, rslot, &g.rslot))) ||
         (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
         (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
         return bail(rc);
