@@ -228,6 +228,31 @@ __device__ __forceinline__ float vmin2(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double vmin2(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float vmax2(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double vmax2(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vabs2(float a) { return fabsf(a); }
+__device__ __forceinline__ double vabs2(double a) { return fabs(a); }
+
+// Sign word w of row r of a warp step from the step's slot ballots: slots
+// wP .. wP + P - 1 (P = 32 / L), L bits each, bit t*L + l = lane l of slot
+// wP + t.  Positional order; the caller reverses it.
+template <int L, int NB>
+__device__ __forceinline__ uint32_t sign_word(const uint32_t (&bal)[NB], int w, int r)
+{
+    constexpr int P = 32 / L;
+    auto at = [&](int b) -> uint32_t { return b < NB ? bal[b] : 0u; };
+    if (L == 32) return at(w);
+    if (L == 16) return __byte_perm(at(2 * w), at(2 * w + 1), r ? 0x7632u : 0x5410u);
+    if (L == 8) {
+        const uint32_t sel = (uint32_t)r | ((uint32_t)(r + 4) << 4);
+        const uint32_t lo = __byte_perm(at(4 * w), at(4 * w + 1), sel);
+        const uint32_t hi = __byte_perm(at(4 * w + 2), at(4 * w + 3), sel);
+        return __byte_perm(lo, hi, 0x5410u);
+    }
+    constexpr uint32_t GM = (1u << L) - 1u;
+    uint32_t word = 0u;
+#pragma unroll
+    for (int t = 0; t < P; ++t) word |= ((at(w * P + t) >> (r * L)) & GM) << (t * L);
+    return word;
+}
 
 // Row pass geometry: L lanes share a row (P = 32 / L rows per warp step); lane
 // l of a row handles positions l, l + L, l + 2L, ... (NB of them).  Padded
@@ -251,13 +276,25 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
     const unsigned FULL = 0xffffffffu;
     const int r = lane / L, l = lane % L;
     const int Cn = g.C, RW = g.rw, lg = g.lg_rsp;
-    for (int base = warp * P; base < Cn; base += nwarp * P) {
+    // the next warp step's row slots load while this one computes
+    const int stride = nwarp * P;
+    int nidx[NB];
+    if (warp * P < Cn) {
+        const int32_t *rs = g.rslot + (size_t)(warp * P + r) * kRowStride + l;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) nidx[b] = __ldg(rs + b * L);
+    }
+    for (int base = warp * P; base < Cn; base += stride) {
         const int i = base + r;
         const int il = min(i, Cn);              // rows past the end read the empty dummy row C
-        const int32_t *rs = g.rslot + (size_t)i * kRowStride + l;
         int idx[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) idx[b] = __ldg(rs + b * L);
+        for (int b = 0; b < NB; ++b) idx[b] = nidx[b];
+        if (base + stride < Cn) {
+            const int32_t *rs = g.rslot + (size_t)(i + stride) * kRowStride + l;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) nidx[b] = __ldg(rs + b * L);
+        }
         const CheckState<S> o = cs[il];
         C om1 = Prec<S>::ld(o.m1), om2 = Prec<S>::ld(o.m2);
         if (LW) {                               // row-tied weight of the old messages
@@ -278,7 +315,7 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             deg = (i < Cn) ? __ldg(g.rptr + il + 1) - e0 : 0;
         }
         C b1 = Num<C>::inf(), b2 = Num<C>::inf();
-        int bi = 0;
+        int bs = 0;                             // slot of the lane's smallest |mu|
         uint32_t bal[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -290,11 +327,12 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             const uint32_t sb = (W[b / P] << ((b % P) * L)) & 0x80000000u;
             const C m = add_rn(Prec<S>::ld(A[idx[b]]), -xsign(mag, sb));
             bal[b] = __ballot_sync(FULL, m < (C)0);
-            const C a = vabs(m);
+            const C a = vabs2(m);
             b2 = vmin2(b2, vmax2(b1, a));
-            bi = (a < b1) ? b * L + l : bi;
+            bs = (a < b1) ? b : bs;
             b1 = vmin2(b1, a);
         }
+        int bi = bs * L + l;
 #pragma unroll
         for (int off = L / 2; off > 0; off >>= 1) {
             const C o1 = __shfl_xor_sync(FULL, b1, off);
@@ -307,14 +345,10 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
 #pragma unroll
         for (int b = 0; b < NB; ++b) X ^= bal[b];
         const uint32_t par = (uint32_t)(__popc((X >> (r * L)) & GM) & 1);
-        // sign word w of row r: slots wP .. wP + P - 1, L bits each
-        uint32_t mine = 0u;
+        uint32_t mine = 0u;                     // lane l of the row stores sign word l
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            uint32_t word = 0u;
-#pragma unroll
-            for (int t = 0; t < P; ++t)
-                if (w * P + t < NB) word |= ((bal[w * P + t] >> (r * L)) & GM) << (t * L);
+            const uint32_t word = sign_word<L, NB>(bal, w, r);
             mine = (l == w) ? word : mine;
         }
         if (i < Cn) {
@@ -365,7 +399,7 @@ struct JobTable {
 // GS: per-shot state in a per-block region of global memory (gstate,
 // state_stride bytes per block, L2-resident) instead of shared memory.
 template <typename S, int L, int NB, bool GS, bool LW>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, GS ? 1 : 2)
 relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__restrict__ work,
                     typename Prec<S>::C *__restrict__ gamma_scratch, int vmax,
                     unsigned char *__restrict__ gstate, size_t state_stride)
@@ -541,9 +575,9 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                             trace[((int64_t)sidx * trace_iters + iters) * V + j] = (double)Mn;
                     }
                     const uint32_t nw = __ballot_sync(FULL, dec);
-                    uint32_t old = 0u;
-                    if (lane == 0) { old = ehat[G]; ehat[G] = nw; }
-                    old = __shfl_sync(FULL, old, 0);
+                    const uint32_t old = ehat[G];       // every lane reads, then lane 0 writes
+                    __syncwarp();
+                    if (lane == 0) ehat[G] = nw;
                     // a5: residual r = s + H e^ kept incrementally
                     if (((old ^ nw) >> lane) & 1u) {
                         for (int k = 0; k < D; ++k) {
