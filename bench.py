@@ -53,7 +53,7 @@ def _args():
     ap.add_argument("--train-steps", type=int, default=300, help="learned: Adam steps of 512 shots at p=0.2%%")
     ap.add_argument("--learned-msg", default="bf16", choices=["bf16", "f16", "f32"], help="learned: message storage")
     ap.add_argument("--mixed-base", type=int, default=2000, help="mixed: shots per unit of the 2:5:10 mix")
-    ap.add_argument("--msg", default=None, choices=["f16", "bf16", "f32"],
+    ap.add_argument("--msg", default=None, choices=["f16", "bf16", "f32", "i8"],
                     help="message storage (default: f32 for zsz160, f16 for mixed)")
     return ap.parse_args()
 
@@ -328,7 +328,7 @@ def run_ours(a):
     iters_rank = int(iters_total.item())
     wall_s = ms / 1e3
     E, V, C = dem.n_edges, dem.n_loc, dem.n_det
-    b_m = {"f32": 4, "f16": 2, "bf16": 2}[msg]
+    b_m = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "i8": 1}[msg]
     bytes_per_iter = 4 * b_m * E + 16 * V + (V + C) / 8.0
     dec_avg_s = sum(dec_ms) / len(dec_ms) / 1e3
     per_launch = (iters_rank / K) * bytes_per_iter / dec_avg_s / 1e9

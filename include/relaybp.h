@@ -59,7 +59,9 @@ enum {                           /* message storage precision */
     RELAYBP_MSG_F64 = 0,         /* FP64 storage and arithmetic */
     RELAYBP_MSG_F32 = 1,         /* FP32 storage and arithmetic (the paper's proc_float = fp32) */
     RELAYBP_MSG_F16 = 2,         /* FP16 storage (saturating at +-65504), FP32 arithmetic */
-    RELAYBP_MSG_BF16 = 3         /* BF16 storage, FP32 arithmetic */
+    RELAYBP_MSG_BF16 = 3,        /* BF16 storage, FP32 arithmetic */
+    RELAYBP_MSG_I8 = 4           /* scaled int8 storage, FP32 arithmetic: q = clamp(rne(v / int8_scale),
+                                    -127, 127), v = q * int8_scale */
 };
 
 /* Compressed sparse rows of a binary matrix, host memory.
@@ -82,7 +84,8 @@ typedef struct {
     int32_t msg_dtype;          /* RELAYBP_MSG_* */
     int32_t stop_all;           /* 1: run every leg regardless of solutions (the paper's 'All') */
     int32_t carry_messages;     /* 1: keep check-to-variable messages across legs */
-    int32_t reserved;           /* must be 0 */
+    float int8_scale;           /* RELAYBP_MSG_I8: value of one int8 step, > 0, or 0 for the automatic
+                                   scale (largest prior LLR / 24, per DEM); must be 0 for the other forms */
     uint64_t seed;              /* key of the memory-strength draws */
 } relaybp_params;
 

@@ -75,6 +75,7 @@ struct DecodeParamsDev {
     int32_t lT, lK;
     const float *lwrow;         // learned weights tied per check row: [lT][C] (NULL: none)
     int32_t llegs;              // legs < llegs use the learned parameters (< 0: every leg)
+    float qscale;               // int8 storage: value of one step
 };
 
 struct StatsDev {               // mirrors relaybp_shot_stats
@@ -178,34 +179,56 @@ struct SmemPlan {               // byte offsets into the per-shot state block (A
     int A, M, cs, sgn, ehat, best, res, syn, obsacc, total;
 };
 
+// Scale of the int8 storage form: value = q * s, q = clamp(rne(value / s),
+// -127, 127); code -128 stands for +inf.  Unused by the other forms.
+struct QScale {
+    float s;
+};
+
 // Storage precision S of the per-shot state (M, A and the check minima) and
 // the arithmetic precision C it is computed in: FP64 and FP32 store what they
-// compute; FP16 and BF16 store rounded values and compute in FP32.  FP16
-// stores saturate at +-65504 (the largest finite half).
+// compute; FP16, BF16 and int8 store rounded values and compute in FP32.  FP16
+// stores saturate at +-65504 (the largest finite half), int8 at +-127 steps.
 template <typename S> struct Prec;
 template <> struct Prec<float> {
     using C = float;
-    static __device__ __forceinline__ C ld(float v) { return v; }
-    static __device__ __forceinline__ float st(C v) { return v; }
+    static __device__ __forceinline__ C ld(float v, const QScale &) { return v; }
+    static __device__ __forceinline__ float st(C v, const QScale &) { return v; }
     static __device__ __forceinline__ float pinf() { return __int_as_float(0x7f800000); }
 };
 template <> struct Prec<double> {
     using C = double;
-    static __device__ __forceinline__ C ld(double v) { return v; }
-    static __device__ __forceinline__ double st(C v) { return v; }
+    static __device__ __forceinline__ C ld(double v, const QScale &) { return v; }
+    static __device__ __forceinline__ double st(C v, const QScale &) { return v; }
     static __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000LL); }
 };
 template <> struct Prec<__half> {
     using C = float;
-    static __device__ __forceinline__ C ld(__half v) { return __half2float(v); }
-    static __device__ __forceinline__ __half st(C v) { return __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f)); }
+    static __device__ __forceinline__ C ld(__half v, const QScale &) { return __half2float(v); }
+    static __device__ __forceinline__ __half st(C v, const QScale &)
+    {
+        return __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f));
+    }
     static __device__ __forceinline__ __half pinf() { return __ushort_as_half((unsigned short)0x7c00u); }
 };
 template <> struct Prec<__nv_bfloat16> {
     using C = float;
-    static __device__ __forceinline__ C ld(__nv_bfloat16 v) { return __bfloat162float(v); }
-    static __device__ __forceinline__ __nv_bfloat16 st(C v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ C ld(__nv_bfloat16 v, const QScale &) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 st(C v, const QScale &) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 pinf() { return __ushort_as_bfloat16((unsigned short)0x7f80u); }
+};
+template <> struct Prec<int8_t> {
+    using C = float;
+    static __device__ __forceinline__ C ld(int8_t q, const QScale &qs)
+    {
+        return q == (int8_t)-128 ? __int_as_float(0x7f800000) : __fmul_rn((float)q, qs.s);
+    }
+    static __device__ __forceinline__ int8_t st(C v, const QScale &qs)
+    {
+        const int q = __float2int_rn(__fdiv_rn(v, qs.s));          // round half to even
+        return (int8_t)max(-127, min(127, q));
+    }
+    static __device__ __forceinline__ int8_t pinf() { return (int8_t)-128; }
 };
 
 // Compressed state of one check row.  m1 / m2 carry the row's parity as their
@@ -266,7 +289,7 @@ __device__ __forceinline__ uint32_t sign_word(const uint32_t (&bal)[NB], int w, 
 template <typename S, int L, int NB, bool LW>
 __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState<S> *cs, uint32_t *sgw,
                                          const uint32_t *syn, int warp, int nwarp, int lane, const float *wprev,
-                                         const float *wrow_new)
+                                         const float *wrow_new, const QScale &qs)
 {
     static_assert(32 % L == 0 && NB <= 16, "row geometry");
     using C = typename Prec<S>::C;
@@ -296,7 +319,7 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             for (int b = 0; b < NB; ++b) nidx[b] = __ldg(rs + b * L);
         }
         const CheckState<S> o = cs[il];
-        C om1 = Prec<S>::ld(o.m1), om2 = Prec<S>::ld(o.m2);
+        C om1 = Prec<S>::ld(o.m1, qs), om2 = Prec<S>::ld(o.m2, qs);
         if (LW) {                               // row-tied weight of the old messages
             om1 = mul_rn(om1, (C)o.wt);
             om2 = mul_rn(om2, (C)o.wt);
@@ -325,7 +348,7 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
                 mag = mul_rn(mag, (C)((pos < deg) ? __ldg(wprev + e0 + pos) : 1.0f));
             }
             const uint32_t sb = (W[b / P] << ((b % P) * L)) & 0x80000000u;
-            const C m = add_rn(Prec<S>::ld(A[idx[b]]), -xsign(mag, sb));
+            const C m = add_rn(Prec<S>::ld(A[idx[b]], qs), -xsign(mag, sb));
             bal[b] = __ballot_sync(FULL, m < (C)0);
             const C a = vabs2(m);
             b2 = vmin2(b2, vmax2(b1, a));
@@ -357,8 +380,8 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
                 const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
                 const bool neg = (par ^ sb) != 0u;
                 CheckState<S> n;
-                n.m1 = Prec<S>::st(neg ? -b1 : b1);
-                n.m2 = Prec<S>::st(neg ? -b2 : b2);
+                n.m1 = Prec<S>::st(neg ? -b1 : b1, qs);
+                n.m2 = Prec<S>::st(neg ? -b2 : b2, qs);
                 n.meta = ((uint32_t)i << lg) + (uint32_t)bi;
                 n.wt = (LW && wrow_new) ? __ldg(wrow_new + i) : 1.0f;
                 cs[i] = n;
@@ -456,19 +479,20 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         const int WC = wordsof(Cn), WV = wordsof(V), WK = wordsof(g.K);
         const int NG = WV;      // variable groups of 32 (one ELL slice each)
         const int lg = g.lg_rsp, NSW = (Cn + 1) * g.rw;
+        const QScale qs{p.qscale};
 
         // ---- shot start: M = L0, leg-0 strengths, zero messages ------------
         for (int j = tid; j < V; j += nthr) {
             const C l0 = Num<C>::l0(g, j);
             const C gm = (C)p.gamma0;
-            M[j] = Prec<S>::st(l0);
+            M[j] = Prec<S>::st(l0, qs);
             gam[j] = gm;
-            A[j] = Prec<S>::st(memprior<C>(gm, l0, l0));
+            A[j] = Prec<S>::st(memprior<C>(gm, l0, l0), qs);
         }
         if (tid == 0) A[V] = Prec<S>::pinf();               // the dummy variable of padded row slots (+inf)
         for (int i = tid; i <= Cn; i += nthr) {             // row C: the empty dummy check
             CheckState<S> z;
-            z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u; z.wt = 1.0f;
+            z.m1 = Prec<S>::st((C)0, qs); z.m2 = Prec<S>::st((C)0, qs); z.meta = 0u; z.wt = 1.0f;
             cs[i] = z;
         }
         for (int w = tid; w < NSW; w += nthr) sgw[w] = 0u;
@@ -501,19 +525,19 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     } else {
                         gn = draw_gamma<C>(p, shot, leg, j, V);
                     }
-                    const C Mj = Prec<S>::ld(M[j]);
+                    const C Mj = Prec<S>::ld(M[j], qs);
                     C carry = (C)0;
                     if (p.carry_messages) {
                         const C go = gam[j];
-                        carry = add_rn(Prec<S>::ld(A[j]), -memprior<C>(go, l0, Mj));
+                        carry = add_rn(Prec<S>::ld(A[j], qs), -memprior<C>(go, l0, Mj));
                     }
                     gam[j] = gn;
-                    A[j] = Prec<S>::st(add_rn(memprior<C>(gn, l0, Mj), carry));
+                    A[j] = Prec<S>::st(add_rn(memprior<C>(gn, l0, Mj), carry), qs);
                 }
                 if (!p.carry_messages) {
                     for (int i = tid; i < Cn; i += nthr) {
                         CheckState<S> z;
-                        z.m1 = Prec<S>::st((C)0); z.m2 = Prec<S>::st((C)0); z.meta = 0u; z.wt = 1.0f;
+                        z.m1 = Prec<S>::st((C)0, qs); z.m2 = Prec<S>::st((C)0, qs); z.meta = 0u; z.wt = 1.0f;
                         cs[i] = z;
                     }
                     for (int w = tid; w < Cn * g.rw; w += nthr) sgw[w] = 0u;
@@ -530,8 +554,8 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     wcur = p.lw + (int64_t)min(t, p.lT - 1) * g.E;
                 }
                 if (lleg && p.lwrow) wrow = p.lwrow + (int64_t)min(t, p.lT - 1) * g.C;
-                if (LW) row_pass<S, L, NB, true>(g, A, cs, sgw, syn, warp, nwarp, lane, wprev, wrow);
-                else row_pass<S, L, NB, false>(g, A, cs, sgw, syn, warp, nwarp, lane, nullptr, nullptr);
+                if (LW) row_pass<S, L, NB, true>(g, A, cs, sgw, syn, warp, nwarp, lane, wprev, wrow, qs);
+                else row_pass<S, L, NB, false>(g, A, cs, sgw, syn, warp, nwarp, lane, nullptr, nullptr, qs);
                 __syncthreads();
                 // ---- a4: variables, one lane per variable, ELL slices --------
                 for (int G = warp; G < NG; G += nwarp) {
@@ -551,7 +575,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     auto msg = [&](uint32_t e, int slot) -> C {
                         const CheckState<S> q = cs[e >> lg];
                         const uint32_t hw = sgw[e >> 5];
-                        C mag = Prec<S>::ld((e == q.meta) ? q.m2 : q.m1);
+                        C mag = Prec<S>::ld((e == q.meta) ? q.m2 : q.m1, qs);
                         if (LW) mag = mul_rn(mag, (C)q.wt);
                         if (LW && wcur) mag = mul_rn(mag, (C)__ldg(wcur + __ldg(cel + slot * 32)));
                         return xsign(mag, __funnelshift_l(hw, hw, e) & 0x80000000u);
@@ -567,9 +591,9 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     for (; k < D; ++k) Ssum = add_rn(Ssum, msg(__ldg(col + k * 32), k));
                     uint32_t dec = 0u;
                     if (act) {
-                        const C Mn = add_rn(memprior<C>(gm, l0, Prec<S>::ld(M[j])), Ssum);
-                        M[j] = Prec<S>::st(Mn);
-                        A[j] = Prec<S>::st(add_rn(memprior<C>(gm, l0, Mn), Ssum));
+                        const C Mn = add_rn(memprior<C>(gm, l0, Prec<S>::ld(M[j], qs)), Ssum);
+                        M[j] = Prec<S>::st(Mn, qs);
+                        A[j] = Prec<S>::st(add_rn(memprior<C>(gm, l0, Mn), Ssum), qs);
                         dec = (Mn < (C)0) ? 1u : 0u;
                         if (trace && iters < trace_iters)
                             trace[((int64_t)sidx * trace_iters + iters) * V + j] = (double)Mn;

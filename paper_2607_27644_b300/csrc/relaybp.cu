@@ -74,6 +74,7 @@ struct relaybp_handle {
     int64_t stage_shots = 0;
     int64_t launches = 0;
     int max_row_deg = 0;
+    double l0max = 0.0;             // largest prior LLR (automatic int8 scale)
     // learned-form training scratch: work counter and one gradient row per block
     int tuned_L = 0, tuned_NB = 0, tuned_threads = 0; // autotuned launch shape (0: heuristic)
     const float *lw = nullptr, *lknots = nullptr;     // learned inference parameters (caller-owned)
@@ -134,9 +135,10 @@ int check_params(const relaybp_params *p)
         p->gamma_min > p->gamma_max)
         return fail(RELAYBP_ERR_INVALID, "memory strengths must be finite with gamma_min <= gamma_max");
     if (p->msg_dtype != RELAYBP_MSG_F64 && p->msg_dtype != RELAYBP_MSG_F32 && p->msg_dtype != RELAYBP_MSG_F16 &&
-        p->msg_dtype != RELAYBP_MSG_BF16)
+        p->msg_dtype != RELAYBP_MSG_BF16 && p->msg_dtype != RELAYBP_MSG_I8)
         return fail(RELAYBP_ERR_UNSUPPORTED, "msg_dtype %d not supported", p->msg_dtype);
-    if (p->reserved != 0) return fail(RELAYBP_ERR_INVALID, "reserved field must be 0");
+    if (p->msg_dtype == RELAYBP_MSG_I8 ? !(p->int8_scale >= 0.0f && p->int8_scale < 1e30f) : p->int8_scale != 0.0f)
+        return fail(RELAYBP_ERR_INVALID, "int8_scale must be finite and >= 0 for int8 storage, 0 otherwise");
     return 0;
 }
 
@@ -327,6 +329,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         J.p.lK = h->lK;
         J.p.lwrow = h->lwrow;
         J.p.llegs = h->llegs;
+        J.p.qscale = h->params.int8_scale > 0.0f ? h->params.int8_scale : (float)(h->l0max / 24.0);
         if (h->lw || h->lknots || h->lwrow) learned = true;
         J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), L);
         J.syn_in = io[d].syn;
@@ -416,6 +419,7 @@ int launch_jobs_dtype(relaybp_handle *const *hs, const JobIO *io, int n, Scratch
     case RELAYBP_MSG_F64: return launch_jobs_geom<double>(hs, io, n, sc, st, on_chip_only);
     case RELAYBP_MSG_F16: return launch_jobs_geom<__half>(hs, io, n, sc, st, on_chip_only);
     case RELAYBP_MSG_BF16: return launch_jobs_geom<__nv_bfloat16>(hs, io, n, sc, st, on_chip_only);
+    case RELAYBP_MSG_I8: return launch_jobs_geom<int8_t>(hs, io, n, sc, st, on_chip_only);
     default: return launch_jobs_geom<float>(hs, io, n, sc, st, on_chip_only);
     }
 }
@@ -740,6 +744,7 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
         thr[j] = t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
     }
     for (int32_t i = 0; i < C; ++i) h->max_row_deg = std::max(h->max_row_deg, rptr[i + 1] - rptr[i]);
+    for (int32_t j = 0; j < V; ++j) h->l0max = std::max(h->l0max, L0d[j]);
     DevDEM &g = h->dem;
     g.C = C; g.V = V; g.K = K; g.E = E;
     g.lg_rsp = lg_rsp;

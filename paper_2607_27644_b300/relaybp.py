@@ -21,7 +21,9 @@ RELAYBP_MSG_F64 = 0
 RELAYBP_MSG_F32 = 1
 RELAYBP_MSG_F16 = 2
 RELAYBP_MSG_BF16 = 3
-_DTYPES = {"f64": RELAYBP_MSG_F64, "f32": RELAYBP_MSG_F32, "f16": RELAYBP_MSG_F16, "bf16": RELAYBP_MSG_BF16}
+RELAYBP_MSG_I8 = 4
+_DTYPES = {"f64": RELAYBP_MSG_F64, "f32": RELAYBP_MSG_F32, "f16": RELAYBP_MSG_F16, "bf16": RELAYBP_MSG_BF16,
+           "i8": RELAYBP_MSG_I8}
 
 
 class relaybp_csr(ctypes.Structure):
@@ -34,7 +36,7 @@ class relaybp_params(ctypes.Structure):
                 ("max_iterations", ctypes.c_int32), ("stop_nconv", ctypes.c_int32),
                 ("gamma_min", ctypes.c_double), ("gamma_max", ctypes.c_double),
                 ("msg_dtype", ctypes.c_int32), ("stop_all", ctypes.c_int32),
-                ("carry_messages", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("carry_messages", ctypes.c_int32), ("int8_scale", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
 STATS_BYTES = 24      # sizeof(relaybp_shot_stats)
@@ -129,11 +131,12 @@ class Params:
     stop_all: bool = False
     carry_messages: bool = False
     seed: int = 0
+    int8_scale: float = 0.0      # int8 storage: value of one step (0: largest prior LLR / 24)
 
     def c(self) -> relaybp_params:
         return relaybp_params(self.gamma0, self.pre_iter, self.num_sets, self.max_iterations, self.stop_nconv,
                               self.gamma_min, self.gamma_max, _DTYPES[self.msg_dtype], int(self.stop_all),
-                              int(self.carry_messages), 0, self.seed)
+                              int(self.carry_messages), float(self.int8_scale), self.seed)
 
 
 @dataclass

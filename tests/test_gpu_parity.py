@@ -242,6 +242,31 @@ def test_low_precision_storage_circuit_level(circ160, dtype, tol):
     _logical_parity(circ160, ro, rg, syn, obs)
 
 
+def test_int8_storage_circuit_level(circ160):
+    """Scaled int8 storage (FP32 arithmetic), automatic scale s = largest prior
+    LLR / 24.  Bound after the first iteration, from the arithmetic: M(0) and
+    A carry at most s/2 of rounding each; a check minimum over inputs off by
+    s/2 is off by s/2 and storing it adds s/2, so each message is within s;
+    hence |M_j(1) - oracle| <= (gamma0 / 2 + deg_j) s (plus FP32 rounding).
+    Beyond it the decoder's answer, validity and the LER band."""
+    from gpu_util import gpu_decode, params_pair
+    po, pg = params_pair(msg_dtype="i8", **CIRC_KW)
+    h = _handle(circ160, pg)
+    s = float(np.log((1 - circ160.priors) / circ160.priors).max()) / 24.0
+    deg = np.bincount(circ160.H_indices, minlength=circ160.n_loc)     # column degrees
+    sub, _, _ = oracle.sample(circ160, 9, 20_000, 10)
+    rot = oracle.decode(circ160, po, sub, shot0=0, trace_iters=1)
+    rgs = gpu_decode(h, sub, shot0=0, trace_iters=1)
+    bound = (CIRC_KW["gamma0"] / 2 + deg) * s * 1.001 + 1e-4
+    for s_ in range(sub.shape[0]):
+        err = np.abs(rgs["trace"][s_][0] - rot["trace"][s_][0])
+        assert np.all(err <= bound), (s_, float((err / bound).max()))
+    syn, obs, _ = oracle.sample(circ160, 9, 20_000, 400)
+    ro = oracle.decode(circ160, po, syn, shot0=20_000)
+    rg = gpu_decode(h, syn, shot0=20_000)
+    _logical_parity(circ160, ro, rg, syn, obs)
+
+
 @pytest.fixture(scope="module")
 def circ320():
     return circuit_dem("ZSZ-LP-320", 0.001, 14, "Z")
