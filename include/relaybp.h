@@ -200,6 +200,19 @@ int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d_syndromes,
                                  uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
                                  void *cuda_stream);
 
+/* relaybp_decode_batch that also records, per shot, the device clock
+ * (%globaltimer, nanoseconds) when a thread block starts decoding it and when
+ * it retires: d_times [shots][2] = {start, retire}, device memory, required.
+ * retire - start is the shot's decoding latency; retire minus the launch
+ * time adds its wait in the batch.  Outputs otherwise equal those of
+ * relaybp_decode_batch, except that FP64 handles always take the compressed
+ * FP64 kernel here (the literal-order kernel records no times).  The paper
+ * reports per-shot decoding latency (Sec. 6.1, App. F, Table 12); this call
+ * measures the same quantity for a batched decoder. */
+int relaybp_decode_timed(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                         uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
+                         uint64_t *d_times, void *cuda_stream);
+
 /* Diagnostic variant of relaybp_decode_batch for parity checks: also writes
  * the marginals M_j after each of the first trace_iters iterations (counted
  * over all legs) to d_trace [shots][trace_iters][V] as FP64 (entries past a

@@ -85,6 +85,14 @@ struct StatsDev {               // mirrors relaybp_shot_stats
 
 __device__ __forceinline__ int wordsof(int64_t bits) { return (int)((bits + 31) >> 5); }
 
+// Device-wide clock in nanoseconds (the %globaltimer register).
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // a2: fault sampler.  One warp per shot; the warp's syndrome / observable /
 // error words are accumulated in shared memory and written out coalesced.
@@ -403,6 +411,7 @@ struct DecodeJob {
     StatsDev *stats_out;
     double *trace;
     int trace_iters;
+    uint64_t *times_out;        // [shots][2] device clock (ns) at shot start and retire, or NULL
 };
 
 constexpr int kMaxJobs = 16;
@@ -432,6 +441,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
     unsigned char *base = GS ? gstate + (size_t)blockIdx.x * state_stride : smem;
 
     __shared__ long long s_shot;
+    __shared__ unsigned long long s_t0;
     __shared__ int s_job, s_nsol, s_have_best, s_copy;
     __shared__ double s_best_w, s_w;
 
@@ -451,6 +461,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             s_nsol = 0;
             s_have_best = 0;
             s_best_w = 0.0;
+            s_t0 = globaltimer_ns();
         }
         __syncthreads();
         if (s_shot >= total) break;
@@ -688,6 +699,10 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             st.iters = iters;
             st.weight = s_w;
             stats_out[sidx] = st;
+        }
+        if (J.times_out && tid == 0) {
+            J.times_out[2 * sidx] = s_t0;
+            J.times_out[2 * sidx + 1] = globaltimer_ns();
         }
         __syncthreads();
     }

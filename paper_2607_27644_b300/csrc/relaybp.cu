@@ -275,6 +275,7 @@ struct JobIO {
     StatsDev *stats;
     double *trace;
     int trace_iters;
+    uint64_t *times = nullptr;
 };
 
 // FP64 in the literal evaluation order when one shot's per-edge messages fit
@@ -340,6 +341,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         J.stats_out = io[d].stats;
         J.trace = io[d].trace;
         J.trace_iters = io[d].trace_iters;
+        J.times_out = io[d].times;
         tab.start[d] = total;
         total += io[d].shots;
         plan_max = std::max(plan_max, J.plan.total);
@@ -427,7 +429,7 @@ int launch_jobs_dtype(relaybp_handle *const *hs, const JobIO *io, int n, Scratch
 // Single-DEM decode: the literal-order FP64 kernel when it applies, else one job.
 int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, bool on_chip_only)
 {
-    if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots && !h->lwrow) {
+    if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots && !h->lwrow && !io.times) {
         int rc = launch_decode_exact(h, sc, io, st);
         if (rc <= 0) return rc;
     }
@@ -869,6 +871,20 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     static_assert(sizeof(StatsDev) == sizeof(relaybp_shot_stats), "stats layout");
     const JobIO io{d_syndromes, shot0, shots, d_corrections, d_pred_obs, reinterpret_cast<StatsDev *>(d_stats),
                    nullptr, 0};
+    return decode_single(h, h->scratch, io, static_cast<cudaStream_t>(cuda_stream), false);
+}
+
+int relaybp_decode_timed(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                         uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
+                         uint64_t *d_times, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (shots == 0) return 0;
+    if (!d_syndromes || !d_times) return fail(RELAYBP_ERR_INVALID, "null pointer");
+    JobIO io{d_syndromes, shot0, shots, d_corrections, d_pred_obs, reinterpret_cast<StatsDev *>(d_stats), nullptr, 0};
+    io.times = d_times;
     return decode_single(h, h->scratch, io, static_cast<cudaStream_t>(cuda_stream), false);
 }
 

@@ -58,6 +58,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_sizes": ([P, P, P, P, P], ctypes.c_int),
         "relaybp_sample": ([P, U64, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_batch": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
+        "relaybp_decode_timed": ([P, P, U64, I64, P, P, P, P, P], ctypes.c_int),
         "relaybp_decode_trace": ([P, P, U64, I64, I32, P, P, P], ctypes.c_int),
         "relaybp_decode_batch_noalloc": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_host": ([P, P, U64, I64, P, P, P], ctypes.c_int),
@@ -87,7 +88,7 @@ _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows",
             "relaybp_set_learned_legs", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
-            "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
+            "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
             "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
@@ -234,6 +235,14 @@ def relaybp_decode_batch(h: Handle, d_syndromes, shot0: int, shots: int, d_corre
                          d_stats=None, stream=None):
     _check(_lib.relaybp_decode_batch(h.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections),
                                      _ptr(d_pred_obs), _ptr(d_stats), _stream(stream)), "relaybp_decode_batch")
+
+
+def relaybp_decode_timed(h: Handle, d_syndromes, shot0: int, shots: int, d_times, d_corrections=None,
+                         d_pred_obs=None, d_stats=None, stream=None):
+    """relaybp_decode_batch recording each shot's device clock at start and retire
+    into d_times [shots][2] (int64 tensor, nanoseconds)."""
+    _check(_lib.relaybp_decode_timed(h.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections), _ptr(d_pred_obs),
+                                     _ptr(d_stats), _ptr(d_times), _stream(stream)), "relaybp_decode_timed")
 
 
 def relaybp_decode_batch_noalloc(h: Handle, d_syndromes, shot0: int, shots: int, d_corrections=None,

@@ -267,6 +267,34 @@ def test_int8_storage_circuit_level(circ160):
     _logical_parity(circ160, ro, rg, syn, obs)
 
 
+def test_decode_timed_records_latency(circ160):
+    """relaybp_decode_timed: outputs equal relaybp_decode_batch; every shot gets
+    a start and a later retire time, and latency grows with the iterations."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from gpu_util import gpu_decode, params_pair, to_dev
+    _, pg = params_pair(msg_dtype="f32", **dict(CIRC_KW, num_sets=100))
+    h = _handle(circ160, pg)
+    syn, _, _ = oracle.sample(circ160, 13, 0, 300)
+    ref = gpu_decode(h, syn)
+    n = syn.shape[0]
+    corr = torch.zeros((n, h.wv), dtype=torch.int32, device="cuda")
+    pobs = torch.zeros((n, h.wk), dtype=torch.int32, device="cuda")
+    stats = torch.zeros((n, 6), dtype=torch.int32, device="cuda")
+    times = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    R.relaybp_decode_timed(h, to_dev(syn), 0, n, times, corr, pobs, stats)
+    torch.cuda.synchronize()
+    assert np.array_equal(corr.cpu().numpy().view(np.uint32), ref["corrections"])
+    assert np.array_equal(pobs.cpu().numpy().view(np.uint32), ref["pred_obs"])
+    assert np.array_equal(stats.cpu().numpy()[:, :4], ref["stats"])
+    t = times.cpu().numpy()
+    assert np.all(t[:, 0] > 0) and np.all(t[:, 1] > t[:, 0])
+    service = (t[:, 1] - t[:, 0]).astype(np.float64)
+    assert np.corrcoef(service, ref["stats"][:, 3])[0, 1] > 0.5
+    with pytest.raises(RuntimeError):
+        R.relaybp_decode_timed(h, to_dev(syn), 0, n, None)
+
+
 @pytest.fixture(scope="module")
 def circ320():
     return circuit_dem("ZSZ-LP-320", 0.001, 14, "Z")
