@@ -183,8 +183,12 @@ __device__ __forceinline__ T draw_gamma(const DecodeParamsDev &p, uint64_t shot,
     return (T)p.gamma_min + ((T)p.gamma_max - (T)p.gamma_min) * u;
 }
 
-struct SmemPlan {               // byte offsets into the per-shot state block (A first, at 0)
-    int A, M, cs, sgn, ehat, best, res, syn, obsacc, total;
+// Byte offsets of one shot's state, A first (at 0) and the rest in falling
+// order of access intensity.  Bytes [0, split) live in shared memory, the rest
+// in the block's region of global memory at (offset - split); split == total
+// when everything fits on chip.
+struct SmemPlan {
+    int A, cs, ehat, res, syn, obsacc, sgn, M, best, total, split;
 };
 
 // Scale of the int8 storage form: value = q * s, q = clamp(rne(value / s),
@@ -428,8 +432,9 @@ struct JobTable {
 // counter, finds its job and decodes that shot with the job's DEM, so shots of
 // all DEMs share the SMs and a block whose shot ends early moves on at once.
 // S: storage precision; L, NB: row geometry (for the longest row of any job);
-// GS: per-shot state in a per-block region of global memory (gstate,
-// state_stride bytes per block, L2-resident) instead of shared memory.
+// GS: the per-shot state does not fit in shared memory: the plan's hottest
+// prefix stays there and the rest goes to a per-block region of global memory
+// (gstate, state_stride bytes per block, L2-resident).
 template <typename S, int L, int NB, bool GS, bool LW>
 __global__ void __launch_bounds__(512, GS ? 1 : 2)
 relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__restrict__ work,
@@ -438,7 +443,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
 {
     using C = typename Prec<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned char *base = GS ? gstate + (size_t)blockIdx.x * state_stride : smem;
+    unsigned char *gblk = GS ? gstate + (size_t)blockIdx.x * state_stride : nullptr;
 
     __shared__ long long s_shot;
     __shared__ unsigned long long s_t0;
@@ -477,15 +482,21 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         StatsDev *stats_out = J.stats_out;
         double *trace = J.trace;
         const int trace_iters = J.trace_iters;
-        S *M = reinterpret_cast<S *>(base + plan.M);
-        S *A = reinterpret_cast<S *>(base);     // plan.A == 0: gathers need no base offset
-        CheckState<S> *cs = reinterpret_cast<CheckState<S> *>(base + plan.cs);
-        uint32_t *sgw = reinterpret_cast<uint32_t *>(base + plan.sgn);
-        uint32_t *ehat = reinterpret_cast<uint32_t *>(base + plan.ehat);
-        uint32_t *best = reinterpret_cast<uint32_t *>(base + plan.best);
-        uint32_t *res = reinterpret_cast<uint32_t *>(base + plan.res);
-        uint32_t *syn = reinterpret_cast<uint32_t *>(base + plan.syn);
-        uint32_t *obsacc = reinterpret_cast<uint32_t *>(base + plan.obsacc);
+        // on chip: everything in shared memory, A at its start (gathers need
+        // no base offset); off chip: the plan's prefix in shared memory
+        auto place = [&](int off) -> unsigned char * {
+            if (!GS) return smem + off;
+            return off < plan.split ? smem + off : gblk + (off - plan.split);
+        };
+        S *M = reinterpret_cast<S *>(place(plan.M));
+        S *A = reinterpret_cast<S *>(GS ? place(plan.A) : smem);
+        CheckState<S> *cs = reinterpret_cast<CheckState<S> *>(place(plan.cs));
+        uint32_t *sgw = reinterpret_cast<uint32_t *>(place(plan.sgn));
+        uint32_t *ehat = reinterpret_cast<uint32_t *>(place(plan.ehat));
+        uint32_t *best = reinterpret_cast<uint32_t *>(place(plan.best));
+        uint32_t *res = reinterpret_cast<uint32_t *>(place(plan.res));
+        uint32_t *syn = reinterpret_cast<uint32_t *>(place(plan.syn));
+        uint32_t *obsacc = reinterpret_cast<uint32_t *>(place(plan.obsacc));
         const int Cn = g.C, V = g.V;
         const int WC = wordsof(Cn), WV = wordsof(V), WK = wordsof(g.K);
         const int NG = WV;      // variable groups of 32 (one ELL slice each)

@@ -160,26 +160,34 @@ RowGeom row_geom(int maxdeg)
     return {0, 0};
 }
 
-SmemPlan make_plan(const DevDEM &g, size_t esz, size_t csz, int L)
+// One shot's state in falling order of access intensity: A (gathered per edge
+// by the row pass), the check states and the bit vectors (per column entry /
+// per variable group), the sign words, M (streamed once per variable), best
+// (per solution).  `budget` = shared-memory bytes available: split = the end
+// of the longest prefix of whole arrays that fits (everything when it all
+// fits).
+SmemPlan make_plan(const DevDEM &g, size_t esz, size_t csz, size_t budget)
 {
     SmemPlan s{};
-    size_t off = 0;
+    size_t off = 0, split = 0;
     auto take = [&](size_t bytes) {
         off = (off + 15) & ~size_t(15);
         size_t at = off;
         off += bytes;
+        if (((split + 15) & ~size_t(15)) == at && off <= budget) split = off;
         return (int)at;
     };
     s.A = take(esz * ((size_t)g.V + 1));            // first: the row pass gathers A[j] at offset 0
-    s.M = take(esz * g.V);
     s.cs = take(csz * ((size_t)g.C + 1));           // + the empty dummy check
-    s.sgn = take(4 * ((size_t)g.C + 1) * (size_t)g.rw);
     s.ehat = take(4 * (size_t)words(g.V));
-    s.best = take(4 * (size_t)words(g.V));
     s.res = take(4 * (size_t)words(g.C));
     s.syn = take(4 * (size_t)words(g.C));
     s.obsacc = take(4 * (size_t)std::max(1, words(g.K)));
+    s.sgn = take(4 * ((size_t)g.C + 1) * (size_t)g.rw);
+    s.M = take(esz * g.V);
+    s.best = take(4 * (size_t)words(g.V));
     s.total = (int)((off + 15) & ~size_t(15));
+    s.split = (size_t)s.total <= budget ? s.total : (int)((split + 15) & ~size_t(15));
     return s;
 }
 
@@ -332,7 +340,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         J.p.llegs = h->llegs;
         J.p.qscale = h->params.int8_scale > 0.0f ? h->params.int8_scale : (float)(h->l0max / 24.0);
         if (h->lw || h->lknots || h->lwrow) learned = true;
-        J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), L);
+        J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), (size_t)-1);
         J.syn_in = io[d].syn;
         J.shot0 = io[d].shot0;
         J.shots = io[d].shots;
@@ -356,22 +364,34 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
     // shared-memory state when one shot's state fits, else a per-block region
     // of global memory (one block per SM keeps the regions L2-resident)
     const bool gs = plan_max + 1024 > maxsm;
+    // off chip: each job keeps its plan's hottest prefix in shared memory
+    int smem_gs = 0, gbytes = 0;
+    if (gs) {
+        for (int d = 0; d < n; ++d) {
+            DecodeJob &J = tab.job[d];
+            J.plan = make_plan(hs[d]->dem, sizeof(S), sizeof(CheckState<S>), (size_t)(maxsm - 1024));
+            smem_gs = std::max(smem_gs, J.plan.split);
+            gbytes = std::max(gbytes, J.plan.total - J.plan.split);
+        }
+    }
     if (gs && on_chip_only)
         return fail(RELAYBP_ERR_UNSUPPORTED, "one shot's decoder state (%d bytes) exceeds shared memory (%d bytes); "
                     "the allocation-free entry point keeps it on chip only: use relaybp_decode_batch",
                     plan_max, maxsm);
     int64_t resident = num_sms;
-    if (!gs) {
-        auto kern = learned ? relay_decode_kernel<S, L, NB, false, true> : relay_decode_kernel<S, L, NB, false, false>;
-        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan_max));
+    {
+        auto kern = gs ? (learned ? relay_decode_kernel<S, L, NB, true, true> : relay_decode_kernel<S, L, NB, true, false>)
+                       : (learned ? relay_decode_kernel<S, L, NB, false, true> : relay_decode_kernel<S, L, NB, false, false>);
+        const int dyn = gs ? smem_gs : plan_max;
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
         int per_sm = 0;
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, plan_max));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
         if (per_sm < 1)
-            return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", plan_max);
+            return fail(RELAYBP_ERR_UNSUPPORTED, "decode kernel cannot be resident with %d bytes", dyn);
         resident = (int64_t)per_sm * num_sms;
     }
     int64_t blocks = std::min<int64_t>(resident, total);
-    const size_t stride = ((size_t)plan_max + 255) & ~(size_t)255;
+    const size_t stride = ((size_t)std::max(gbytes, 16) + 255) & ~(size_t)255;
     const size_t gamma_need = (size_t)(sc.fixed ? blocks : resident) * vmax * sizeof(C);
     if (int rc = scratch_reserve(sc, gamma_need, gs ? (size_t)resident * stride : 0)) return rc;
     CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
@@ -382,10 +402,10 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         relay_decode_kernel<S, L, NB, false, true><<<(unsigned)blocks, threads, plan_max, st>>>(
             tab, sc.work, static_cast<C *>(sc.gamma), vmax, nullptr, 0);
     else if (!learned)
-        relay_decode_kernel<S, L, NB, true, false><<<(unsigned)blocks, threads, 0, st>>>(
+        relay_decode_kernel<S, L, NB, true, false><<<(unsigned)blocks, threads, smem_gs, st>>>(
             tab, sc.work, static_cast<C *>(sc.gamma), vmax, sc.gstate, stride);
     else
-        relay_decode_kernel<S, L, NB, true, true><<<(unsigned)blocks, threads, 0, st>>>(
+        relay_decode_kernel<S, L, NB, true, true><<<(unsigned)blocks, threads, smem_gs, st>>>(
             tab, sc.work, static_cast<C *>(sc.gamma), vmax, sc.gstate, stride);
     CUDA_TRY(cudaGetLastError());
     return 0;
