@@ -128,8 +128,10 @@ int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const fl
 
 /* Same with weights tied per check row: d_wrow [T][C], the weight of every
  * message check i sends in iteration t+1 of a leg (the per-edge weights with
- * w[t][e] = d_wrow[t][row of e]).  The weight travels in the row's compressed
- * state, so decoding costs one multiply per message and no extra loads.
+ * w[t][e] = d_wrow[t][row of e]).  The weight is applied once per row when
+ * the row's compressed state is formed, so decoding costs no extra loads and
+ * no per-message multiply.  With FP16/BF16/int8 storage the weighted minima
+ * are what is rounded (per-edge weights multiply after the rounding).
  * Replaces any per-edge weights. */
 int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, const float *d_knots, int32_t K);
 

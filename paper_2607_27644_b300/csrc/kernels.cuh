@@ -244,13 +244,14 @@ template <> struct Prec<int8_t> {
 };
 
 // Compressed state of one check row.  m1 / m2 carry the row's parity as their
-// sign (parity = s_i xor the row's mu sign bits); meta is the column code
-// (i << lg_rsp | position) of the argmin, so a column entry is the argmin iff
-// its code equals meta.
-template <typename S> struct alignas(16) CheckState {
-    S m1, m2;                   // +-smallest / +-second-smallest |mu| over the row
+// sign (parity = s_i xor the row's mu sign bits) and, in the learned form with
+// row-tied weights, the weight of the messages they stand for; meta is the
+// column code (i << lg_rsp | position) of the argmin, so a column entry is the
+// argmin iff its code equals meta.  16 bytes for FP32 (one 16-byte load), 32
+// for FP64, 8 for FP16 / BF16 / int8.
+template <typename S> struct alignas(sizeof(S) >= 4 ? 16 : 8) CheckState {
+    S m1, m2;                   // +-(w) smallest / +-(w) second-smallest |mu| over the row
     uint32_t meta;              // column code of the argmin
-    float wt;                   // learned weight shared by the row's messages (1 if none)
 };
 
 // Flip the sign of v when bit 31 of s is set (exact: sign-magnitude).
@@ -331,11 +332,7 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             for (int b = 0; b < NB; ++b) nidx[b] = __ldg(rs + b * L);
         }
         const CheckState<S> o = cs[il];
-        C om1 = Prec<S>::ld(o.m1, qs), om2 = Prec<S>::ld(o.m2, qs);
-        if (LW) {                               // row-tied weight of the old messages
-            om1 = mul_rn(om1, (C)o.wt);
-            om2 = mul_rn(om2, (C)o.wt);
-        }
+        const C om1 = Prec<S>::ld(o.m1, qs), om2 = Prec<S>::ld(o.m2, qs);     // weighted when learned
         // slot b holds the argmin iff q == b * L
         const int q = (int)o.meta - (il << lg) - l;
         uint32_t W[NW];
@@ -391,11 +388,16 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             if (l == 0) {
                 const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
                 const bool neg = (par ^ sb) != 0u;
+                C v1 = neg ? -b1 : b1, v2 = neg ? -b2 : b2;
+                if (LW && wrow_new) {           // row-tied weight of the messages just formed
+                    const C wn = (C)__ldg(wrow_new + i);
+                    v1 = mul_rn(v1, wn);
+                    v2 = mul_rn(v2, wn);
+                }
                 CheckState<S> n;
-                n.m1 = Prec<S>::st(neg ? -b1 : b1, qs);
-                n.m2 = Prec<S>::st(neg ? -b2 : b2, qs);
+                n.m1 = Prec<S>::st(v1, qs);
+                n.m2 = Prec<S>::st(v2, qs);
                 n.meta = ((uint32_t)i << lg) + (uint32_t)bi;
-                n.wt = (LW && wrow_new) ? __ldg(wrow_new + i) : 1.0f;
                 cs[i] = n;
             }
         }
@@ -514,7 +516,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         if (tid == 0) A[V] = Prec<S>::pinf();               // the dummy variable of padded row slots (+inf)
         for (int i = tid; i <= Cn; i += nthr) {             // row C: the empty dummy check
             CheckState<S> z;
-            z.m1 = Prec<S>::st((C)0, qs); z.m2 = Prec<S>::st((C)0, qs); z.meta = 0u; z.wt = 1.0f;
+            z.m1 = Prec<S>::st((C)0, qs); z.m2 = Prec<S>::st((C)0, qs); z.meta = 0u;
             cs[i] = z;
         }
         for (int w = tid; w < NSW; w += nthr) sgw[w] = 0u;
@@ -559,7 +561,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                 if (!p.carry_messages) {
                     for (int i = tid; i < Cn; i += nthr) {
                         CheckState<S> z;
-                        z.m1 = Prec<S>::st((C)0, qs); z.m2 = Prec<S>::st((C)0, qs); z.meta = 0u; z.wt = 1.0f;
+                        z.m1 = Prec<S>::st((C)0, qs); z.m2 = Prec<S>::st((C)0, qs); z.meta = 0u;
                         cs[i] = z;
                     }
                     for (int w = tid; w < Cn * g.rw; w += nthr) sgw[w] = 0u;
@@ -598,7 +600,6 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                         const CheckState<S> q = cs[e >> lg];
                         const uint32_t hw = sgw[e >> 5];
                         C mag = Prec<S>::ld((e == q.meta) ? q.m2 : q.m1, qs);
-                        if (LW) mag = mul_rn(mag, (C)q.wt);
                         if (LW && wcur) mag = mul_rn(mag, (C)__ldg(wcur + __ldg(cel + slot * 32)));
                         return xsign(mag, __funnelshift_l(hw, hw, e) & 0x80000000u);
                     };
