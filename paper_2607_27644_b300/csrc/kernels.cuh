@@ -389,7 +389,7 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
                 const uint32_t sb = (syn[i >> 5] >> (i & 31)) & 1u;
                 const bool neg = (par ^ sb) != 0u;
                 C v1 = neg ? -b1 : b1, v2 = neg ? -b2 : b2;
-                if (LW && wrow_new) {           // row-tied weight of the messages just formed
+                if (wrow_new) {                 // row-tied weight of the messages just formed
                     const C wn = (C)__ldg(wrow_new + i);
                     v1 = mul_rn(v1, wn);
                     v2 = mul_rn(v2, wn);
@@ -531,7 +531,9 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         int legs = 0, iters = 0;
         for (int leg = 0; leg <= p.num_sets; ++leg) {
             ++legs;
-            const bool lleg = LW && (p.llegs < 0 || leg < p.llegs);   // learned parameters in this leg
+            // learned parameters in this leg (row-tied weights and knots act
+            // outside the inner loops; LW kernels add per-edge weights)
+            const bool lleg = (p.lw || p.lwrow || p.lknots) && (p.llegs < 0 || leg < p.llegs);
             if (leg > 0) {
                 // a6: new leg -- fresh strengths, marginals carried over
                 for (int j = tid; j < V; j += nthr) {
@@ -573,13 +575,13 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: check rows, L lanes per row ---------------------------
                 const float *wprev = nullptr, *wcur = nullptr, *wrow = nullptr;
-                if (lleg && p.lw) {
+                if (LW && lleg && p.lw) {
                     wprev = p.lw + (int64_t)min(t > 0 ? t - 1 : 0, p.lT - 1) * g.E;
                     wcur = p.lw + (int64_t)min(t, p.lT - 1) * g.E;
                 }
                 if (lleg && p.lwrow) wrow = p.lwrow + (int64_t)min(t, p.lT - 1) * g.C;
                 if (LW) row_pass<S, L, NB, true>(g, A, cs, sgw, syn, warp, nwarp, lane, wprev, wrow, qs);
-                else row_pass<S, L, NB, false>(g, A, cs, sgw, syn, warp, nwarp, lane, nullptr, nullptr, qs);
+                else row_pass<S, L, NB, false>(g, A, cs, sgw, syn, warp, nwarp, lane, nullptr, wrow, qs);
                 __syncthreads();
                 // ---- a4: variables, one lane per variable, ELL slices --------
                 for (int G = warp; G < NG; G += nwarp) {

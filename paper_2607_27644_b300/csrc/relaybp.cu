@@ -339,7 +339,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         J.p.lwrow = h->lwrow;
         J.p.llegs = h->llegs;
         J.p.qscale = h->params.int8_scale > 0.0f ? h->params.int8_scale : (float)(h->l0max / 24.0);
-        if (h->lw || h->lknots || h->lwrow) learned = true;
+        if (h->lw) learned = true;      // per-edge weights; row-tied weights and knots run in the plain kernel
         J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), (size_t)-1);
         J.syn_in = io[d].syn;
         J.shot0 = io[d].shot0;
