@@ -340,7 +340,7 @@ def run_ours(a):
     # DRAM bytes of one 3,000-shot decode launch (ncu, same kernel build), scaled
     # by shots to one launch of this run: the state stays on chip, DRAM carries
     # syndromes in and results out
-    traffic = 1.12896e6 * B / 3000 if (msg == "f32" and B >= 3000) else None
+    traffic = 1.132544e6 * B / 3000 if (msg == "f32" and B >= 3000) else None
     roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
             "traffic": traffic,
             "kernel": f"relay_decode_kernel<{msg}>",
