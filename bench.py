@@ -177,7 +177,11 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "shots/s", "n_gpus": 1, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox-sampled syndromes of the circuit DEM)",
-            "config": _config(dem, n, a.steps, 1, {"arm": "FP64 CPU oracle, OpenMP over shots"}),
+            "config": _config(dem, n, a.steps, 1, {"arm": "FP64 CPU oracle, OpenMP over shots",
+                                                    "l2": "n/a (host CPU)",
+                                                    "parallelism": f"{cores} host threads over the shots of a step",
+                                                    "sample": f"{n} shots per step, a bounded sample of the "
+                                                              "workload"}),
             "cpu_baseline": {"value": v, "unit": "shots/s", "cores": cores, "kind": "oracle",
                              "sample": f"{n} shots per step x {a.steps} steps"},
             "e2e": {"value": v, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

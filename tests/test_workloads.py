@@ -210,3 +210,53 @@ def test_multi_p_builder_matches_single():
     for D in many:
         one = circuit_dem("ZSZ-LP-60", D.meta["p"], 3, "Z")
         assert np.array_equal(D.H_indices, one.H_indices) and np.array_equal(D.priors, one.priors)
+
+
+@pytest.mark.parametrize("basis,n_single,n_cx", [("Z", None, 200), ("X", 120, 60)])
+def test_dem_faults_match_tableau_simulation(basis, n_single, n_cx):
+    """The DEM builder's per-fault detector and observable flips against an
+    independent stabilizer-tableau simulation of the same circuit (CHP,
+    Aaronson-Gottesman 2004), on the [[60,12,6]] code with 2 rounds: the
+    noiseless circuit gives all detectors and observables 0 under random
+    measurement outcomes; every reset and measurement fault and a seeded
+    sample of the CNOT Pauli components flip exactly what the Pauli-frame
+    propagation says; and each such flip pattern is a column of the DEM."""
+    from chp import run_memory_circuit
+    from workloads.dem import _count_faults, _frame_sim, _set_bits_by_fault
+    code = load_code("ZSZ-LP-60")
+    circ, info = memory_circuit(code, 2, basis)
+    for seed in range(3):
+        d, o = run_memory_circuit(circ, info, None, seed)
+        assert not d.any() and not o.any()
+    nf = _count_faults(circ)
+    rec, _ = _frame_sim(circ, 0.001, 0, nf)
+    fa, row = _set_bits_by_fault(rec, nf)
+    R = np.zeros((nf, circ.n_kept), dtype=np.int64)
+    R[fa, row] = 1
+    Dm = np.zeros((circ.n_kept, len(info["detectors"])), dtype=np.int64)
+    for k, rows in enumerate(info["detectors"]):
+        Dm[rows, k] = 1
+    Om = np.zeros((circ.n_kept, len(info["observables"])), dtype=np.int64)
+    for k, rows in enumerate(info["observables"]):
+        Om[rows, k] = 1
+    FD, FO = (R @ Dm) % 2, (R @ Om) % 2
+    # fault ids: resets and measurements by op, CNOT components sampled
+    single, cx = [], []
+    base = 0
+    for op in circ.ops:
+        n_op = len(op[1]) * (15 if op[0] == "CX" else 1)
+        (cx if op[0] == "CX" else single).extend(range(base, base + n_op))
+        base += n_op
+    assert base == nf
+    rng = np.random.default_rng(7)
+    if n_single is not None:
+        single = list(rng.choice(single, n_single, replace=False))
+    pick = list(single) + list(rng.choice(cx, n_cx, replace=False))
+    D = circuit_dem("ZSZ-LP-60", 0.001, 2, basis)
+    Hd, Od = D.dense_H(), D.dense_O()
+    cols = {(tuple(np.nonzero(Hd[:, j])[0]), tuple(np.nonzero(Od[:, j])[0])) for j in range(D.n_loc)}
+    for f in pick:
+        d, o = run_memory_circuit(circ, info, int(f), int(f))
+        assert np.array_equal(d, FD[f]) and np.array_equal(o, FO[f]), f
+        if d.any() or o.any():
+            assert (tuple(np.nonzero(d)[0]), tuple(np.nonzero(o)[0])) in cols, f
