@@ -55,6 +55,8 @@ def _load():
                                                ctypes.c_int32])
         _lib.oracle_relaybp_decode.restype = ctypes.c_int
         _lib.oracle_max_threads.restype = ctypes.c_int
+        _lib.oracle_min_weight.argtypes = [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32]
+        _lib.oracle_min_weight.restype = ctypes.c_int
         _lib.oracle_learned_loss.argtypes = ([ctypes.c_int32] * 2 + [P] * 3 + [ctypes.c_int32, P, ctypes.c_int32, P,
                                              ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64, P, P,
                                              ctypes.c_int32])
@@ -79,6 +81,21 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib.oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def min_weight(G: np.ndarray, n_threads: int = 0) -> int:
+    """Minimum nonzero codeword weight of the row space of a binary k x n
+    matrix G (k <= 63, n <= 64) by Gray-code enumeration of all codewords
+    (test infrastructure for the Table 2 distance pin)."""
+    G = np.asarray(G, dtype=np.uint8)
+    k, n = G.shape
+    rows = np.zeros(k, dtype=np.uint64)
+    for c in range(n):
+        rows |= G[:, c].astype(np.uint64) << np.uint64(c)
+    d = _load().oracle_min_weight(k, n, rows.ctypes.data_as(ctypes.c_void_p), n_threads)
+    if d < 0:
+        raise ValueError("min_weight needs 1 <= k <= 63 and 1 <= n <= 64")
+    return d
 
 
 def max_threads() -> int:

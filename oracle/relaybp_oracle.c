@@ -541,3 +541,40 @@ int oracle_learned_loss(int32_t n_det, int32_t n_loc, const int32_t *H_indptr, c
 
 
 static double knot_gamma_l(const double *knots, int32_t K, double u) { return knot_gamma(knots, K, u); }
+
+
+/* Minimum weight of a nonzero codeword of the binary code spanned by k <= 63
+ * generator rows of length n <= 64 (row r: bit c of gens[r] = entry c), by
+ * Gray-code enumeration of all 2^k - 1 nonzero codewords: consecutive Gray
+ * codes differ in one generator, so each step is one XOR and one popcount.
+ * Test infrastructure for the code-builder pin of Table 2 (ZSZ-2BGA-64 is a
+ * [64, 32, 10] code); the top bits of the message are split over threads.
+ * Returns the distance, or -1 on bad sizes. */
+int oracle_min_weight(int32_t k, int32_t n, const uint64_t *gens, int32_t n_threads)
+{
+    if (k < 1 || k > 63 || n < 1 || n > 64) return -1;
+    const int top = k > 8 ? 8 : k - 1;             /* message bits fixed per task */
+    const int low = k - top;
+    const int64_t tasks = (int64_t)1 << top;
+    int best = n + 1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : best)
+    for (int64_t task = 0; task < tasks; ++task) {
+        uint64_t w = 0;                            /* codeword of message (task << low) */
+        for (int b = 0; b < top; ++b)
+            if ((task >> b) & 1) w ^= gens[low + b];
+        int mine = n + 1;
+        if (w) mine = __builtin_popcountll(w);
+        for (uint64_t g = 1; g < ((uint64_t)1 << low); ++g) {
+            w ^= gens[__builtin_ctzll(g)];         /* Gray code g ^ (g >> 1) steps by one bit */
+            int c = __builtin_popcountll(w);
+            if (c < mine && w) mine = c;
+        }
+        if (mine < best) best = mine;
+    }
+    return best;
+}

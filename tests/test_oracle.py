@@ -388,3 +388,39 @@ def test_learned_legs_cutoff():
     early = full["stats"][:, 2] <= 2
     assert early.any()
     assert np.array_equal(full["corrections"][early], cut2["corrections"][early])
+
+
+def test_mw_brute_force_weight_le4_60():
+    """[[60,12,6]] code capacity (H_X, equal priors), errors of weight 3 and 4:
+    the minimum weight of every syndrome of a weight <= 4 error, by enumerating
+    all 523,686 patterns of weight <= 4; every converged Relay-BP answer
+    satisfies H e^ = s and has Hamming weight >= that minimum, and nearly all
+    reach it (measured on 2,000 shots: 99.8% at weight 3, 99.5% at weight 4)."""
+    D = code_capacity_dem("ZSZ-LP-60", 0.01)
+    Hd = D.dense_H().astype(np.int64)
+    C, V = Hd.shape
+    assert C <= 24
+    col = (Hd * (1 << np.arange(C))[:, None]).sum(0)           # column j as a C-bit integer
+    mw = np.full(1 << C, 127, dtype=np.int8)
+    mw[0] = 0
+    for w in range(1, 5):
+        idx = np.array(list(itertools.combinations(range(V), w)), dtype=np.int64)
+        syn = np.bitwise_xor.reduce(col[idx], axis=1)
+        fresh = mw[syn] > w
+        mw[syn[fresh]] = w
+    rng = np.random.default_rng(11)
+    E = np.zeros((240, V), dtype=np.uint8)
+    for t in range(E.shape[0]):
+        E[t, rng.choice(V, 3 + t % 2, replace=False)] = 1
+    S = (E.astype(np.int64) @ Hd.T) % 2
+    r = oracle.decode(D, DecodeParams(num_sets=50, gamma_min=-0.24, gamma_max=0.66, seed=9), pack_bits(S))
+    eh = unpack_bits(r["corrections"], V).astype(np.int64)
+    conv = r["stats"][:, 0] == 1
+    assert conv.mean() > 0.9
+    assert np.array_equal((eh[conv] @ Hd.T) % 2, S[conv])
+    sid = (S * (1 << np.arange(C))).sum(1)
+    best = mw[sid].astype(np.int64)
+    assert np.all(best <= E.sum(1))
+    got = eh.sum(1)
+    assert np.all(got[conv] >= best[conv])
+    assert (got[conv] == best[conv]).mean() > 0.95

@@ -260,3 +260,33 @@ def test_dem_faults_match_tableau_simulation(basis, n_single, n_cx):
         assert np.array_equal(d, FD[f]) and np.array_equal(o, FO[f]), f
         if d.any() or o.any():
             assert (tuple(np.nonzero(d)[0]), tuple(np.nonzero(o)[0])) in cols, f
+
+
+def test_min_weight_enumerator_small_codes():
+    """The Gray-code enumerator against direct enumeration of every message on
+    small random codes, and the [7,4,3] Hamming code."""
+    import itertools
+    import oracle
+    ham = np.array([[1, 0, 0, 0, 0, 1, 1], [0, 1, 0, 0, 1, 0, 1], [0, 0, 1, 0, 1, 1, 0], [0, 0, 0, 1, 1, 1, 1]])
+    assert oracle.min_weight(ham) == 3
+    rng = np.random.default_rng(3)
+    for k, n in ((5, 12), (9, 20), (10, 64)):
+        G = rng.integers(0, 2, (k, n))
+        best = min(int(((np.array(m) @ G) % 2).sum()) for m in itertools.product((0, 1), repeat=k) if any(m)
+                   if ((np.array(m) @ G) % 2).any())
+        assert oracle.min_weight(G) == best
+
+
+@pytest.mark.parametrize("row", _table("zsz_2bga_distances.txt"), ids=lambda r: r[0])
+def test_classical_seed_distance_brute_force(row):
+    """Table 2: the seed codes H_left and H_right of ZSZ-LP-160 are [64, 32, 10],
+    checked by enumerating all 2^32 codewords of each."""
+    import oracle
+    from workloads.zsz import gf2_nullspace
+    name, n, k, dl, dr = row[0], *map(int, row[1:])
+    code = load_code(name)
+    for H, d in ((code.H_left, dl), (code.H_right, dr)):
+        G = gf2_nullspace(H)
+        assert H.shape[1] == n and G.shape[0] == k
+        assert not ((G.astype(np.int64) @ H.T.astype(np.int64)) % 2).any()
+        assert oracle.min_weight(G) == d
