@@ -123,7 +123,7 @@ int relaybp_set_params(relaybp_handle *h, const relaybp_params *params);
  * (same meaning as in relaybp_learned_forward; u from stream 1 of the leg).
  * Either may be NULL (NULL and NULL restore the plain method).  Device
  * pointers stay owned by the caller and must outlive the decodes that use
- * them.  Needs msg_dtype F32, F16 or BF16 and carry_messages = 0. */
+ * them.  Needs msg_dtype F32, F16, BF16 or I8 and carry_messages = 0. */
 int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const float *d_knots, int32_t K);
 
 /* Same with weights tied per check row: d_wrow [T][C], the weight of every

@@ -802,7 +802,7 @@ int relaybp_set_learned(relaybp_handle *h, const float *d_w, int32_t T, const fl
     if ((d_w && T < 1) || (d_knots && (K < 1 || K > 64)))
         return fail(RELAYBP_ERR_INVALID, "need T >= 1 with weights and 1 <= K <= 64 with knots");
     if ((d_w || d_knots) && h->params.msg_dtype == RELAYBP_MSG_F64)
-        return fail(RELAYBP_ERR_UNSUPPORTED, "learned decoding runs with FP32 arithmetic (msg_dtype F32/F16/BF16)");
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned decoding runs with FP32 arithmetic (msg_dtype F32/F16/BF16/I8)");
     if (d_w && h->params.carry_messages)
         return fail(RELAYBP_ERR_UNSUPPORTED, "learned weights with carry_messages are not supported");
     h->lw = d_w;
@@ -820,7 +820,7 @@ int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, 
     if ((d_wrow && T < 1) || (d_knots && (K < 1 || K > 64)))
         return fail(RELAYBP_ERR_INVALID, "need T >= 1 with weights and 1 <= K <= 64 with knots");
     if ((d_wrow || d_knots) && h->params.msg_dtype == RELAYBP_MSG_F64)
-        return fail(RELAYBP_ERR_UNSUPPORTED, "learned decoding runs with FP32 arithmetic (msg_dtype F32/F16/BF16)");
+        return fail(RELAYBP_ERR_UNSUPPORTED, "learned decoding runs with FP32 arithmetic (msg_dtype F32/F16/BF16/I8)");
     if (d_wrow && h->params.carry_messages)
         return fail(RELAYBP_ERR_UNSUPPORTED, "learned weights with carry_messages are not supported");
     h->lw = nullptr;
