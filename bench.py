@@ -47,10 +47,13 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--streams", type=int, default=3, help="zsz160: streams (handle sets) the steps rotate over")
-    ap.add_argument("--workload", default="zsz160", choices=["zsz160", "mixed", "learned", "stream550"],
+    ap.add_argument("--workload", default="zsz160",
+                    choices=["zsz160", "mixed", "learned", "stream550", "gamma_sweep"],
                     help="zsz160: the headline workload; mixed: nine DEMs in one persistent launch; "
                          "learned: train, then learned vs plain Relay-BP at equal LER; stream550: ZSZ-LP-550 "
-                         "d=18 in CUDA-graph batches with int8 storage and per-shot latency")
+                         "d=18 in CUDA-graph batches with int8 storage and per-shot latency; gamma_sweep: "
+                         "Table 9's gamma-interval grid search and the XZ-averaged LER-vs-p curve")
+    ap.add_argument("--sweep-shots", type=int, default=200_000, help="gamma_sweep: shots per point and basis")
     ap.add_argument("--stream-batch", type=int, default=1 << 16, help="stream550: shots per graph batch")
     ap.add_argument("--train-steps", type=int, default=300, help="learned: Adam steps of 512 shots at p=0.2%%")
     ap.add_argument("--learned-msg", default="bf16", choices=["bf16", "f16", "f32"], help="learned: message storage")
@@ -782,6 +785,47 @@ def run_stream550(a):
         R.relaybp_destroy(x)
 
 
+def run_gamma_sweep(a):
+    """ZSZ-LP-160: the gamma-interval grid search of Table 9 at p_sweep = 0.2%
+    (X- and Z-memory, fewest pooled failures), then the XZ-averaged LER per
+    qubit-round at p = 0.1/0.2/0.3% with the chosen interval and with Table
+    9's, 95% Clopper-Pearson bounds."""
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from paper_2607_27644_b300.sweep import GpuDecoder, gamma_grid_search, ler_curve
+    from workloads.dem import circuit_dems
+    from workloads.zsz import load_code
+
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    code, rounds = WORKLOAD["code"], WORKLOAD["rounds"]
+    k = load_code(code).k
+    ps = [0.001, 0.002, 0.003]
+    zs, xs = circuit_dems(code, ps, rounds, "Z"), circuit_dems(code, ps, rounds, "X")
+    dems = {p: {"Z": z, "X": x} for p, z, x in zip(ps, zs, xs)}
+    dec = GpuDecoder(batch=1 << 16, sample_seed=SAMPLE_SEED)
+    base = R.Params(msg_dtype=a.msg or "f32", **DECODER)
+    t0 = time.perf_counter()
+    best, grid = gamma_grid_search(dec, dems[0.002], base, [-0.24, -0.15, -0.05], [0.5, 0.61, 0.7],
+                                   a.sweep_shots, 0.002, rounds, k)
+    t_grid = time.perf_counter() - t0
+    chosen = R.Params(**dict(vars(base), gamma_min=best.gamma[0], gamma_max=best.gamma[1]))
+    curve = ler_curve(dec, dems, chosen, a.sweep_shots, rounds, k, shot0=10**9)
+    table9 = ler_curve(dec, dems, base, a.sweep_shots, rounds, k, shot0=10**9)
+    dt = time.perf_counter() - t0
+    shots = 2 * a.sweep_shots * (len(grid) + 2 * len(ps))
+    line = {"metric": "gamma-interval grid search and XZ-averaged LER per qubit-round, ZSZ-LP-160",
+            "value": shots / dt, "unit": "shots/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": base.msg_dtype,
+            "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEMs (X and Z memory)",
+            "config": {"workload": f"{code}, d={rounds}, grid at p_sweep=0.002, curve at p in {ps}",
+                       "shots_per_point_and_basis": a.sweep_shots, "grid_seconds": t_grid},
+            "chosen_gamma": list(best.gamma), "table9_gamma": [DECODER["gamma_min"], DECODER["gamma_max"]],
+            "grid": [q.as_dict() for q in grid], "curve_chosen": [q.as_dict() for q in curve],
+            "curve_table9": [q.as_dict() for q in table9]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -792,6 +836,8 @@ def main():
         run_learned(a)
     elif a.workload == "stream550":
         run_stream550(a)
+    elif a.workload == "gamma_sweep":
+        run_gamma_sweep(a)
     else:
         run_ours(a)
 
