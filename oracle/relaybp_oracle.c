@@ -371,7 +371,7 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
         free(fill);
     }
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
+    omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());   /* <= 0: every core */
 #else
     (void)n_threads;
 #endif
@@ -409,7 +409,7 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP
-    return omp_get_max_threads();
+    return omp_get_num_procs();             /* what a call with n_threads <= 0 uses */
 #else
     return 1;
 #endif
@@ -477,7 +477,7 @@ int oracle_learned_loss(int32_t n_det, int32_t n_loc, const int32_t *H_indptr, c
         free(fill);
     }
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
+    omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());   /* <= 0: every core */
 #else
     (void)n_threads;
 #endif
@@ -558,7 +558,7 @@ int oracle_min_weight(int32_t k, int32_t n, const uint64_t *gens, int32_t n_thre
     const int64_t tasks = (int64_t)1 << top;
     int best = n + 1;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
+    omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());   /* <= 0: every core */
 #else
     (void)n_threads;
 #endif
