@@ -775,6 +775,7 @@ def run_stream550(a):
                     "per_qubit_round": per_qubit_round(blk, rounds, kq),
                     "per_qubit_round_95": [per_qubit_round(lo, rounds, kq), per_qubit_round(hi, rounds, kq)]},
             "latency_ms": {"service_p50": pct(service, 50), "service_p99": pct(service, 99),
+                           "service_p99.9": pct(service, 99.9),
                            "service_max": float(service.max()), "service_mean": float(service.mean()),
                            "in_batch_p50": pct(sojourn, 50), "in_batch_p99": pct(sojourn, 99),
                            "definition": "service = retire - start of the shot's thread block (device %globaltimer); "
