@@ -20,15 +20,17 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "relaybp_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "awgn_oracle.c")]
 _LIB = os.path.join(_HERE, "librelaybp_oracle.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP over shots)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp,
+                               *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -57,6 +59,12 @@ def _load():
         _lib.oracle_max_threads.restype = ctypes.c_int
         _lib.oracle_min_weight.argtypes = [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32]
         _lib.oracle_min_weight.restype = ctypes.c_int
+        _lib.oracle_awgn_llr.argtypes = [ctypes.c_int32, P, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.c_uint64, ctypes.c_int64, P]
+        _lib.oracle_awgn_llr.restype = ctypes.c_int
+        _lib.oracle_sum_product.argtypes = ([ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_int32, P, P, P, P, ctypes.c_int32])
+        _lib.oracle_sum_product.restype = ctypes.c_int
         _lib.oracle_learned_loss.argtypes = ([ctypes.c_int32] * 2 + [P] * 3 + [ctypes.c_int32, P, ctypes.c_int32, P,
                                              ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64, P, P,
                                              ctypes.c_int32])
@@ -96,6 +104,45 @@ def min_weight(G: np.ndarray, n_threads: int = 0) -> int:
     if d < 0:
         raise ValueError("min_weight needs 1 <= k <= 63 and 1 <= n <= 64")
     return d
+
+
+def awgn_sigma(ebn0_db: float, rate: float) -> float:
+    """Noise deviation of BPSK over AWGN at E_b/N_0 (dB) for code rate R:
+    E_b/N_0 = 1 / (2 R sigma^2) for unit-energy symbols (Sec. 6.2)."""
+    return float(np.sqrt(1.0 / (2.0 * rate * 10.0 ** (ebn0_db / 10.0))))
+
+
+def awgn_llr(n: int, sigma: float, seed: int, shot0: int, shots: int, codewords=None,
+             llr_max: float = 20.0) -> np.ndarray:
+    """Channel LLRs [shots, n] of BPSK transmissions over AWGN (all-zero
+    codeword unless packed `codewords` [shots, ceil(n/32)] are given)."""
+    out = np.zeros((shots, n), dtype=np.float64)
+    cw = None if codewords is None else np.ascontiguousarray(codewords, dtype=np.uint32)
+    rc = _load().oracle_awgn_llr(n, None if cw is None else cw.ctypes.data_as(ctypes.c_void_p), sigma, llr_max,
+                                 seed, shot0, shots, out.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError("oracle_awgn_llr rejected its arguments")
+    return out
+
+
+def sum_product(indptr, indices, m: int, n: int, llr: np.ndarray, max_iter: int = 100, llr_max: float = 20.0,
+                early_stop: bool = True, posteriors: bool = False, n_threads: int = 0) -> dict:
+    """Flooding sum-product BP (boxplus-phi check update) of LLR vectors
+    llr [shots, n] for the m x n check matrix in CSR form (Sec. 6.2)."""
+    llr = np.ascontiguousarray(llr, dtype=np.float64)
+    shots = llr.shape[0]
+    ip = np.ascontiguousarray(indptr, dtype=np.int32)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    bits = np.zeros((shots, (n + 31) // 32), dtype=np.uint32)
+    iters = np.zeros(shots, dtype=np.int32)
+    valid = np.zeros(shots, dtype=np.int32)
+    post = np.zeros((shots, n), dtype=np.float64) if posteriors else None
+    vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    rc = _load().oracle_sum_product(m, n, vp(ip), vp(ix), vp(llr), shots, max_iter, llr_max, int(early_stop), vp(bits),
+                                    vp(iters), vp(valid), vp(post), n_threads)
+    if rc != 0:
+        raise ValueError("oracle_sum_product rejected its arguments")
+    return dict(bits=bits, iters=iters, valid=valid.astype(bool), posteriors=post)
 
 
 def max_threads() -> int:
