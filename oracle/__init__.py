@@ -65,6 +65,8 @@ def _load():
         _lib.oracle_sum_product.argtypes = ([ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int64, ctypes.c_int32,
                                              ctypes.c_double, ctypes.c_int32, P, P, P, P, ctypes.c_int32])
         _lib.oracle_sum_product.restype = ctypes.c_int
+        _lib.oracle_osd0.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.c_int64, P, P, ctypes.c_int32]
+        _lib.oracle_osd0.restype = ctypes.c_int
         _lib.oracle_learned_loss.argtypes = ([ctypes.c_int32] * 2 + [P] * 3 + [ctypes.c_int32, P, ctypes.c_int32, P,
                                              ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64, P, P,
                                              ctypes.c_int32])
@@ -143,6 +145,24 @@ def sum_product(indptr, indices, m: int, n: int, llr: np.ndarray, max_iter: int 
     if rc != 0:
         raise ValueError("oracle_sum_product rejected its arguments")
     return dict(bits=bits, iters=iters, valid=valid.astype(bool), posteriors=post)
+
+
+def osd0(indptr, indices, m: int, n: int, syndromes: np.ndarray, soft: np.ndarray, n_threads: int = 0) -> dict:
+    """OSD-0: for each shot the solution of H e = s supported on the first
+    rank(H) independent columns in ascending order of `soft` (posterior LLRs:
+    the most likely errors first).  syndromes [shots, ceil(m/32)] packed."""
+    soft = np.ascontiguousarray(soft, dtype=np.float64)
+    shots = soft.shape[0]
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint32)
+    ip = np.ascontiguousarray(indptr, dtype=np.int32)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    e = np.zeros((shots, (n + 31) // 32), dtype=np.uint32)
+    valid = np.zeros(shots, dtype=np.int32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = _load().oracle_osd0(m, n, vp(ip), vp(ix), vp(syn), vp(soft), shots, vp(e), vp(valid), n_threads)
+    if rc != 0:
+        raise ValueError("oracle_osd0 rejected its arguments")
+    return dict(corrections=e, valid=valid.astype(bool))
 
 
 def max_threads() -> int:

@@ -1,7 +1,8 @@
 /*
  * awgn_oracle.c -- plain FP64 CPU oracle for the classical channel-coding
  * workload: BPSK over the additive white Gaussian noise channel, decoded by
- * flooding sum-product belief propagation.
+ * flooding sum-product belief propagation; and OSD-0 post-processing of
+ * decoder outputs (at the end of the file).
  *
  * TEST INFRASTRUCTURE ONLY, like relaybp_oracle.c (compiled into the same
  * library, sharing its Philox4x32-10): nothing on the product path may link,
@@ -163,5 +164,81 @@ int oracle_sum_product(int32_t m, int32_t n, const int32_t *indptr, const int32_
         free(nu); free(mu); free(post); free(hard);
     }
     free(cptr); free(cedge);
+    return 0;
+}
+
+
+/* ------------------------------------------------------------------------- */
+/* OSD-0 post-processing (the outlook of Sec. 7, improved decoding, names  */
+/* ordered-statistics decoding for the flagged nonconvergences)            */
+/* ------------------------------------------------------------------------- */
+/* For each shot: order the n columns by the soft value `soft` ascending (the
+ * most negative posterior LLR, i.e. the most likely error, first; ties by
+ * index), take the first columns that are linearly independent over GF(2)
+ * (the information set, rank(H) of them) and return the unique e supported
+ * on them with H e = s; out_valid[s] = 0 when s is not in the column space of
+ * H (e is then the solution of the consistent rows only).  Plain dense GF(2)
+ * elimination, one byte per entry.  Returns 0, or -1 on bad sizes. */
+int oracle_osd0(int32_t m, int32_t n, const int32_t *indptr, const int32_t *indices, const uint32_t *syndromes,
+                const double *soft, int64_t shots, uint32_t *out_e, int32_t *out_valid, int32_t n_threads)
+{
+    if (m < 1 || n < 1 || shots < 0) return -1;
+    const int64_t wm = (m + 31) / 32, wn = (n + 31) / 32;
+#ifdef _OPENMP
+    omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());
+#else
+    (void)n_threads;
+#endif
+#pragma omp parallel
+    {
+        unsigned char *A = malloc((size_t)m * (size_t)(n + 1));     /* [H_perm | s], row-major */
+        int32_t *order = malloc(sizeof(int32_t) * (size_t)n);
+        int32_t *pivcol = malloc(sizeof(int32_t) * (size_t)m);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t s = 0; s < shots; ++s) {
+            const double *q = soft + s * n;
+            for (int32_t j = 0; j < n; ++j) order[j] = j;
+            /* insertion sort by (q, index): plain and stable */
+            for (int32_t a = 1; a < n; ++a) {
+                const int32_t v = order[a];
+                int32_t b = a - 1;
+                while (b >= 0 && (q[order[b]] > q[v])) { order[b + 1] = order[b]; --b; }
+                order[b + 1] = v;
+            }
+            memset(A, 0, (size_t)m * (size_t)(n + 1));
+            for (int32_t i = 0; i < m; ++i) {
+                for (int32_t e = indptr[i]; e < indptr[i + 1]; ++e) A[(size_t)i * (n + 1) + indices[e]] = 1;
+                A[(size_t)i * (n + 1) + n] = (unsigned char)((syndromes[s * wm + i / 32] >> (i % 32)) & 1u);
+            }
+            /* forward elimination over the columns in the chosen order */
+            int32_t r = 0;
+            for (int32_t t = 0; t < n && r < m; ++t) {
+                const int32_t c = order[t];
+                int32_t p = -1;
+                for (int32_t i = r; i < m; ++i)
+                    if (A[(size_t)i * (n + 1) + c]) { p = i; break; }
+                if (p < 0) continue;
+                if (p != r)
+                    for (int32_t k = 0; k <= n; ++k) {
+                        unsigned char tmp = A[(size_t)p * (n + 1) + k];
+                        A[(size_t)p * (n + 1) + k] = A[(size_t)r * (n + 1) + k];
+                        A[(size_t)r * (n + 1) + k] = tmp;
+                    }
+                for (int32_t i = 0; i < m; ++i)
+                    if (i != r && A[(size_t)i * (n + 1) + c])
+                        for (int32_t k = 0; k <= n; ++k) A[(size_t)i * (n + 1) + k] ^= A[(size_t)r * (n + 1) + k];
+                pivcol[r++] = c;
+            }
+            int valid = 1;
+            for (int32_t i = r; i < m; ++i)
+                if (A[(size_t)i * (n + 1) + n]) valid = 0;          /* 0 = 1 row: s outside the column space */
+            uint32_t *e = out_e + s * wn;
+            memset(e, 0, sizeof(uint32_t) * (size_t)wn);
+            for (int32_t i = 0; i < r; ++i)                          /* reduced form: e_pivot = rhs */
+                if (A[(size_t)i * (n + 1) + n]) e[pivcol[i] / 32] |= 1u << (pivcol[i] % 32);
+            out_valid[s] = valid;
+        }
+        free(A); free(order); free(pivcol);
+    }
     return 0;
 }

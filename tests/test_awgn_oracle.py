@@ -1,5 +1,6 @@
 """Pins of the classical channel-coding oracle (BPSK over AWGN, sum-product
-BP; arXiv 2607.27644 Sec. 6.2) to what the mathematics fixes."""
+BP; arXiv 2607.27644 Sec. 6.2) and of the OSD-0 post-processing oracle
+(Sec. 7, improved decoding) to what the mathematics fixes."""
 import itertools
 
 import numpy as np
@@ -140,3 +141,67 @@ def test_zsz_2bga_64_decoding_regimes():
             assert ok.all() and r["iters"].max() <= 10
         else:
             assert 0 < (~ok).sum() < 300
+
+
+def _info_set(H, order):
+    """First rank(H) columns of `order` that are independent over GF(2)
+    (greedy, by rank of the growing prefix)."""
+    from workloads.zsz import gf2_rank
+    chosen = []
+    for c in order:
+        if gf2_rank(H[:, chosen + [c]]) > len(chosen):
+            chosen.append(c)
+    return chosen
+
+
+def test_osd0_solution_lives_on_the_information_set():
+    """[[60,12,6]] code capacity (H_X): for random errors and random soft
+    values, OSD-0 returns a solution of H e = s supported on the information
+    set (computed here independently by growing ranks) -- unique there."""
+    from workloads.dem import code_capacity_dem
+    D = code_capacity_dem("ZSZ-LP-60", 0.05)
+    H = D.dense_H().astype(np.uint8)
+    m, n = H.shape
+    rng = np.random.default_rng(4)
+    E = (rng.random((20, n)) < 0.06).astype(np.uint8)
+    S = (E.astype(np.int64) @ H.T) % 2
+    soft = rng.normal(0.0, 3.0, (20, n))
+    r = oracle.osd0(D.H_indptr, D.H_indices, m, n, oracle.pack_bits(S), soft)
+    e = oracle.unpack_bits(r["corrections"], n).astype(np.int64)
+    assert r["valid"].all()
+    assert np.array_equal((e @ H.T) % 2, S)
+    for s in range(20):
+        order = sorted(range(n), key=lambda j: (soft[s, j], j))
+        info = set(_info_set(H, order))
+        assert set(np.nonzero(e[s])[0]) <= info
+
+
+def test_osd0_recovers_errors_ranked_first():
+    """When the soft values rank the true error's support first and that
+    support is independent (weight < the code distance 6), OSD-0 returns the
+    error itself."""
+    from workloads.dem import code_capacity_dem
+    D = code_capacity_dem("ZSZ-LP-60", 0.05)
+    H = D.dense_H().astype(np.uint8)
+    m, n = H.shape
+    rng = np.random.default_rng(5)
+    E = np.zeros((30, n), dtype=np.uint8)
+    for t in range(30):
+        E[t, rng.choice(n, 1 + t % 5, replace=False)] = 1
+    S = (E.astype(np.int64) @ H.T) % 2
+    soft = np.where(E == 1, -8.0, 4.0) + rng.uniform(-1, 1, E.shape)
+    r = oracle.osd0(D.H_indptr, D.H_indices, m, n, oracle.pack_bits(S), soft)
+    assert np.array_equal(oracle.unpack_bits(r["corrections"], n), E)
+
+
+def test_osd0_flags_syndromes_outside_the_column_space():
+    """A rank-deficient check matrix (a repeated row): syndromes that break
+    the row dependency are flagged invalid, the others solved."""
+    H = np.array([[1, 1, 0, 1], [0, 1, 1, 1], [1, 1, 0, 1]], dtype=np.uint8)
+    ip, ix = _csr(H)
+    S = np.array([[1, 0, 1], [1, 0, 0], [0, 1, 0]])
+    r = oracle.osd0(ip, ix, 3, 4, oracle.pack_bits(S), np.zeros((3, 4)))
+    assert list(r["valid"]) == [True, False, True]
+    e = oracle.unpack_bits(r["corrections"], 4).astype(np.int64)
+    for s in (0, 2):
+        assert np.array_equal((e[s] @ H.T) % 2, S[s])
