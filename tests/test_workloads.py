@@ -290,3 +290,58 @@ def test_classical_seed_distance_brute_force(row):
         assert H.shape[1] == n and G.shape[0] == k
         assert not ((G.astype(np.int64) @ H.T.astype(np.int64)) % 2).any()
         assert oracle.min_weight(G) == d
+
+
+def _ogs_rows():
+    rows = []
+    for r in _table("ogs_generators.txt"):
+        terms = [(int(a), int(g.split(":")[0])) for g in r[3:] for a in g.split(":")[1].split(",")]
+        rows.append((r[0], r[1], int(r[2]), terms))
+    return rows
+
+
+@pytest.mark.parametrize("row", _ogs_rows(), ids=lambda r: f"{r[0]}-{r[1]}")
+def test_ogs_generators(row):
+    """Table 8: with u = 1 the generator validity conditions u_L a~ + v_L b~ = 0
+    and c~ u_R + d~ v_R = 0 become v_L b~ = a~ and d~ v_R = c~; the printed
+    systematic polynomials satisfy them, have the printed weights, and are the
+    unique solutions (b and d are units: L[b], L[d] have full rank)."""
+    name, side, weight, terms = row
+    code = load_code(name)
+    G = code.G
+
+    def alg(ts):
+        v = np.zeros(G.order, dtype=np.uint8)
+        for (a, b) in ts:
+            v[G.elem(a, b)] ^= 1
+        return v
+
+    def mul(u, v):
+        out = np.zeros(G.order, dtype=np.uint8)
+        for g in np.nonzero(u)[0]:
+            for h in np.nonzero(v)[0]:
+                out[G.mul[g, h]] ^= 1
+        return out
+
+    def bar(u):
+        out = np.zeros_like(u)
+        out[G.inv[np.nonzero(u)[0]]] = 1
+        return out
+
+    def left_matrix(u):                     # column h = u * h
+        M = np.zeros((G.order, G.order), dtype=np.uint8)
+        for h in range(G.order):
+            for g in np.nonzero(u)[0]:
+                M[G.mul[g, h], h] ^= 1
+        return M
+
+    v = alg(terms)
+    assert len(terms) == weight and v.sum() == weight
+    if side == "L":
+        a, b = alg(code.a_terms), alg(code.b_terms)
+        assert np.array_equal(mul(v, bar(b)), bar(a))
+        assert gf2_rank(left_matrix(b)) == G.order
+    else:
+        c, d = alg(code.c_terms), alg(code.d_terms)
+        assert np.array_equal(mul(bar(d), v), bar(c))
+        assert gf2_rank(left_matrix(d)) == G.order
