@@ -65,8 +65,12 @@ def _load():
         _lib.oracle_sum_product.argtypes = ([ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int64, ctypes.c_int32,
                                              ctypes.c_double, ctypes.c_int32, P, P, P, P, ctypes.c_int32])
         _lib.oracle_sum_product.restype = ctypes.c_int
-        _lib.oracle_osd0.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.c_int64, P, P, ctypes.c_int32]
-        _lib.oracle_osd0.restype = ctypes.c_int
+        _lib.oracle_osd.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32, ctypes.c_int64, P, P,
+                                    ctypes.c_int32]
+        _lib.oracle_osd.restype = ctypes.c_int
+        _lib.oracle_relaybp_decode_post.argtypes = ([ctypes.c_int32] * 3 + [P] * 5 + [ctypes.POINTER(OracleParams), P,
+                                                     ctypes.c_uint64, ctypes.c_int64, P, P, P, P, P, ctypes.c_int32])
+        _lib.oracle_relaybp_decode_post.restype = ctypes.c_int
         _lib.oracle_learned_loss.argtypes = ([ctypes.c_int32] * 2 + [P] * 3 + [ctypes.c_int32, P, ctypes.c_int32, P,
                                              ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64, P, P,
                                              ctypes.c_int32])
@@ -147,22 +151,32 @@ def sum_product(indptr, indices, m: int, n: int, llr: np.ndarray, max_iter: int 
     return dict(bits=bits, iters=iters, valid=valid.astype(bool), posteriors=post)
 
 
-def osd0(indptr, indices, m: int, n: int, syndromes: np.ndarray, soft: np.ndarray, n_threads: int = 0) -> dict:
-    """OSD-0: for each shot the solution of H e = s supported on the first
-    rank(H) independent columns in ascending order of `soft` (posterior LLRs:
-    the most likely errors first).  syndromes [shots, ceil(m/32)] packed."""
+def osd(indptr, indices, m: int, n: int, syndromes: np.ndarray, soft: np.ndarray, order: int = 0,
+        weights: np.ndarray | None = None, n_threads: int = 0) -> dict:
+    """Ordered-statistics decoding: the solution of H e = s on the first rank(H)
+    independent columns in ascending order of `soft` (posterior LLRs: the most
+    likely errors first), OSD-0; with order > 0 also every flip of one or two
+    of the first `order` columns outside that set, keeping the least sum of
+    `weights` (prior LLRs).  syndromes [shots, ceil(m/32)] packed."""
     soft = np.ascontiguousarray(soft, dtype=np.float64)
     shots = soft.shape[0]
     syn = np.ascontiguousarray(syndromes, dtype=np.uint32)
     ip = np.ascontiguousarray(indptr, dtype=np.int32)
     ix = np.ascontiguousarray(indices, dtype=np.int32)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     e = np.zeros((shots, (n + 31) // 32), dtype=np.uint32)
     valid = np.zeros(shots, dtype=np.int32)
-    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    rc = _load().oracle_osd0(m, n, vp(ip), vp(ix), vp(syn), vp(soft), shots, vp(e), vp(valid), n_threads)
+    vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    rc = _load().oracle_osd(m, n, vp(ip), vp(ix), vp(syn), vp(soft), vp(w), order, shots, vp(e), vp(valid),
+                            n_threads)
     if rc != 0:
-        raise ValueError("oracle_osd0 rejected its arguments")
+        raise ValueError("oracle_osd rejected its arguments")
     return dict(corrections=e, valid=valid.astype(bool))
+
+
+def osd0(indptr, indices, m: int, n: int, syndromes: np.ndarray, soft: np.ndarray, n_threads: int = 0) -> dict:
+    """OSD-0 (order 0 of `osd`)."""
+    return osd(indptr, indices, m, n, syndromes, soft, 0, None, n_threads)
 
 
 def max_threads() -> int:
@@ -243,6 +257,28 @@ def decode(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0, tra
     if rc != 0:
         raise ValueError("oracle_relaybp_decode rejected its input")
     return dict(corrections=corr, pred_obs=pobs, stats=stats, weights=wts, trace=trace)
+
+
+def decode_with_posteriors(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0,
+                           n_threads: int = 0) -> dict:
+    """decode() plus each shot's marginals M after its last iteration
+    (key "posteriors", [shots, n_loc]): the soft input of OSD post-processing."""
+    lib = _load()
+    Hp, Hi, Op, Oi, pr = _dem_arrays(dem)
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint32)
+    shots = syn.shape[0]
+    corr = np.zeros((shots, (dem.n_loc + 31) // 32), dtype=np.uint32)
+    pobs = np.zeros((shots, max(1, (dem.n_obs + 31) // 32)), dtype=np.uint32)
+    stats = np.zeros((shots, 4), dtype=np.int32)
+    wts = np.zeros(shots, dtype=np.float64)
+    post = np.zeros((shots, dem.n_loc), dtype=np.float64)
+    cp = params.c()
+    rc = lib.oracle_relaybp_decode_post(dem.n_det, dem.n_loc, dem.n_obs, _ptr(Hp), _ptr(Hi), _ptr(Op), _ptr(Oi),
+                                        _ptr(pr), ctypes.byref(cp), _ptr(syn), shot0, shots, _ptr(corr), _ptr(pobs),
+                                        _ptr(stats), _ptr(wts), _ptr(post), n_threads)
+    if rc != 0:
+        raise ValueError("oracle_relaybp_decode_post rejected its input")
+    return dict(corrections=corr, pred_obs=pobs, stats=stats, weights=wts, posteriors=post)
 
 
 def unpack_bits(words: np.ndarray, nbits: int) -> np.ndarray:

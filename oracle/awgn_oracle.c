@@ -175,14 +175,19 @@ int oracle_sum_product(int32_t m, int32_t n, const int32_t *indptr, const int32_
 /* For each shot: order the n columns by the soft value `soft` ascending (the
  * most negative posterior LLR, i.e. the most likely error, first; ties by
  * index), take the first columns that are linearly independent over GF(2)
- * (the information set, rank(H) of them) and return the unique e supported
- * on them with H e = s; out_valid[s] = 0 when s is not in the column space of
- * H (e is then the solution of the consistent rows only).  Plain dense GF(2)
- * elimination, one byte per entry.  Returns 0, or -1 on bad sizes. */
-int oracle_osd0(int32_t m, int32_t n, const int32_t *indptr, const int32_t *indices, const uint32_t *syndromes,
-                const double *soft, int64_t shots, uint32_t *out_e, int32_t *out_valid, int32_t n_threads)
+ * (the information set, rank(H) of them) and solve H e = s on them (OSD-0).
+ * With order lambda > 0 (combination sweep): every set T of one or two of the
+ * first lambda columns outside the information set, in the same order, is
+ * also tried -- e_T = 1 and the information-set bits re-solved -- and the
+ * candidate of least weight sum_j e_j w_j (w = col_weights, the prior LLRs)
+ * is kept, OSD-0's on ties.  out_valid[s] = 0 when s is not in the column
+ * space of H.  Plain dense GF(2) elimination, one byte per entry.  Returns 0,
+ * or -1 on bad sizes. */
+int oracle_osd(int32_t m, int32_t n, const int32_t *indptr, const int32_t *indices, const uint32_t *syndromes,
+               const double *soft, const double *col_weights, int32_t lambda, int64_t shots, uint32_t *out_e,
+               int32_t *out_valid, int32_t n_threads)
 {
-    if (m < 1 || n < 1 || shots < 0) return -1;
+    if (m < 1 || n < 1 || shots < 0 || lambda < 0 || (lambda > 0 && !col_weights)) return -1;
     const int64_t wm = (m + 31) / 32, wn = (n + 31) / 32;
 #ifdef _OPENMP
     omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());
@@ -194,6 +199,9 @@ int oracle_osd0(int32_t m, int32_t n, const int32_t *indptr, const int32_t *indi
         unsigned char *A = malloc((size_t)m * (size_t)(n + 1));     /* [H_perm | s], row-major */
         int32_t *order = malloc(sizeof(int32_t) * (size_t)n);
         int32_t *pivcol = malloc(sizeof(int32_t) * (size_t)m);
+        unsigned char *ispiv = malloc((size_t)n);
+        int32_t *free_cols = malloc(sizeof(int32_t) * (size_t)n);
+        unsigned char *x = malloc((size_t)m + 1), *bestx = malloc((size_t)m + 1);
 #pragma omp for schedule(dynamic, 1)
         for (int64_t s = 0; s < shots; ++s) {
             const double *q = soft + s * n;
@@ -210,7 +218,8 @@ int oracle_osd0(int32_t m, int32_t n, const int32_t *indptr, const int32_t *indi
                 for (int32_t e = indptr[i]; e < indptr[i + 1]; ++e) A[(size_t)i * (n + 1) + indices[e]] = 1;
                 A[(size_t)i * (n + 1) + n] = (unsigned char)((syndromes[s * wm + i / 32] >> (i % 32)) & 1u);
             }
-            /* forward elimination over the columns in the chosen order */
+            /* forward elimination to reduced form over the columns in the chosen order */
+            memset(ispiv, 0, (size_t)n);
             int32_t r = 0;
             for (int32_t t = 0; t < n && r < m; ++t) {
                 const int32_t c = order[t];
@@ -228,17 +237,47 @@ int oracle_osd0(int32_t m, int32_t n, const int32_t *indptr, const int32_t *indi
                     if (i != r && A[(size_t)i * (n + 1) + c])
                         for (int32_t k = 0; k <= n; ++k) A[(size_t)i * (n + 1) + k] ^= A[(size_t)r * (n + 1) + k];
                 pivcol[r++] = c;
+                ispiv[c] = 1;
             }
             int valid = 1;
             for (int32_t i = r; i < m; ++i)
                 if (A[(size_t)i * (n + 1) + n]) valid = 0;          /* 0 = 1 row: s outside the column space */
+            /* OSD-0: information-set bits = reduced right-hand side */
+            for (int32_t i = 0; i < r; ++i) bestx[i] = A[(size_t)i * (n + 1) + n];
+            int32_t bt1 = -1, bt2 = -1;                            /* best flipped non-pivot columns */
+            if (lambda > 0) {
+                int32_t nf = 0;
+                for (int32_t t = 0; t < n && nf < lambda; ++t)
+                    if (!ispiv[order[t]]) free_cols[nf++] = order[t];
+                double bestw = 0.0;
+                for (int32_t i = 0; i < r; ++i) if (bestx[i]) bestw += col_weights[pivcol[i]];
+                for (int32_t u = 0; u < nf; ++u)
+                    for (int32_t v = u; v < nf; ++v) {             /* v == u: the single flip */
+                        const int32_t c1 = free_cols[u], c2 = free_cols[v];
+                        double w = col_weights[c1] + (v != u ? col_weights[c2] : 0.0);
+                        for (int32_t i = 0; i < r; ++i) {
+                            unsigned char bit = A[(size_t)i * (n + 1) + n] ^ A[(size_t)i * (n + 1) + c1];
+                            if (v != u) bit ^= A[(size_t)i * (n + 1) + c2];
+                            x[i] = bit;
+                            if (bit) w += col_weights[pivcol[i]];
+                        }
+                        if (w < bestw) {
+                            bestw = w;
+                            memcpy(bestx, x, (size_t)r);
+                            bt1 = c1;
+                            bt2 = (v != u) ? c2 : -1;
+                        }
+                    }
+            }
             uint32_t *e = out_e + s * wn;
             memset(e, 0, sizeof(uint32_t) * (size_t)wn);
-            for (int32_t i = 0; i < r; ++i)                          /* reduced form: e_pivot = rhs */
-                if (A[(size_t)i * (n + 1) + n]) e[pivcol[i] / 32] |= 1u << (pivcol[i] % 32);
+            for (int32_t i = 0; i < r; ++i)
+                if (bestx[i]) e[pivcol[i] / 32] |= 1u << (pivcol[i] % 32);
+            if (bt1 >= 0) e[bt1 / 32] |= 1u << (bt1 % 32);
+            if (bt2 >= 0) e[bt2 / 32] |= 1u << (bt2 % 32);
             out_valid[s] = valid;
         }
-        free(A); free(order); free(pivcol);
+        free(A); free(order); free(pivcol); free(ispiv); free(free_cols); free(x); free(bestx);
     }
     return 0;
 }

@@ -201,7 +201,7 @@ static double knot_gamma_l(const double *knots, int32_t K, double u);
 static void decode_one(const graph_t *g, const oracle_params *P, const learned_t *LP, const uint32_t *syn,
                        uint64_t shot, uint32_t *corr, int32_t *stats, double *weight, int trace_iters,
                        double *trace, double *nu, double *mu, double *M, double *Lam, double *gam, uint8_t *ehat,
-                       uint8_t *best)
+                       uint8_t *best, double *final_post)
 {
     const int32_t V = g->n_loc, C = g->n_det, E = g->rptr[C];
     const double *L0 = g->L0;
@@ -293,6 +293,7 @@ static void decode_one(const graph_t *g, const oracle_params *P, const learned_t
     stats[2] = legs;
     stats[3] = iters;
     *weight = w;
+    if (final_post) memcpy(final_post, M, sizeof(double) * (size_t)V);     /* marginals after the last iteration */
 }
 
 /* Decode `shots` syndromes.  stats: [shots][4] = converged, #solutions, legs,
@@ -305,7 +306,7 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
                        const double *priors, const oracle_params *P, const learned_t *LP,
                        const uint32_t *syndromes, uint64_t shot0, int64_t shots,
                        uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
-                       int32_t trace_iters, double *trace, int32_t n_threads);
+                       int32_t trace_iters, double *trace, double *final_post, int32_t n_threads);
 
 int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
                           const int32_t *H_indptr, const int32_t *H_indices,
@@ -316,7 +317,22 @@ int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
                           int32_t trace_iters, double *trace, int32_t n_threads)
 {
     return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, NULL, syndromes,
-                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, n_threads);
+                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, NULL, n_threads);
+}
+
+/* Same, also writing each shot's marginals M after its last iteration to
+ * final_post [shots][n_loc] (the soft output that OSD post-processing of a
+ * nonconverged shot orders its columns by). */
+int oracle_relaybp_decode_post(int32_t n_det, int32_t n_loc, int32_t n_obs,
+                               const int32_t *H_indptr, const int32_t *H_indices,
+                               const int32_t *O_indptr, const int32_t *O_indices,
+                               const double *priors, const oracle_params *P,
+                               const uint32_t *syndromes, uint64_t shot0, int64_t shots,
+                               uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
+                               double *final_post, int32_t n_threads)
+{
+    return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, NULL, syndromes,
+                       shot0, shots, corrections, pred_obs, stats, weights, 0, NULL, final_post, n_threads);
 }
 
 /* Relay-BP with learned parameters: w [T][E] (or NULL), knots [K+1] (or NULL). */
@@ -332,7 +348,7 @@ int oracle_relaybp_decode_learned(int32_t n_det, int32_t n_loc, int32_t n_obs,
     if ((w && T < 1) || (knots && K < 1) || (w && P->carry_messages)) return -1;
     learned_t LP = {T, K, w, knots, legs};
     return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, &LP, syndromes,
-                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, n_threads);
+                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, NULL, n_threads);
 }
 
 static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
@@ -341,7 +357,7 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
                        const double *priors, const oracle_params *P, const learned_t *LP,
                        const uint32_t *syndromes, uint64_t shot0, int64_t shots,
                        uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
-                       int32_t trace_iters, double *trace, int32_t n_threads)
+                       int32_t trace_iters, double *trace, double *final_post, int32_t n_threads)
 {
     if (n_det < 0 || n_loc < 0 || shots < 0 || !P) return -1;
     if (P->pre_iter < 0 || P->max_iterations < 0 || P->num_sets < 0 || P->stop_nconv < 1) return -1;
@@ -389,7 +405,7 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
             uint32_t *corr = corrections + s * wv;
             decode_one(&g, P, LP, syndromes + s * wd, shot0 + (uint64_t)s, corr, stats + 4 * s, weights + s,
                        trace_iters, trace ? trace + s * (int64_t)trace_iters * n_loc : NULL,
-                       nu, mu, M, Lam, gam, ehat, best);
+                       nu, mu, M, Lam, gam, ehat, best, final_post ? final_post + s * (int64_t)n_loc : NULL);
             if (pred_obs) {
                 uint32_t *po = pred_obs + s * wo;
                 memset(po, 0, sizeof(uint32_t) * (size_t)wo);

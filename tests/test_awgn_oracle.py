@@ -205,3 +205,63 @@ def test_osd0_flags_syndromes_outside_the_column_space():
     e = oracle.unpack_bits(r["corrections"], 4).astype(np.int64)
     for s in (0, 2):
         assert np.array_equal((e[s] @ H.T) % 2, S[s])
+
+
+def _gf2_solve(A, b):
+    """x with A x = b over GF(2) for A of full column rank (plain elimination)."""
+    A = (np.asarray(A, dtype=np.uint8) % 2).copy()
+    b = (np.asarray(b, dtype=np.uint8) % 2).copy()
+    m, k = A.shape
+    row, piv = 0, []
+    for c in range(k):
+        p = next((i for i in range(row, m) if A[i, c]), None)
+        assert p is not None
+        A[[row, p]] = A[[p, row]]
+        b[[row, p]] = b[[p, row]]
+        for i in range(m):
+            if i != row and A[i, c]:
+                A[i] ^= A[row]
+                b[i] ^= b[row]
+        piv.append(c)
+        row += 1
+    assert not b[row:].any()
+    return b[:k]
+
+
+def test_osd_combination_sweep_minimises_weight():
+    """OSD with order 8: independently, for the information set and each flip
+    of one or two of the first 8 other columns, solve H e = s and weigh e by
+    the prior LLRs; the oracle's answer attains the least weight, is valid,
+    and never weighs more than its OSD-0 answer."""
+    from workloads.dem import circuit_dem
+    D = circuit_dem("ZSZ-LP-60", 0.01, 1, "Z")
+    H = D.dense_H().astype(np.uint8)
+    m, n = H.shape
+    w = np.log((1 - D.priors) / D.priors)
+    rng = np.random.default_rng(8)
+    E = (rng.random((8, n)) < 0.01).astype(np.uint8)
+    S = (E.astype(np.int64) @ H.T) % 2
+    soft = rng.normal(2.0, 3.0, (8, n))
+    lam = 8
+    r = oracle.osd(D.H_indptr, D.H_indices, m, n, oracle.pack_bits(S), soft, order=lam, weights=w)
+    r0 = oracle.osd0(D.H_indptr, D.H_indices, m, n, oracle.pack_bits(S), soft)
+    e = oracle.unpack_bits(r["corrections"], n).astype(np.int64)
+    e0 = oracle.unpack_bits(r0["corrections"], n).astype(np.int64)
+    assert np.array_equal((e @ H.T) % 2, S)
+    for s in range(S.shape[0]):
+        order = sorted(range(n), key=lambda j: (soft[s, j], j))
+        info = _info_set(H, order)
+        rest = [c for c in order if c not in set(info)][:lam]
+        best = None
+        for T in [()] + [(a,) for a in rest] + [(a, b) for i, a in enumerate(rest) for b in rest[i + 1:]]:
+            rhs = S[s].copy()
+            for c in T:
+                rhs ^= H[:, c]
+            x = _gf2_solve(H[:, info], rhs)
+            cand = np.zeros(n, dtype=np.int64)
+            cand[info] = x
+            cand[list(T)] = 1
+            cw = float(w[cand == 1].sum())
+            best = cw if best is None else min(best, cw)
+        assert float(w[e[s] == 1].sum()) == pytest.approx(best, rel=1e-12)
+        assert float(w[e[s] == 1].sum()) <= float(w[e0[s] == 1].sum()) + 1e-12
