@@ -424,3 +424,48 @@ def test_mw_brute_force_weight_le4_60():
     got = eh.sum(1)
     assert np.all(got[conv] >= best[conv])
     assert (got[conv] == best[conv]).mean() > 0.95
+
+
+def test_mw_brute_force_classical_zsz_2bga_64():
+    """ZSZ-2BGA-64 (H_left of ZSZ-LP-160, [64, 32, 10]) under i.i.d. bit flips:
+    the minimum weight of every syndrome of a weight <= 5 error, by tabulating
+    all 8,303,633 patterns of weight <= 5 (<= d/2, so each such error is a
+    minimum-weight solution of its syndrome, the only one below d/2); every
+    converged Relay-BP answer to weight-4 and weight-5 errors satisfies
+    H e^ = s, weighs at least that minimum, and here always reaches it."""
+    from workloads.dem import dem_from_dense
+    from workloads.zsz import load_code
+    H = load_code("ZSZ-LP-160").H_left.astype(np.int64)
+    m, n = H.shape
+    col = (H * (1 << np.arange(m, dtype=np.int64))[:, None]).sum(0)
+    syn_all, wt_all = [np.zeros(1, dtype=np.int64)], [np.zeros(1, dtype=np.int8)]
+    for w in range(1, 6):
+        idx = np.fromiter(itertools.chain.from_iterable(itertools.combinations(range(n), w)), dtype=np.int8)
+        idx = idx.reshape(-1, w).astype(np.int64)
+        syn_all.append(np.bitwise_xor.reduce(col[idx], axis=1))
+        wt_all.append(np.full(idx.shape[0], w, dtype=np.int8))
+    syn_all, wt_all = np.concatenate(syn_all), np.concatenate(wt_all)
+    order = np.lexsort((wt_all, syn_all))
+    syn_s, wt_s = syn_all[order], wt_all[order]
+    first = np.r_[True, syn_s[1:] != syn_s[:-1]]
+    keys, mw = syn_s[first], wt_s[first]
+    # below half the distance every syndrome has a single pattern of that weight
+    assert np.unique(syn_all[wt_all <= 4]).size == int((wt_all <= 4).sum())
+    D = dem_from_dense(H.astype(np.uint8), np.full(n, 0.03))
+    rng = np.random.default_rng(21)
+    E = np.zeros((200, n), dtype=np.uint8)
+    for t in range(E.shape[0]):
+        E[t, rng.choice(n, 4 + t % 2, replace=False)] = 1
+    S = (E.astype(np.int64) @ H.T) % 2
+    r = oracle.decode(D, DecodeParams(num_sets=50, gamma_min=-0.24, gamma_max=0.66, seed=3), pack_bits(S))
+    eh = unpack_bits(r["corrections"], n).astype(np.int64)
+    conv = r["stats"][:, 0] == 1
+    assert conv.mean() > 0.9
+    assert np.array_equal((eh[conv] @ H.T) % 2, S[conv])
+    sid = (S * (1 << np.arange(m, dtype=np.int64))).sum(1)
+    best = mw[np.searchsorted(keys, sid)].astype(np.int64)
+    assert np.array_equal(keys[np.searchsorted(keys, sid)], sid)
+    assert np.all(best == E.sum(1))                 # weight <= d/2: the error itself is a minimum
+    got = eh.sum(1)
+    assert np.all(got[conv] >= best[conv])
+    assert (got[conv] == best[conv]).mean() > 0.95
