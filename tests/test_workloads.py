@@ -345,3 +345,55 @@ def test_ogs_generators(row):
         c, d = alg(code.c_terms), alg(code.d_terms)
         assert np.array_equal(mul(bar(d), v), bar(c))
         assert gf2_rank(left_matrix(d)) == G.order
+
+
+def test_ogm_orbits_give_full_rank_logical_bases_160():
+    """Sec. 3.2 and Table 7: the OGM seed codewords (bar u, bar v) of H_left and
+    H_right (weight d = 10) generate, under the group action that commutes
+    with each seed code (right multiplication for H_left = (L[a] L[b]), left
+    for H_right = (R[c] R[d])), orbits of rank l = 32; embedded as
+    z1 = (c1, 0, c2, 0, 0), z2 = (0, c1, 0, c2, 0) they lie in ker H_X, as
+    x1 = (c1, c2, 0, 0, 0), x2 = (0, 0, c1, c2, 0) in ker H_Z, and span a
+    full k = 32 dimensional logical space outside rs H_Z (rs H_X); z1 has
+    weight 10, so d_Z <= 10."""
+    code = load_code("ZSZ-LP-160")
+    G, ell = code.G, code.ell
+
+    def alg(ts):
+        v = np.zeros(G.order, dtype=np.uint8)
+        for (a, b) in ts:
+            v[G.elem(a, b)] ^= 1
+        return v
+
+    def bar(u):
+        out = np.zeros_like(u)
+        out[G.inv[np.nonzero(u)[0]]] = 1
+        return out
+
+    def right(x, g):                       # R[g]: basis element h -> h g
+        out = np.zeros_like(x)
+        out[G.mul[np.nonzero(x)[0], g]] = 1
+        return out
+
+    def left(x, g):                        # L[g]: basis element h -> g h
+        out = np.zeros_like(x)
+        out[G.mul[g, np.nonzero(x)[0]]] = 1
+        return out
+
+    cl = (bar(alg([(8, 0), (11, 0), (4, 1), (8, 1), (13, 1)])), bar(alg([(0, 0), (10, 0), (15, 0), (3, 1), (11, 1)])))
+    cr = (bar(alg([(3, 0), (8, 0), (13, 0), (3, 1), (5, 1), (7, 1), (10, 1)])), bar(alg([(5, 0), (8, 0), (10, 1)])))
+    z0 = np.zeros(ell, dtype=np.uint8)
+    orb_l = np.array([np.r_[right(cl[0], g), right(cl[1], g)] for g in range(ell)])
+    orb_r = np.array([np.r_[left(cr[0], g), left(cr[1], g)] for g in range(ell)])
+    assert not ((orb_l.astype(int) @ code.H_left.T.astype(int)) % 2).any()
+    assert not ((orb_r.astype(int) @ code.H_right.T.astype(int)) % 2).any()
+    assert gf2_rank(orb_l) == ell and gf2_rank(orb_r) == ell
+    Z = np.array([np.r_[c[:ell], z0, c[ell:], z0, z0] for c in orb_l] +
+                 [np.r_[z0, c[:ell], z0, c[ell:], z0] for c in orb_l])
+    X = np.array([np.r_[c[:ell], c[ell:], z0, z0, z0] for c in orb_r] +
+                 [np.r_[z0, z0, c[:ell], c[ell:], z0] for c in orb_r])
+    assert not ((Z.astype(int) @ code.H_X.T.astype(int)) % 2).any()
+    assert not ((X.astype(int) @ code.H_Z.T.astype(int)) % 2).any()
+    assert gf2_rank(np.r_[code.H_Z, Z]) - gf2_rank(code.H_Z) == code.k
+    assert gf2_rank(np.r_[code.H_X, X]) - gf2_rank(code.H_X) == code.k
+    assert Z[0].sum() == code.d and gf2_rank(np.r_[code.H_Z, Z[:1]]) > gf2_rank(code.H_Z)
