@@ -469,3 +469,42 @@ def test_mw_brute_force_classical_zsz_2bga_64():
     got = eh.sum(1)
     assert np.all(got[conv] >= best[conv])
     assert (got[conv] == best[conv]).mean() > 0.95
+
+
+def test_center_automorphism_symmetry():
+    """ZSZ-LP-160 H_X with random (generic) priors: for every centre element z,
+    permuting the syndrome by P_z^{+2} and the priors by P_z^{+5} permutes the
+    decoder's state by P_z^{+5} (H P_z^{+5} = P_z^{+2} H, App. D).  Leg 0
+    only, so every memory strength is gamma0 and needs no permuting.  Min-sum's
+    check update is a symmetric function of the other inputs, so only the order
+    of the variable sums changes: the posteriors agree to rounding over the
+    first iterations, and the decisions agree exactly on every shot that
+    settles quickly (later, the iteration map amplifies the roundings, as for
+    any two evaluation orders)."""
+    from workloads.dem import dem_from_dense
+    from workloads.zsz import L_mat, load_code
+    code = load_code("ZSZ-LP-160")
+    H = code.H_X.astype(np.int64)
+    m, n = H.shape
+    rng = np.random.default_rng(31)
+    p = rng.uniform(0.005, 0.03, n)
+    E = (rng.random((80, n)) < p).astype(np.int64)
+    S = (E @ H.T) % 2
+    prm = DecodeParams(num_sets=0, pre_iter=80, seed=1)
+    r = oracle.decode(dem_from_dense(H.astype(np.uint8), p), prm, pack_bits(S), trace_iters=4)
+    eh = unpack_bits(r["corrections"], n).astype(np.int64)
+    quick = (r["stats"][:, 0] == 1) & (r["stats"][:, 3] <= 10)
+    assert quick.sum() >= 40
+    centre = [z for z in code.G.center() if z != code.G.elem(0, 0)]
+    assert len(centre) == 7
+    for z in centre:
+        P = L_mat(code.G, [z]).astype(np.int64)
+        P5, P2 = np.kron(np.eye(5, dtype=np.int64), P), np.kron(np.eye(2, dtype=np.int64), P)
+        rz = oracle.decode(dem_from_dense(H.astype(np.uint8), P5 @ p), prm, pack_bits((S @ P2.T) % 2),
+                           trace_iters=4)
+        for s_ in range(S.shape[0]):
+            t = min(4, int(r["stats"][s_, 3]), int(rz["stats"][s_, 3]))
+            assert np.allclose(rz["trace"][s_, :t], r["trace"][s_, :t] @ P5.T, rtol=1e-12, atol=1e-12)
+        ez = unpack_bits(rz["corrections"], n).astype(np.int64)
+        assert np.array_equal(ez[quick], ((eh @ P5.T) % 2)[quick])
+        assert np.array_equal(rz["stats"][quick], r["stats"][quick])
