@@ -77,3 +77,57 @@ def test_null_handle_calls_fail_cleanly():
     assert R._lib.relaybp_decode_batch(None, None, 0, 1, None, None, None, None) == -1
     assert R._lib.relaybp_sample(None, 0, 0, 1, None, None, None, None) == -1
     assert R._lib.relaybp_destroy(None) == 0
+
+
+# Entry points whose first argument is a handle (or group): called with a NULL
+# one and zero / NULL everywhere else, each returns a negative status (or -1
+# for the size queries) and sets an error message -- no crash, no device work.
+_HANDLE_CALLS = ["relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows", "relaybp_set_learned_legs",
+                 "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch", "relaybp_decode_timed",
+                 "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host",
+                 "relaybp_count_failures", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
+                 "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_decode"]
+
+
+@pytest.mark.parametrize("name", _HANDLE_CALLS)
+def test_every_handle_call_rejects_a_null_handle(name):
+    from paper_2607_27644_b300 import relaybp as R
+    fn = getattr(R._lib, name)
+    args = []
+    for t in fn.argtypes:
+        if t is ctypes.c_double:
+            args.append(0.0)
+        elif t in (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64):
+            args.append(1 if t is ctypes.c_int64 else 0)          # one shot where a count is asked for
+        else:
+            args.append(None)
+    assert fn(*args) < 0
+    assert R.relaybp_last_error()
+
+
+def test_group_create_rejects_empty_and_oversized_groups():
+    from paper_2607_27644_b300 import relaybp as R
+    out = ctypes.c_void_p()
+    assert R._lib.relaybp_group_create(None, 0, ctypes.byref(out)) < 0 and out.value is None
+    assert R._lib.relaybp_group_create(None, 17, ctypes.byref(out)) < 0 and out.value is None
+
+
+@pytest.mark.parametrize("dtype,scale,ok", [("f32", 0.5, False), ("i8", -1.0, False), ("i8", float("inf"), False),
+                                            ("f16", 0.0, True)])
+def test_int8_scale_is_validated_before_any_device_work(dtype, scale, ok):
+    """int8_scale must be 0 except for int8 storage, and finite and >= 0 there;
+    a rejected parameter set fails before any CUDA call (so also here)."""
+    from paper_2607_27644_b300 import relaybp as R
+    cp = R.Params(msg_dtype=dtype, int8_scale=scale).c()
+    H, keep = _csr(2, 3, [0, 2, 4], [0, 1, 1, 2])
+    pr = np.full(3, 0.1)
+    out = ctypes.c_void_p()
+    rc = R._lib.relaybp_build(ctypes.byref(H), pr.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(cp),
+                              ctypes.byref(out))
+    msg = R.relaybp_last_error()
+    if ok:
+        assert rc == 0 or "int8_scale" not in msg
+    else:
+        assert rc == -1 and "int8_scale" in msg and out.value is None
+    if rc == 0:
+        R._lib.relaybp_destroy(out)
