@@ -1,13 +1,20 @@
 """CPU oracle for the Relay-BP hot path -- TEST INFRASTRUCTURE ONLY.
 
 Only the tests, the smoke check and the benchmark's CPU-baseline / reference
-legs may import this package.  It wraps ``relaybp_oracle.c`` (plain C, FP64)
-through ctypes; that file cites the passages of arXiv 2607.27644 it follows.
+legs may import this package.  It wraps ``relaybp_oracle.c`` (Relay-BP, the
+fault sampler, the learned loss) and ``awgn_oracle.c`` (BPSK-AWGN sum-product
+BP, OSD post-processing), plain C in FP64, through ctypes, and adds
+``windows.py`` (sliding-window decoding over the Relay-BP oracle); each file
+cites the passages of arXiv 2607.27644 it follows.  ``min_weight`` enumerates
+codewords for the distance pins of the code builder.
 
-Pins (tests/test_oracle_*.py) tie it to things other than itself: published
-Philox known-answer vectors, brute-force min-marginals on cycle-free graphs,
-a closed-form memory recurrence, brute-force minimum-weight decoding of the
-[[60,12,6]] code, and invariants (H e^ = s on every claimed success).
+Pins (tests/test_oracle.py, tests/test_awgn_oracle.py, tests/test_windows.py,
+tests/test_workloads.py) tie it to things other than itself: published
+Philox known-answer vectors, brute-force min-marginals and exact bitwise MAP
+on cycle-free graphs, a closed-form memory recurrence, brute-force
+minimum-weight decoding of the [[60,12,6]] and ZSZ-2BGA-64 codes, centre
+automorphism equivariance, a stabilizer-tableau simulation of the circuits,
+and invariants (H e^ = s on every claimed success).
 """
 from __future__ import annotations
 
