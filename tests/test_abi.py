@@ -42,7 +42,8 @@ def _csr(rows, cols, indptr, indices):
     return relaybp_csr(rows, cols, ip.ctypes.data_as(ctypes.c_void_p), ix.ctypes.data_as(ctypes.c_void_p)), (ip, ix)
 
 
-@pytest.mark.parametrize("case", ["col_range", "unsorted", "single", "prior", "params", "dtype"])
+@pytest.mark.parametrize("case", ["col_range", "unsorted", "single", "prior", "prior_nan", "prior_one", "params",
+                                  "dtype"])
 def test_build_rejects_invalid_input(case):
     from paper_2607_27644_b300 import relaybp as R
     indptr, indices, pri = [0, 2, 4], [0, 1, 1, 2], [0.1, 0.1, 0.1]
@@ -55,6 +56,10 @@ def test_build_rejects_invalid_input(case):
         indptr, indices = [0, 1, 3], [0, 1, 2]
     elif case == "prior":
         pri = [0.1, 0.0, 0.1]
+    elif case == "prior_nan":
+        pri = [0.1, float("nan"), 0.1]
+    elif case == "prior_one":
+        pri = [0.1, 1.0, 0.1]
     elif case == "params":
         p = R.Params(stop_nconv=0)
     elif case == "dtype":
