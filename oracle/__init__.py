@@ -14,7 +14,9 @@ Philox known-answer vectors, brute-force min-marginals and exact bitwise MAP
 on cycle-free graphs, a closed-form memory recurrence, brute-force
 minimum-weight decoding of the [[60,12,6]] and ZSZ-2BGA-64 codes, centre
 automorphism equivariance, a stabilizer-tableau simulation of the circuits,
-and invariants (H e^ = s on every claimed success).
+and invariants (H e^ = s on every claimed success); the minimum-weight
+select against per-shot solution records (``solutions``) and brute-force
+solution sets, and the leg carry-over against a hand-derived recurrence.
 """
 from __future__ import annotations
 
@@ -88,6 +90,9 @@ def _load():
                                                         ctypes.c_int64,
                                                         P, P, P, P, ctypes.c_int32, P, ctypes.c_int32])
         _lib.oracle_relaybp_decode_learned.restype = ctypes.c_int
+        _lib.oracle_relaybp_solutions.argtypes = ([ctypes.c_int32] * 2 + [P] * 3 + [ctypes.POINTER(OracleParams), P,
+                                                  ctypes.c_uint64, P, P, P, ctypes.c_int32, P, P, P, P, P])
+        _lib.oracle_relaybp_solutions.restype = ctypes.c_int
     return _lib
 
 
@@ -264,6 +269,34 @@ def decode(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0, tra
     if rc != 0:
         raise ValueError("oracle_relaybp_decode rejected its input")
     return dict(corrections=corr, pred_obs=pobs, stats=stats, weights=wts, trace=trace)
+
+
+def solutions(dem, params: DecodeParams, syndrome: np.ndarray, shot: int = 0, cap: int = 64) -> dict:
+    """Decode one syndrome [ceil(C/32)] and record every solution found, in
+    order: dict(correction, stats[4], weight, found, legs[n], iters[n],
+    weights[n], bits[n, ceil(V/32)]) with n = min(found, cap); iters[r] is the
+    shot's iteration count when solution r was found."""
+    lib = _load()
+    Hp, Hi, _, _, pr = _dem_arrays(dem)
+    syn = np.ascontiguousarray(np.asarray(syndrome, dtype=np.uint32).reshape(-1))
+    wv = (dem.n_loc + 31) // 32
+    corr = np.zeros(wv, dtype=np.uint32)
+    stats = np.zeros(4, dtype=np.int32)
+    wt = np.zeros(1, dtype=np.float64)
+    legs = np.zeros(max(1, cap), dtype=np.int32)
+    iters = np.zeros(max(1, cap), dtype=np.int32)
+    wts = np.zeros(max(1, cap), dtype=np.float64)
+    bits = np.zeros((max(1, cap), wv), dtype=np.uint32)
+    found = np.zeros(1, dtype=np.int32)
+    cp = params.c()
+    rc = lib.oracle_relaybp_solutions(dem.n_det, dem.n_loc, _ptr(Hp), _ptr(Hi), _ptr(pr), ctypes.byref(cp), _ptr(syn),
+                                      shot, _ptr(corr), _ptr(stats), _ptr(wt), cap, _ptr(legs), _ptr(iters),
+                                      _ptr(wts), _ptr(bits), _ptr(found))
+    if rc != 0:
+        raise ValueError("oracle_relaybp_solutions rejected its input")
+    n = min(int(found[0]), cap)
+    return dict(correction=corr, stats=stats, weight=float(wt[0]), found=int(found[0]), legs=legs[:n],
+                iters=iters[:n], weights=wts[:n], bits=bits[:n])
 
 
 def decode_with_posteriors(dem, params: DecodeParams, syndromes: np.ndarray, shot0: int = 0,

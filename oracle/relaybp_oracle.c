@@ -198,10 +198,22 @@ typedef struct {
 
 static double knot_gamma_l(const double *knots, int32_t K, double u);
 
+/* Optional record of every solution a decode finds, in the order found: its
+ * leg, the shot's iteration count when it was found, its FP64 weight and its
+ * bits (packed, ceil(V/32) words each).  Test infrastructure for the
+ * minimum-weight select (a7): a test recomputes each weight from the bits and
+ * checks that the returned correction is the first record of least weight. */
+typedef struct {
+    int32_t cap, n;
+    int32_t *leg, *iter;
+    double *weight;
+    uint32_t *bits;
+} sol_rec_t;
+
 static void decode_one(const graph_t *g, const oracle_params *P, const learned_t *LP, const uint32_t *syn,
                        uint64_t shot, uint32_t *corr, int32_t *stats, double *weight, int trace_iters,
                        double *trace, double *nu, double *mu, double *M, double *Lam, double *gam, uint8_t *ehat,
-                       uint8_t *best, double *final_post)
+                       uint8_t *best, double *final_post, sol_rec_t *rec)
 {
     const int32_t V = g->n_loc, C = g->n_det, E = g->rptr[C];
     const double *L0 = g->L0;
@@ -274,6 +286,16 @@ static void decode_one(const graph_t *g, const oracle_params *P, const learned_t
                 double w = 0.0;                                  /* a7: FP64 weight */
                 for (int32_t j = 0; j < V; ++j) if (ehat[j]) w += L0[j];
                 nsol++;
+                if (rec && rec->n < rec->cap) {
+                    const int32_t wv = (V + 31) / 32;
+                    uint32_t *rb = rec->bits + (int64_t)rec->n * wv;
+                    memset(rb, 0, sizeof(uint32_t) * (size_t)wv);
+                    for (int32_t j = 0; j < V; ++j) if (ehat[j]) flip_bit(rb, j);
+                    rec->leg[rec->n] = leg;
+                    rec->iter[rec->n] = iters;
+                    rec->weight[rec->n] = w;
+                    rec->n++;
+                }
                 if (!have_best || w < best_w) {
                     have_best = 1;
                     best_w = w;
@@ -306,7 +328,8 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
                        const double *priors, const oracle_params *P, const learned_t *LP,
                        const uint32_t *syndromes, uint64_t shot0, int64_t shots,
                        uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
-                       int32_t trace_iters, double *trace, double *final_post, int32_t n_threads);
+                       int32_t trace_iters, double *trace, double *final_post, int32_t n_threads,
+                       sol_rec_t *rec);
 
 int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
                           const int32_t *H_indptr, const int32_t *H_indices,
@@ -317,7 +340,7 @@ int oracle_relaybp_decode(int32_t n_det, int32_t n_loc, int32_t n_obs,
                           int32_t trace_iters, double *trace, int32_t n_threads)
 {
     return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, NULL, syndromes,
-                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, NULL, n_threads);
+                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, NULL, n_threads, NULL);
 }
 
 /* Same, also writing each shot's marginals M after its last iteration to
@@ -332,7 +355,24 @@ int oracle_relaybp_decode_post(int32_t n_det, int32_t n_loc, int32_t n_obs,
                                double *final_post, int32_t n_threads)
 {
     return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, NULL, syndromes,
-                       shot0, shots, corrections, pred_obs, stats, weights, 0, NULL, final_post, n_threads);
+                       shot0, shots, corrections, pred_obs, stats, weights, 0, NULL, final_post, n_threads, NULL);
+}
+
+/* One shot's decode with every solution it finds recorded (sol_rec_t above):
+ * up to `cap` records of leg, iteration count, weight and packed bits
+ * [cap][ceil(n_loc/32)]; *n_found = solutions found (may exceed cap).
+ * Single-threaded.  Returns 0, or -1 on invalid input. */
+int oracle_relaybp_solutions(int32_t n_det, int32_t n_loc, const int32_t *H_indptr, const int32_t *H_indices,
+                             const double *priors, const oracle_params *P, const uint32_t *syndrome, uint64_t shot,
+                             uint32_t *correction, int32_t *stats, double *weight, int32_t cap, int32_t *rec_leg,
+                             int32_t *rec_iter, double *rec_weight, uint32_t *rec_bits, int32_t *n_found)
+{
+    if (cap < 0 || (cap > 0 && (!rec_leg || !rec_iter || !rec_weight || !rec_bits)) || !n_found) return -1;
+    sol_rec_t rec = {cap, 0, rec_leg, rec_iter, rec_weight, rec_bits};
+    int rc = decode_impl(n_det, n_loc, 0, H_indptr, H_indices, NULL, NULL, priors, P, NULL, syndrome, shot, 1,
+                         correction, NULL, stats, weight, 0, NULL, NULL, 1, &rec);
+    *n_found = rc == 0 ? stats[1] : 0;
+    return rc;
 }
 
 /* Relay-BP with learned parameters: w [T][E] (or NULL), knots [K+1] (or NULL). */
@@ -348,7 +388,7 @@ int oracle_relaybp_decode_learned(int32_t n_det, int32_t n_loc, int32_t n_obs,
     if ((w && T < 1) || (knots && K < 1) || (w && P->carry_messages)) return -1;
     learned_t LP = {T, K, w, knots, legs};
     return decode_impl(n_det, n_loc, n_obs, H_indptr, H_indices, O_indptr, O_indices, priors, P, &LP, syndromes,
-                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, NULL, n_threads);
+                       shot0, shots, corrections, pred_obs, stats, weights, trace_iters, trace, NULL, n_threads, NULL);
 }
 
 static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
@@ -357,9 +397,11 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
                        const double *priors, const oracle_params *P, const learned_t *LP,
                        const uint32_t *syndromes, uint64_t shot0, int64_t shots,
                        uint32_t *corrections, uint32_t *pred_obs, int32_t *stats, double *weights,
-                       int32_t trace_iters, double *trace, double *final_post, int32_t n_threads)
+                       int32_t trace_iters, double *trace, double *final_post, int32_t n_threads,
+                       sol_rec_t *rec)
 {
     if (n_det < 0 || n_loc < 0 || shots < 0 || !P) return -1;
+    if (rec && shots != 1) return -1;                         /* a record covers one shot */
     if (P->pre_iter < 0 || P->max_iterations < 0 || P->num_sets < 0 || P->stop_nconv < 1) return -1;
     int64_t wd = (n_det + 31) / 32, wv = (n_loc + 31) / 32, wo = (n_obs + 31) / 32;
     int32_t E = H_indptr[n_det];
@@ -405,7 +447,7 @@ static int decode_impl(int32_t n_det, int32_t n_loc, int32_t n_obs,
             uint32_t *corr = corrections + s * wv;
             decode_one(&g, P, LP, syndromes + s * wd, shot0 + (uint64_t)s, corr, stats + 4 * s, weights + s,
                        trace_iters, trace ? trace + s * (int64_t)trace_iters * n_loc : NULL,
-                       nu, mu, M, Lam, gam, ehat, best, final_post ? final_post + s * (int64_t)n_loc : NULL);
+                       nu, mu, M, Lam, gam, ehat, best, final_post ? final_post + s * (int64_t)n_loc : NULL, rec);
             if (pred_obs) {
                 uint32_t *po = pred_obs + s * wo;
                 memset(po, 0, sizeof(uint32_t) * (size_t)wo);

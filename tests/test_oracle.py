@@ -9,6 +9,11 @@
   * Minimum-weight decoding of single errors on the [[60,12,6]] code (Table 13).
   * Invariants on circuit-level DEMs: H e^ = s on every claimed success, the
     reported weight, solution counts and leg limits.
+  * Minimum-weight select: every recorded solution against the brute-force
+    solution set of tiny graphs, weights recomputed from the bits, the first
+    record of least weight returned (ties to the earliest).
+  * Leg carry-over (messages reset or carried, M carried): a hand-derived
+    two-check, two-variable recurrence across leg boundaries.
 """
 import itertools
 import math
@@ -508,3 +513,129 @@ def test_center_automorphism_symmetry():
         ez = unpack_bits(rz["corrections"], n).astype(np.int64)
         assert np.array_equal(ez[quick], ((eh @ P5.T) % 2)[quick])
         assert np.array_equal(rz["stats"][quick], r["stats"][quick])
+
+
+# ---------------------------------------------------------------------------
+# a7 minimum-weight select and the leg carry-over, pinned independently
+# (Sec. 6.1 decoder configuration list: collect up to stop_nconv solutions
+# over the relay legs and keep the one of least weight).
+# ---------------------------------------------------------------------------
+def _all_solutions(H: np.ndarray, syn: np.ndarray) -> set:
+    """Every e in {0,1}^V with H e = s, by enumeration (V <= 12)."""
+    C, V = H.shape
+    out = set()
+    for bits in itertools.product((0, 1), repeat=V):
+        e = np.array(bits, dtype=np.int64)
+        if np.array_equal((H.astype(np.int64) @ e) % 2, syn):
+            out.add(bits)
+    return out
+
+
+def _random_small_dem(rng, C, V):
+    H = np.zeros((C, V), dtype=np.uint8)
+    for j in range(V):
+        H[rng.choice(C, size=int(rng.integers(1, 3)), replace=False), j] = 1
+    for i in range(C):
+        if H[i].sum() == 1:                          # rows need 0 or >= 2 entries
+            H[i, rng.choice(np.nonzero(H[i] == 0)[0])] = 1
+    return H
+
+
+def test_select_returns_first_least_weight_solution():
+    """Every solution a decode records is a true solution of H e = s (checked
+    against the brute-force solution set), its weight is the sum of the prior
+    LLRs log((1-p)/p) over its ones (recomputed here from the bits), and the
+    returned correction is the FIRST record of least weight.  The sample must
+    contain shots where the least weight is not the first solution and shots
+    where a heavier solution follows the least one, so that a select keeping
+    the first or the last solution fails; the tie case is the next test."""
+    rng = np.random.default_rng(7)
+    seen_later_best = seen_heavier_after = 0
+    for trial in range(12):
+        C, V = int(rng.integers(3, 6)), int(rng.integers(6, 11))
+        H = _random_small_dem(rng, C, V)
+        pr = rng.uniform(0.02, 0.3, size=V)
+        L0 = np.log((1 - pr) / pr)
+        D = dem_from_dense(H, pr)
+        P = DecodeParams(gamma0=0.1, pre_iter=20, num_sets=40, max_iterations=15, stop_nconv=5,
+                         gamma_min=-0.24, gamma_max=0.66, seed=trial)
+        for s in range(20):
+            e = (rng.random(V) < 0.25).astype(np.uint8)
+            syn = (H.astype(np.int64) @ e) % 2
+            sols = _all_solutions(H, syn)
+            r = oracle.solutions(D, P, pack_bits(syn), shot=s, cap=64)
+            n = len(r["weights"])
+            assert n == r["found"] == r["stats"][1] <= P.stop_nconv
+            assert r["stats"][0] == (1 if n else 0)
+            bits = unpack_bits(r["bits"], V)
+            for k in range(n):
+                assert tuple(int(x) for x in bits[k]) in sols, "a recorded solution does not satisfy H e = s"
+                assert math.isclose(r["weights"][k], float(np.sum(L0[bits[k] == 1])), rel_tol=1e-12, abs_tol=1e-12)
+            assert list(r["legs"]) == sorted(r["legs"]) and len(set(r["legs"])) == n   # one per leg, in order
+            if n == 0:
+                continue
+            w = r["weights"]
+            b = int(np.argmin(w))                      # numpy: first index of the minimum
+            assert np.array_equal(r["correction"], r["bits"][b])
+            assert r["weight"] == w[b]
+            seen_later_best += b > 0
+            seen_heavier_after += any(w[k] > w[b] for k in range(b + 1, n))
+    assert seen_later_best >= 5 and seen_heavier_after >= 5, (seen_later_best, seen_heavier_after)
+
+
+def test_select_keeps_earliest_of_equal_weights():
+    """One check on two variables with equal priors and syndrome 1: the
+    solutions {1,0} and {0,1} weigh the same.  Leg 0 (uniform memory strength)
+    stays symmetric and never settles; each later leg's random strengths pick
+    one of the two.  The returned correction must be the first solution found
+    even when a later leg finds the other one."""
+    p = 0.1
+    H = np.array([[1, 1]], dtype=np.uint8)
+    D = dem_from_dense(H, [p, p])
+    L0 = math.log((1 - p) / p)
+    swaps = 0
+    for shot in range(40):
+        P = DecodeParams(gamma0=0.125, pre_iter=5, num_sets=12, max_iterations=5, stop_nconv=4,
+                         gamma_min=-0.24, gamma_max=0.66, seed=99)
+        r = oracle.solutions(D, P, pack_bits(np.array([1])), shot=shot, cap=16)
+        assert r["found"] == 4 and 0 not in r["legs"]
+        assert np.all(r["weights"] == L0)
+        assert np.array_equal(r["correction"], r["bits"][0])
+        swaps += any(not np.array_equal(r["bits"][k], r["bits"][0]) for k in range(1, 4))
+    assert swaps >= 10                                 # a '<=' select would return a later, different one
+
+
+def test_carry_messages_two_check_recurrence():
+    """Two checks on the same two variables, syndrome (1, 0): unsatisfiable,
+    so every leg runs to its cap.  Each check has degree 2, so its message to
+    one variable is its syndrome sign times the other variable's message to
+    it: with x_c = nu_{c->1}, y_c = nu_{c->2}, sigma_c = (-1)^{s_c},
+        x_1(t) = sigma_1 (L_2(t) + y_2(t-1)),  x_2(t) = sigma_2 (L_2(t) + y_1(t-1)),
+        y_1(t) = sigma_1 (L_1(t) + x_2(t-1)),  y_2(t) = sigma_2 (L_1(t) + x_1(t-1)),
+        M_1 = L_1 + x_1 + x_2,  M_2 = L_2 + y_1 + y_2,  L_k(t) = (1-g) L0_k + g M_k(t-1).
+    At a leg boundary the messages restart from 0 by default and continue
+    with carry_messages = 1; M carries in both."""
+    pa, pb = 0.1, 0.3
+    a, b = math.log((1 - pa) / pa), math.log((1 - pb) / pb)
+    H = np.array([[1, 1], [1, 1]], dtype=np.uint8)
+    D = dem_from_dense(H, [pa, pb])
+    s1, s2 = -1.0, 1.0
+    for carry in (False, True):
+        for g in (0.125, 0.4, -0.2):
+            T0, T1, legs = 4, 3, 3
+            P = DecodeParams(gamma0=g, pre_iter=T0, num_sets=legs - 1, max_iterations=T1, stop_nconv=1,
+                             gamma_min=g, gamma_max=g, carry_messages=carry, seed=5)
+            r = oracle.decode(D, P, pack_bits(np.array([[1, 0]])), trace_iters=T0 + (legs - 1) * T1)
+            M1, M2 = a, b
+            x1 = x2 = y1 = y2 = 0.0
+            want = []
+            for leg in range(legs):
+                if leg > 0 and not carry:
+                    x1 = x2 = y1 = y2 = 0.0
+                for _ in range(T0 if leg == 0 else T1):
+                    L1, L2 = (1 - g) * a + g * M1, (1 - g) * b + g * M2
+                    x1, x2, y1, y2 = s1 * (L2 + y2), s2 * (L2 + y1), s1 * (L1 + x2), s2 * (L1 + x1)
+                    M1, M2 = L1 + x1 + x2, L2 + y1 + y2
+                    want.append((M1, M2))
+            assert np.allclose(r["trace"][0], np.array(want), rtol=1e-12, atol=1e-12), (carry, g)
+            assert r["stats"][0, 0] == 0 and r["stats"][0, 2] == legs
