@@ -30,6 +30,9 @@
  *   - "d_" pointers are device memory owned by the caller; "h_" pointers are
  *     host memory owned by the caller.  Structures passed to relaybp_build are
  *     copied; the caller may free them on return.
+ *   - A handle belongs to the device that was current when it was built:
+ *     every call that launches work checks that this device is current and
+ *     returns RELAYBP_ERR_INVALID otherwise.
  *   - Calls taking a stream are asynchronous on that stream (NULL = the legacy
  *     default stream); the caller synchronises before reading results.  A
  *     handle is not thread-safe: use one handle per host thread and stream.
@@ -85,7 +88,9 @@ typedef struct {
     int32_t stop_all;           /* 1: run every leg regardless of solutions (the paper's 'All') */
     int32_t carry_messages;     /* 1: keep check-to-variable messages across legs */
     float int8_scale;           /* RELAYBP_MSG_I8: value of one int8 step, > 0, or 0 for the automatic
-                                   scale (largest prior LLR / 24, per DEM); must be 0 for the other forms */
+                                   scale (largest |prior LLR| / 24, per DEM; rejected with
+                                   RELAYBP_ERR_INVALID when every prior is 1/2, which makes it 0);
+                                   must be 0 for the other forms */
     uint64_t seed;              /* key of the memory-strength draws */
 } relaybp_params;
 
@@ -186,7 +191,8 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
  *
  * - The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with the handle's device current and caches it;
- *   make that first call before any stream capture.
+ *   make that first call before any stream capture.  Every call checks that
+ *   the handle's device is current (RELAYBP_ERR_INVALID otherwise).
  * - The call zeroes the work counter in the array before its launch; the
  *   memory-strength rows are rewritten before use, so nothing else needs
  *   clearing.  The array keeps the last call's contents.

@@ -49,6 +49,11 @@ int words(int64_t bits) { return (int)((bits + 31) / 32); }
 
 }  // namespace
 
+struct relaybp_handle;
+namespace {
+int check_device(const relaybp_handle *h);
+}
+
 // Device scratch of a launch owner (a handle or a group): the persistent
 // kernel's work counter, one row of memory strengths per resident block and,
 // for DEMs too large for shared memory, one state region per resident block.
@@ -74,7 +79,7 @@ struct relaybp_handle {
     int64_t stage_shots = 0;
     int64_t launches = 0;
     int max_row_deg = 0;
-    double l0max = 0.0;             // largest prior LLR (automatic int8 scale)
+    double l0max = 0.0;             // largest |prior LLR| (automatic int8 scale)
     // learned-form training scratch: work counter and one gradient row per block
     int tuned_L = 0, tuned_NB = 0, tuned_threads = 0; // autotuned launch shape (0: heuristic)
     const float *lw = nullptr, *lknots = nullptr;     // learned inference parameters (caller-owned)
@@ -92,6 +97,19 @@ struct relaybp_group {
     Scratch scratch;
     int64_t launches = 0;
 };
+
+namespace {
+// Launching entry points work on the handle's own device only: its arrays
+// live there, and a launch on another device would read them across devices.
+int check_device(const relaybp_handle *h)
+{
+    int cur = -1;
+    CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != h->device)
+        return fail(RELAYBP_ERR_INVALID, "the handle's device %d is not current (device %d is)", h->device, cur);
+    return 0;
+}
+}  // namespace
 
 namespace {
 
@@ -147,6 +165,15 @@ int check_legs(const relaybp_params *p, int32_t V)
 {
     if ((uint64_t)(p->num_sets + 1) * (uint64_t)((V + 3) / 4) > 0xffffffffull)
         return fail(RELAYBP_ERR_INVALID, "num_sets * ceil(V/4) exceeds the 32-bit draw counter");
+    return 0;
+}
+
+// The automatic int8 step is the largest |prior LLR| / 24; it is 0 only when
+// every prior is exactly 1/2, and a zero step cannot scale anything.
+int check_int8_step(const relaybp_params &p, double l0max)
+{
+    if (p.msg_dtype == RELAYBP_MSG_I8 && p.int8_scale == 0.0f && !((float)(l0max / 24.0) > 0.0f))
+        return fail(RELAYBP_ERR_INVALID, "automatic int8 step is 0 (every prior LLR is 0): give int8_scale > 0");
     return 0;
 }
 
@@ -592,6 +619,7 @@ int learned_dispatch(relaybp_handle *h, const LearnedCall &c, bool backward, cud
 int learned_check(relaybp_handle *h, const LearnedCall &c, bool backward)
 {
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (c.precision != RELAYBP_MSG_F32 && c.precision != RELAYBP_MSG_F64)
         return fail(RELAYBP_ERR_UNSUPPORTED, "learned training runs in FP32 or FP64");
     if (c.T < 1 || c.K < 1 || c.K > 64) return fail(RELAYBP_ERR_INVALID, "need T >= 1 and 1 <= K <= 64");
@@ -665,9 +693,13 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     const int32_t C = H->rows, V = H->cols, K = obs ? obs->rows : 0;
     const int64_t E = H->indptr[C];
     if (C >= (1 << 20) || E >= (int64_t)1 << 30) return fail(RELAYBP_ERR_UNSUPPORTED, "DEM too large");
-    for (int32_t j = 0; j < V; ++j)
+    double l0max = 0.0;                                 // largest |prior LLR| (automatic int8 step)
+    for (int32_t j = 0; j < V; ++j) {
         if (!(priors[j] > 0.0 && priors[j] < 1.0))
             return fail(RELAYBP_ERR_INVALID, "prior %d = %g is not in (0, 1)", j, priors[j]);
+        l0max = std::max(l0max, std::fabs(std::log((1.0 - priors[j]) / priors[j])));
+    }
+    if (int rc = check_int8_step(*params, l0max)) return rc;
     for (int32_t i = 0; i < C; ++i) {
         const int32_t deg = H->indptr[i + 1] - H->indptr[i];
         if (deg == 1)
@@ -766,7 +798,7 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
         thr[j] = t >= 4294967295.0 ? 0xffffffffu : (uint32_t)t;
     }
     for (int32_t i = 0; i < C; ++i) h->max_row_deg = std::max(h->max_row_deg, rptr[i + 1] - rptr[i]);
-    for (int32_t j = 0; j < V; ++j) h->l0max = std::max(h->l0max, L0d[j]);
+    h->l0max = l0max;
     DevDEM &g = h->dem;
     g.C = C; g.V = V; g.K = K; g.E = E;
     g.lg_rsp = lg_rsp;
@@ -791,6 +823,7 @@ int relaybp_set_params(relaybp_handle *h, const relaybp_params *params)
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
     if (int rc = check_params(params)) return rc;
     if (int rc = check_legs(params, h->dem.V)) return rc;
+    if (int rc = check_int8_step(*params, h->l0max)) return rc;
     h->params = *params;
     return 0;
 }
@@ -855,6 +888,7 @@ int relaybp_sample(relaybp_handle *h, uint64_t seed, uint64_t shot0, int64_t sho
 {
     g_err.clear();
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
     if (shots == 0) return 0;
     if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
@@ -885,6 +919,7 @@ int relaybp_decode_batch(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
 {
     g_err.clear();
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
     if (shots == 0) return 0;
     if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
@@ -900,6 +935,7 @@ int relaybp_decode_timed(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
 {
     g_err.clear();
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
     if (shots == 0) return 0;
     if (!d_syndromes || !d_times) return fail(RELAYBP_ERR_INVALID, "null pointer");
@@ -913,6 +949,7 @@ int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
 {
     g_err.clear();
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (shots < 0 || trace_iters < 0) return fail(RELAYBP_ERR_INVALID, "negative size");
     if (shots == 0) return 0;
     if (!d_syndromes || (trace_iters > 0 && !d_trace)) return fail(RELAYBP_ERR_INVALID, "null pointer");
@@ -926,6 +963,7 @@ int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t
 {
     g_err.clear();
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
     if (shots == 0) return 0;
     if (!h_syndromes) return fail(RELAYBP_ERR_INVALID, "h_syndromes is NULL");
@@ -962,6 +1000,7 @@ int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const 
 {
     g_err.clear();
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
     if (shots == 0) return 0;
     if (!d_stats || !d_counters || (h->dem.K > 0 && (!d_pred_obs || !d_true_obs)))
@@ -982,6 +1021,7 @@ int relaybp_autotune(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t sh
 {
     g_err.clear();
     if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
     if (shots < 1 || !d_syndromes) return fail(RELAYBP_ERR_INVALID, "need at least one syndrome");
     if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots) {
         ExactPlan ep = make_exact_plan(h->dem);
@@ -1063,6 +1103,7 @@ int relaybp_group_decode(relaybp_group *grp, const uint32_t *const *d_syndromes,
     if (!grp) return fail(RELAYBP_ERR_INVALID, "group is NULL");
     if (!d_syndromes || !shot0 || !shots) return fail(RELAYBP_ERR_INVALID, "null array");
     const int n = (int)grp->handles.size();
+    if (int rc = check_device(grp->handles[0])) return rc;
     std::vector<JobIO> io(n);
     for (int d = 0; d < n; ++d) {
         if (shots[d] < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count for DEM %d", d);
@@ -1181,6 +1222,7 @@ extern "C" int relaybp_decode_batch_noalloc(relaybp_handle *h, const uint32_t *d
     if (shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
     if (shots == 0) return 0;
     if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
+    if (int rc = check_device(h)) return rc;           // every call, not only the first on a device
     unsigned char *scratch = nullptr;
     if (int rc = noalloc_scratch(h->device, &scratch)) return rc;
     // a fixed scratch view of the static array: counter first, then the rows;

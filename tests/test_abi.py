@@ -136,3 +136,25 @@ def test_int8_scale_is_validated_before_any_device_work(dtype, scale, ok):
         assert rc == -1 and "int8_scale" in msg and out.value is None
     if rc == 0:
         R._lib.relaybp_destroy(out)
+
+
+@pytest.mark.parametrize("priors,scale,ok", [([0.5, 0.5, 0.5], 0.0, False), ([0.5, 0.5, 0.5], 0.25, True),
+                                             ([0.9, 0.95, 0.5], 0.0, True)])
+def test_int8_automatic_step_needs_a_nonzero_prior_llr(priors, scale, ok):
+    """The automatic int8 step is the largest |prior LLR| / 24: priors all 1/2
+    make it 0, which is rejected before any device work; an explicit step, or
+    priors above 1/2 (negative LLRs, counted by magnitude), are accepted."""
+    from paper_2607_27644_b300 import relaybp as R
+    cp = R.Params(msg_dtype="i8", int8_scale=scale).c()
+    H, keep = _csr(2, 3, [0, 2, 4], [0, 1, 1, 2])
+    pr = np.asarray(priors, dtype=np.float64)
+    out = ctypes.c_void_p()
+    rc = R._lib.relaybp_build(ctypes.byref(H), pr.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(cp),
+                              ctypes.byref(out))
+    msg = R.relaybp_last_error()
+    if ok:
+        assert rc == 0 or "automatic int8 step" not in msg
+    else:
+        assert rc == -1 and "automatic int8 step" in msg and out.value is None
+    if rc == 0:
+        R._lib.relaybp_destroy(out)
