@@ -245,14 +245,17 @@ int relaybp_count_failures(relaybp_handle *h, const uint32_t *d_pred_obs, const 
                            void *cuda_stream);
 
 /* Autotuner (launch shape only; no counterpart in the paper): times the
- * compressed decode kernel on d_syndromes for every valid row geometry (L
- * lanes per check row x NB positions per lane, L*NB >= the longest row) and
- * block size (256, 512 threads), and keeps the fastest in the handle for
- * later single-DEM decodes.  Synchronises the stream.  Results of a decode do
- * not depend on the launch shape (per-shot arithmetic is identical), only
- * its speed.  Outputs (each may be NULL): the chosen L, NB, threads and its
- * time in ms.  RELAYBP_ERR_UNSUPPORTED for DEMs decoded by the literal-order
- * FP64 kernel, which has no shape to tune. */
+ * decode kernel the handle uses on d_syndromes and keeps the fastest launch
+ * shape in the handle for later single-DEM decodes.  For the two-shot FP32
+ * kernel (relaybp_set_pair_kernel) that is the warps per block (16..32,
+ * L = 4 lanes per row, NB its row slots per lane); for the general kernel
+ * every valid row geometry (L lanes per check row x NB positions per lane,
+ * L*NB >= the longest row) and block size (256, 512 threads).  Synchronises
+ * the stream.  Results of a decode do not depend on the launch shape
+ * (per-shot arithmetic is identical), only its speed.  Outputs (each may be
+ * NULL): the chosen L, NB, threads and its time in ms.
+ * RELAYBP_ERR_UNSUPPORTED for DEMs decoded by the literal-order FP64 kernel,
+ * which has no shape to tune. */
 int relaybp_autotune(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots, int32_t *out_L,
                      int32_t *out_NB, int32_t *out_threads, float *out_ms, void *cuda_stream);
 
@@ -316,6 +319,20 @@ int64_t relaybp_launch_count(const relaybp_handle *h);
  * dividing by its event-timed duration gives the shared-memory bandwidth that
  * bounds the decode kernel.  d_sink: one float per block, device memory. */
 int relaybp_probe_smem_read(int32_t reps, float *d_sink, double *bytes_read, void *cuda_stream);
+
+/* Kernel choice for FP32 single-DEM decodes (no counterpart in the paper;
+ * results are identical either way, bit for bit).  By default a DEM whose
+ * rows have at most 108 entries and whose two-shot state fits in shared
+ * memory (ZSZ-LP-160 circuit DEMs: 217 KB) is decoded by the two-shot
+ * kernel: each thread block decodes two shots in lockstep, sharing every
+ * load of the DEM structure between them and adding their messages as packed
+ * FP32 pairs.  enable = 0 selects the general one-shot-per-block kernel
+ * (relaybp_autotune tunes whichever is selected); warps = warps per block of
+ * the two-shot kernel, 0 for the built-in choice.  Per-edge learned weights
+ * (relaybp_set_learned) and the other storage precisions always use the
+ * general kernel.  RELAYBP_ERR_UNSUPPORTED when enable = 1 and the DEM's
+ * rows are too long; RELAYBP_ERR_INVALID for warps outside 0..32. */
+int relaybp_set_pair_kernel(relaybp_handle *h, int32_t enable, int32_t warps);
 
 /* Free the handle and every device allocation it owns (synchronises its
  * device first).  NULL is accepted. */

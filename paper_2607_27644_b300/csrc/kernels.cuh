@@ -152,10 +152,19 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-// memory-biased prior (1 - g) L0 + g M
-template <typename C> __device__ __forceinline__ C memprior(C g, C l0, C m)
+// memory-biased prior (1 - g) L0 + g M: in FP64 two rounded products and a
+// rounded sum (the oracle's evaluation); in FP32 the product (1 - g) L0
+// rounded, then g M added to it in one fused multiply-add -- the form the
+// two-shot kernel's packed FP32 pairs evaluate (a packed multiply followed by
+// a packed add is always fused), so every FP32 kernel rounds alike.
+template <typename C> __device__ __forceinline__ C memprior(C g, C l0, C m);
+template <> __device__ __forceinline__ double memprior<double>(double g, double l0, double m)
 {
-    return add_rn(mul_rn(add_rn((C)1, -g), l0), mul_rn(g, m));
+    return add_rn(mul_rn(add_rn(1.0, -g), l0), mul_rn(g, m));
+}
+template <> __device__ __forceinline__ float memprior<float>(float g, float l0, float m)
+{
+    return __fmaf_rn(g, m, mul_rn(add_rn(1.f, -g), l0));
 }
 
 template <typename T> __device__ __forceinline__ T vmin(T a, T b) { return b < a ? b : a; }
@@ -172,15 +181,33 @@ template <> struct Num<double> {
 };
 
 // Memory strength of variable j in leg `leg` >= 1: the top 24 bits of Philox
-// stream 1 word (leg * 4 * ceil(V/4) + j), scaled to [0, 1) exactly.
+// stream 1 word (leg * 4 * ceil(V/4) + j), scaled to [0, 1) exactly, mapped
+// to gamma_min + (gamma_max - gamma_min) u with explicitly rounded FP64
+// operations (the FP64 value of the definition, never contracted into an
+// FMA) and rounded once to T: every kernel draws the same strengths.
 template <typename T>
 __device__ __forceinline__ T draw_gamma(const DecodeParamsDev &p, uint64_t shot, int leg, int j, int V)
 {
     const uint32_t nblk = (uint32_t)((V + 3) / 4);
     const uint4 r = philox_block(p.seed, shot, 1u, (uint32_t)leg * nblk + (uint32_t)(j >> 2));
     const uint32_t w = uint4_word(r, j & 3);
-    const T u = (T)(w >> 8) * (T)(1.0 / 16777216.0);
-    return (T)p.gamma_min + ((T)p.gamma_max - (T)p.gamma_min) * u;
+    const double u = __dmul_rn((double)(w >> 8), 1.0 / 16777216.0);
+    return (T)__dadd_rn(p.gamma_min, __dmul_rn(__dadd_rn(p.gamma_max, -p.gamma_min), u));
+}
+
+// Memory strength of variable j in leg `leg` from the learned inverse CDF of
+// K+1 knots at the same stream-1 draw u: knots[k] + (knots[k+1] - knots[k])
+// (uK - k), k = floor(uK), in explicitly rounded FP32 operations.
+__device__ __forceinline__ float knot_draw(const DecodeParamsDev &p, uint64_t shot, int leg, int j, int V)
+{
+    const uint32_t nblk = (uint32_t)((V + 3) / 4);
+    const uint4 rr = philox_block(p.seed, shot, 1u, (uint32_t)leg * nblk + (uint32_t)(j >> 2));
+    const float u = __fmul_rn((float)(uint4_word(rr, j & 3) >> 8), (float)(1.0 / 16777216.0));
+    const float x = __fmul_rn(u, (float)p.lK);
+    int kk = (int)floorf(x);
+    if (kk >= p.lK) kk = p.lK - 1;
+    const float lo = __ldg(p.lknots + kk), hi = __ldg(p.lknots + kk + 1);
+    return __fadd_rn(lo, __fmul_rn(__fadd_rn(hi, -lo), __fadd_rn(x, -(float)kk)));
 }
 
 // Byte offsets of one shot's state, A first (at 0) and the rest in falling
@@ -260,10 +287,26 @@ __device__ __forceinline__ double xsign(double v, uint32_t s)
 {
     return __hiloint2double(__double2hiint(v) ^ (int)s, __double2loint(v));
 }
-__device__ __forceinline__ float vmin2(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double vmin2(double a, double b) { return fmin(a, b); }
-__device__ __forceinline__ float vmax2(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double vmax2(double a, double b) { return fmax(a, b); }
+// Minimum and maximum that propagate NaN (any NaN operand gives NaN).  A
+// shot whose values overflow the arithmetic's range meets inf - inf = NaN in
+// mu; with NaN-ignoring min/max the row minima would then depend on the
+// order the slots are reduced in (the launch shape).  Propagating it makes
+// the overflowed shot's state NaN in every kernel and shape alike: it never
+// converges and is reported as a nonconvergence.
+__device__ __forceinline__ float vmin2(float a, float b)
+{
+    float r;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float vmax2(float a, float b)
+{
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ double vmin2(double a, double b) { return (a != a || b != b) ? a + b : fmin(a, b); }
+__device__ __forceinline__ double vmax2(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
 __device__ __forceinline__ float vabs2(float a) { return fabsf(a); }
 __device__ __forceinline__ double vabs2(double a) { return fabs(a); }
 
@@ -370,8 +413,9 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
             const C o1 = __shfl_xor_sync(FULL, b1, off);
             const C o2 = __shfl_xor_sync(FULL, b2, off);
             const int oi = __shfl_xor_sync(FULL, bi, off);
-            if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin(b1, o2); b1 = o1; bi = oi; }
-            else { b2 = vmin(b2, o1); }
+            if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin2(b1, o2); b1 = o1; bi = oi; }
+            else { b2 = vmin2(b2, o1); }
+            b1 = vmin2(b1, o1);                 // NaN from either side reaches every lane
         }
         uint32_t X = 0u;
 #pragma unroll
@@ -540,14 +584,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     const C l0 = Num<C>::l0(g, j);
                     C gn;
                     if (lleg && p.lknots) {
-                        const uint32_t nblk = (uint32_t)((V + 3) / 4);
-                        const uint4 rr = philox_block(p.seed, shot, 1u, (uint32_t)leg * nblk + (uint32_t)(j >> 2));
-                        const C u = (C)(uint4_word(rr, j & 3) >> 8) * (C)(1.0 / 16777216.0);
-                        const C x = u * (C)p.lK;
-                        int kk = (int)floor((double)x);
-                        if (kk >= p.lK) kk = p.lK - 1;
-                        const C lo = (C)__ldg(p.lknots + kk), hi = (C)__ldg(p.lknots + kk + 1);
-                        gn = lo + (hi - lo) * (x - (C)kk);
+                        gn = (C)knot_draw(p, shot, leg, j, V);
                     } else {
                         gn = draw_gamma<C>(p, shot, leg, j, V);
                     }

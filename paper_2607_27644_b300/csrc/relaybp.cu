@@ -19,6 +19,7 @@
 #include "../../include/relaybp.h"
 #include "kernels.cuh"
 #include "learned.cuh"
+#include "pair.cuh"
 
 using namespace relaybp;
 
@@ -82,6 +83,11 @@ struct relaybp_handle {
     double l0max = 0.0;             // largest |prior LLR| (automatic int8 scale)
     // learned-form training scratch: work counter and one gradient row per block
     int tuned_L = 0, tuned_NB = 0, tuned_threads = 0; // autotuned launch shape (0: heuristic)
+    // two-shot lockstep kernel (FP32): row slots and column codes, or NULL
+    const uint32_t *rslot2 = nullptr, *ecode2 = nullptr;
+    int pair_nb = 0;                                  // row slots per lane (template NB)
+    int pair_warps = 0;                               // warps per block (0: heuristic)
+    int pair_off = 1;                                 // 1: never use it (relaybp_set_kernel)
     const float *lw = nullptr, *lknots = nullptr;     // learned inference parameters (caller-owned)
     const float *lwrow = nullptr;                     // row-tied learned weights [lT][C]
     int lT = 0, lK = 0;
@@ -473,12 +479,134 @@ int launch_jobs_dtype(relaybp_handle *const *hs, const JobIO *io, int n, Scratch
     }
 }
 
-// Single-DEM decode: the literal-order FP64 kernel when it applies, else one job.
+// ---- two-shot lockstep kernel (FP32) -----------------------------------------
+// Row slots per lane of the instantiated kernels; a DEM uses the smallest that
+// covers its longest row (4 lanes per row).
+constexpr int kPairNB[] = {4, 8, 12, 16, 23, 27};
+
+PairPlan make_pair_plan(const DevDEM &g)
+{
+    PairPlan s{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        size_t at = off;
+        off += bytes;
+        return (int)at;
+    };
+    s.ehat = take(2 * 4 * (size_t)words(g.V));
+    s.best = take(2 * 4 * (size_t)words(g.V));
+    s.res = take(2 * 4 * (size_t)words(g.C));
+    s.syn = take(2 * 4 * (size_t)words(g.C));
+    s.obsacc = take(2 * 4 * (size_t)std::max(1, words(g.K)));
+    // MM at X, SG at 2X (X >= the minima's size, a multiple of 16)
+    const size_t X = (std::max(off, (size_t)(g.C + 1) * 16) + 15) & ~size_t(15);
+    s.MM = (int)X;
+    s.SG = (int)(2 * X);
+    off = 2 * X + (size_t)(g.C + 1) * 32;
+    s.A2 = take(8 * ((size_t)g.V + 1));
+    s.M2 = take(8 * (size_t)g.V);
+    s.total = (int)((off + 15) & ~size_t(15));
+    return s;
+}
+
+// Warps per block: the count in [16, the kernel's limit] with the least work
+// on the busiest warp (row steps of 8 rows at NB slot pairs, column groups at
+// their slots).
+int pair_warps_heuristic(const relaybp_handle *h)
+{
+    const int steps = (h->dem.C + 7) / 8, groups = words(h->dem.V);
+    const double grp_cost = 30.0 + 15.0 * (double)h->dem.E / std::max(1, h->dem.V);
+    const int wmax = pair_max_threads(h->pair_nb) / 32;
+    int best = wmax;
+    double bw = 1e300;
+    for (int w = wmax; w >= 16; --w) {
+        const double work = ((steps + w - 1) / w) * 22.0 * h->pair_nb + ((groups + w - 1) / w) * grp_cost;
+        if (work < bw * 0.999) { bw = work; best = w; }
+    }
+    return best;
+}
+
+// The pair kernel decodes single-DEM FP32 launches without per-edge learned
+// weights whose two-shot state fits in shared memory; returns 1 otherwise.
+template <int NB>
+int launch_pair_nb(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, int dyn)
+{
+    const DevDEM &g = h->dem;
+    PairJob J{};
+    J.g = g;
+    J.p = dev_params(h->params);
+    J.p.lknots = h->lknots;
+    J.p.lK = h->lK;
+    J.p.lwrow = h->lwrow;
+    J.p.lT = h->lT;
+    J.p.llegs = h->llegs;
+    J.plan = make_pair_plan(g);
+    J.rslot2 = h->rslot2;
+    J.ecode2 = h->ecode2;
+    J.syn_in = io.syn;
+    J.shot0 = io.shot0;
+    J.shots = io.shots;
+    J.corr_out = io.corr;
+    J.pobs_out = io.pobs;
+    J.stats_out = io.stats;
+    J.trace = io.trace;
+    J.trace_iters = io.trace_iters;
+    J.times_out = io.times;
+    const int warps = std::min(h->pair_warps > 0 ? h->pair_warps : pair_warps_heuristic(h),
+                               pair_max_threads(NB) / 32);
+    const int threads = 32 * warps;
+    auto kern = io.trace ? relay_pair_kernel<NB, true> : relay_pair_kernel<NB, false>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
+    if (per_sm < 1) return 1;
+    const int64_t blocks = std::min<int64_t>((int64_t)per_sm * h->num_sms, (io.shots + 1) / 2);
+    const size_t gamma_need = (size_t)blocks * g.V * sizeof(float2);
+    if (int rc = scratch_reserve(sc, gamma_need, 0)) return rc;
+    CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
+    if (io.trace)
+        relay_pair_kernel<NB, true><<<(unsigned)blocks, threads, dyn, st>>>(J, sc.work,
+                                                                           static_cast<float2 *>(sc.gamma));
+    else
+        relay_pair_kernel<NB, false><<<(unsigned)blocks, threads, dyn, st>>>(J, sc.work,
+                                                                            static_cast<float2 *>(sc.gamma));
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_pair(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st)
+{
+    if (h->pair_off || !h->rslot2 || h->params.msg_dtype != RELAYBP_MSG_F32 || h->lw) return 1;
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const PairPlan pl = make_pair_plan(h->dem);
+    if (pl.total + 1024 > maxsm) return 1;
+    switch (h->pair_nb) {
+    case 4: return launch_pair_nb<4>(h, sc, io, st, pl.total);
+    case 8: return launch_pair_nb<8>(h, sc, io, st, pl.total);
+    case 12: return launch_pair_nb<12>(h, sc, io, st, pl.total);
+    case 16: return launch_pair_nb<16>(h, sc, io, st, pl.total);
+    case 23: return launch_pair_nb<23>(h, sc, io, st, pl.total);
+    case 27: return launch_pair_nb<27>(h, sc, io, st, pl.total);
+    default: return 1;
+    }
+}
+
+// Single-DEM decode: the literal-order FP64 kernel when it applies, the
+// two-shot FP32 kernel when it applies, else one job of the general kernel.
 int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, bool on_chip_only)
 {
     if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots && !h->lwrow && !io.times) {
         int rc = launch_decode_exact(h, sc, io, st);
         if (rc <= 0) return rc;
+    }
+    {
+        int rc = launch_pair(h, sc, io, st);
+        if (rc <= 0) {
+            if (rc == 0) h->launches += 1;
+            return rc;
+        }
     }
     int rc = launch_jobs_dtype(&h, &io, 1, sc, st, on_chip_only);
     if (rc == 0) h->launches += 1;
@@ -773,6 +901,36 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
             }
         }
     }
+    // two-shot kernel: row slots (lane k % 4, slot k / 4 of row entry k) as
+    // shared byte offsets of A2[j], and column codes (sign-word offset << 5 |
+    // 32 - NB + slot); rows padded with the dummy variable V, columns with the
+    // dummy row C
+    int32_t pair_nb = 0;
+    for (int nb : kPairNB)
+        if (4 * nb >= maxdeg) { pair_nb = nb; break; }
+    std::vector<uint32_t> rslot2, ecode2;
+    if (pair_nb > 0) {
+        DevDEM tmp{};
+        tmp.C = C; tmp.V = V; tmp.K = K; tmp.E = E;
+        const PairPlan pl = make_pair_plan(tmp);
+        const int32_t nbp = (pair_nb + 3) & ~3, CP8 = (C + 7) / 8 * 8;
+        rslot2.assign((size_t)CP8 * kPairLanes * nbp, (uint32_t)pl.A2 + 8u * (uint32_t)V);
+        for (int32_t i = 0; i < C; ++i)
+            for (int32_t k = 0; k < rptr[i + 1] - rptr[i]; ++k)
+                rslot2[((size_t)i * kPairLanes + k % kPairLanes) * nbp + k / kPairLanes] =
+                    (uint32_t)pl.A2 + 8u * (uint32_t)rvar[rptr[i] + k];
+        const uint32_t dummy = ((uint32_t)pl.SG + 32u * (uint32_t)C) << 5;
+        ecode2.assign((size_t)goff[NG] + 8 * 32, dummy);   // + a group's worth: prefetches stay in bounds
+        for (int32_t j = 0; j < V; ++j) {
+            const int32_t G = j / 32, l = j % 32;
+            for (int32_t k = 0; k < cptr[j + 1] - cptr[j]; ++k) {
+                const int32_t i = cchk[cptr[j] + k];
+                const int32_t pos = cedge[cptr[j] + k] - rptr[i];
+                const uint32_t sg = (uint32_t)pl.SG + 32u * (uint32_t)i + 8u * (uint32_t)(pos % kPairLanes);
+                ecode2[(size_t)goff[G] + (size_t)k * 32 + l] = (sg << 5) | (uint32_t)(32 - pair_nb + pos / kPairLanes);
+            }
+        }
+    }
     // observables per column
     std::vector<int32_t> optr(V + 1, 0), oidx;
     if (obs) {
@@ -812,6 +970,11 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
         (rc = upload(h, optr, &g.optr)) || (rc = upload(h, oidx, &g.oidx)) || (rc = upload(h, L0d, &g.L0d)) ||
         (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
         return bail(rc);
+    if (pair_nb > 0) {
+        if ((rc = upload(h, rslot2, &h->rslot2)) || (rc = upload(h, ecode2, &h->ecode2))) return bail(rc);
+        h->pair_nb = pair_nb;
+        h->pair_off = 0;
+    }
     if ((rc = scratch_reserve(h->scratch, 0, 0))) return bail(rc);
     *out = h;
     return 0;
@@ -861,6 +1024,19 @@ int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, 
     h->lT = d_wrow ? T : 0;
     h->lknots = d_knots;
     h->lK = d_knots ? K : 0;
+    return 0;
+}
+
+int relaybp_set_pair_kernel(relaybp_handle *h, int32_t enable, int32_t warps)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (warps != 0 && (warps < 1 || warps > 32)) return fail(RELAYBP_ERR_INVALID, "warps must be 0 or 1..32");
+    if (enable && !h->rslot2)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "rows of %d entries exceed the two-shot kernel's %d", h->max_row_deg,
+                    kPairLanes * kPairNB[sizeof(kPairNB) / sizeof(kPairNB[0]) - 1]);
+    h->pair_off = enable ? 0 : 1;
+    h->pair_warps = warps;
     return 0;
 }
 
@@ -1035,6 +1211,40 @@ int relaybp_autotune(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t sh
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
+    if (!h->pair_off && h->rslot2 && h->params.msg_dtype == RELAYBP_MSG_F32 && !h->lw) {
+        // the two-shot kernel: warps per block
+        const int sw = h->pair_warps;
+        const JobIO io{d_syndromes, shot0, shots, nullptr, nullptr, nullptr, nullptr, 0};
+        float best = 0.f;
+        int bw = 0;
+        for (int w = 16; w <= pair_max_threads(h->pair_nb) / 32; w += 2) {
+            h->pair_warps = w;
+            int rc = launch_pair(h, h->scratch, io, st);
+            if (rc == 0) {
+                cudaEventRecord(e0, st);
+                rc = launch_pair(h, h->scratch, io, st);
+                cudaEventRecord(e1, st);
+            }
+            if (rc != 0) continue;
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (bw == 0 || ms < best) { best = ms; bw = w; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (bw == 0) {
+            h->pair_warps = sw;
+            return fail(RELAYBP_ERR_UNSUPPORTED, "no launch shape ran");
+        }
+        h->pair_warps = bw;
+        g_err.clear();
+        if (out_L) *out_L = kPairLanes;
+        if (out_NB) *out_NB = h->pair_nb;
+        if (out_threads) *out_threads = 32 * bw;
+        if (out_ms) *out_ms = best;
+        return 0;
+    }
     const int sL = h->tuned_L, sNB = h->tuned_NB, sT = h->tuned_threads;
     float best = 0.f;
     int bL = 0, bNB = 0, bT = 0;

@@ -55,6 +55,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_set_learned": ([P, P, I32, P, I32], ctypes.c_int),
         "relaybp_set_learned_rows": ([P, P, I32, P, I32], ctypes.c_int),
         "relaybp_set_learned_legs": ([P, I32], ctypes.c_int),
+        "relaybp_set_pair_kernel": ([P, I32, I32], ctypes.c_int),
         "relaybp_sizes": ([P, P, P, P, P], ctypes.c_int),
         "relaybp_sample": ([P, U64, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_batch": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
@@ -87,7 +88,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows",
-            "relaybp_set_learned_legs", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
+            "relaybp_set_learned_legs", "relaybp_set_pair_kernel", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
@@ -223,6 +224,13 @@ def relaybp_set_learned_rows(h: Handle, d_wrow=None, d_knots=None):
 
 def relaybp_set_learned_legs(h: Handle, legs: int):
     _check(_lib.relaybp_set_learned_legs(h.ptr, legs), "relaybp_set_learned_legs")
+
+
+def relaybp_set_pair_kernel(h: Handle, enable: bool, warps: int = 0):
+    """Select the two-shot FP32 kernel (default where it applies) or the
+    general one-shot-per-block kernel; warps per block of the former (0: the
+    library's choice)."""
+    _check(_lib.relaybp_set_pair_kernel(h.ptr, int(bool(enable)), warps), "relaybp_set_pair_kernel")
 
 
 def relaybp_sample(h: Handle, seed: int, shot0: int, shots: int, d_syndromes, d_obs=None, d_errors=None,

@@ -87,6 +87,15 @@ def test_autotune_keeps_results():
     syn = torch.zeros((2000, h.wc), dtype=torch.int32, device="cuda")
     R.relaybp_sample(h, 8, 0, 2000, syn)
     before = _single(R, h, syn, 0)
+    # the two-shot kernel (default for this DEM): warps per block
+    shape = R.relaybp_autotune(h, syn, 0, 2000)
+    assert shape["L"] == 4 and shape["L"] * shape["NB"] >= 92 and 512 <= shape["threads"] <= 640
+    assert shape["ms"] > 0
+    after = _single(R, h, syn, 0)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    # the general kernel: row geometry and block size
+    R.relaybp_set_pair_kernel(h, False)
     shape = R.relaybp_autotune(h, syn, 0, 2000)
     assert shape["L"] * shape["NB"] >= 92 and shape["threads"] in (256, 512) and shape["ms"] > 0
     after = _single(R, h, syn, 0)
