@@ -50,7 +50,10 @@ struct PairJob {
     DecodeParamsDev p;
     PairPlan plan;
     const uint32_t *rslot2;     // [round_up(C, 8)][4][NBP]: shared byte offset of A2[j] per row slot
-    const uint32_t *ecode2;     // sliced ELL (g.goff / g.gdeg): column entry codes, padded with row C's
+    const uint32_t *ecode2;     // sliced ELL (goff2 / g.gdeg): column entry codes, padded with row C's;
+                                // every group holds max(gdeg, 8) slots
+    const int32_t *goff2;       // [ceil(V/32)] offset of each group's slots in ecode2
+    const float *L0p;           // [ceil(V/32) * 32] prior LLRs in FP32, padded with 0
     const uint32_t *syn_in;     // [shots][ceil(C/32)]
     uint64_t shot0;
     int64_t shots;
@@ -80,13 +83,25 @@ __device__ __forceinline__ void pair_row_pass(const PairJob &J, unsigned char *s
     const int r = lane >> 2, l = lane & 3;
     const int Cn = J.g.C;
     const float INF = __int_as_float(0x7f800000);
+    constexpr int NQ = NBP / 4;                 // 16-byte vectors of row slots per lane and step
+    // Row slots stream two vectors ahead of their use: vector q + 2 of a step
+    // loads when vector q starts, and the last two vectors of a step load the
+    // next step's first two, so the L2 latency overlaps the slot arithmetic
+    // with only a few vectors in registers.
+    auto slots = [&](int i) {
+        return reinterpret_cast<const uint4 *>(J.rslot2 + ((size_t)i * kPairLanes + l) * NBP);
+    };
+    uint4 ix[NQ];
+    if (warp * P < Cn) {
+        ix[0] = __ldg(slots(warp * P + r));
+        if constexpr (NQ > 1) ix[1] = __ldg(slots(warp * P + r) + 1);
+    }
     for (int base = warp * P; base < Cn; base += nwarp * P) {
         const int i = base + r;                 // rslot2 covers round_up(C, 8) rows
         const int il = min(i, Cn);              // rows past the end read the empty dummy row C
-        const uint4 *rs = reinterpret_cast<const uint4 *>(J.rslot2 + ((size_t)i * kPairLanes + l) * NBP);
-        uint4 ix[NBP / 4];
-#pragma unroll
-        for (int q = 0; q < NBP / 4; ++q) ix[q] = __ldg(rs + q);
+        const bool more = base + nwarp * P < Cn;
+        const uint4 *rs = slots(i);
+        const uint4 *rsn = slots(more ? i + nwarp * P : i);
         unsigned char *mrow = smem + J.plan.MM + 16 * il;
         unsigned char *srow = smem + J.plan.SG + 32 * il + 8 * l;
         const float4 mm = *reinterpret_cast<const float4 *>(mrow);
@@ -97,6 +112,11 @@ __device__ __forceinline__ void pair_row_pass(const PairJob &J, unsigned char *s
         uint32_t n0 = 0u, n1 = 0u;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
+            if ((b & 3) == 0) {
+                const int qn = (b >> 2) + 2;
+                if (qn < NQ) ix[qn] = __ldg(rs + qn);
+                else if (NQ > 2 && more && qn - NQ < 2) ix[qn - NQ] = __ldg(rsn + (qn - NQ));
+            }
             const uint32_t off = uint4_word(ix[b >> 2], b & 3);
             const float2 a = *reinterpret_cast<const float2 *>(smem + off);
             constexpr uint32_t K0 = 32 - NB;
@@ -115,6 +135,10 @@ __device__ __forceinline__ void pair_row_pass(const PairJob &J, unsigned char *s
             b21 = vmin2(b21, vmax2(b11, a1));
             s1 = (a1 < b11) ? b : s1;
             b11 = vmin2(b11, a1);
+        }
+        if (NQ <= 2 && more) {                  // short rows: the next step's vectors now
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) ix[q] = __ldg(rsn + q);
         }
         // row minima over the 4 lanes; ties go to the lower position, NaN
         // (an overflowed shot) reaches every lane
@@ -207,7 +231,7 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
     auto res = [&](int s) { return reinterpret_cast<uint32_t *>(smem + J.plan.res) + s * WC; };
     auto syn = [&](int s) { return reinterpret_cast<uint32_t *>(smem + J.plan.syn) + s * WC; };
     auto obsacc = [&](int s) { return reinterpret_cast<uint32_t *>(smem + J.plan.obsacc) + s * WKa; };
-    float2 *gam = gamma_scratch + (size_t)blockIdx.x * V;
+    float2 *gam = gamma_scratch + (size_t)blockIdx.x * (NG * 32);    // rows padded to whole groups
 
     // the dummy row C and the dummy variable V (never rewritten)
     if (tid < 4) reinterpret_cast<uint32_t *>(smem + J.plan.MM + 16 * Cn)[tid] = 0u;
@@ -286,36 +310,33 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
         // group the next group's first eight column codes and the shape of the
         // group after it start loading, with this group's prior and strengths,
         // so the L2 latency of the DEM structure overlaps this group's work.
-        auto codes8 = [&](uint32_t (&c)[8], int D, int off) {
+        auto codes8 = [&](uint32_t (&c)[8], int off) {     // every group holds >= 8 slots
+            const uint32_t *p8 = J.ecode2 + off + lane;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) c[u] = (u < D) ? __ldg(J.ecode2 + off + lane + u * 32) : 0u;
+            for (int u = 0; u < 8; ++u) c[u] = __ldg(p8 + u * 32);
         };
         int G = warp, D = 0, off = 0, D1 = 0, off1 = 0;
         uint32_t c[8];
         if (G < NG) {
             D = __ldg(J.g.gdeg + G);
-            off = __ldg(J.g.goff + G);
-            codes8(c, D, off);
+            off = __ldg(J.goff2 + G);
+            codes8(c, off);
         }
         if (G + nwarp < NG) {
             D1 = __ldg(J.g.gdeg + G + nwarp);
-            off1 = __ldg(J.g.goff + G + nwarp);
+            off1 = __ldg(J.goff2 + G + nwarp);
         }
         for (; G < NG; G += nwarp) {
             const int j = G * 32 + lane;
             uint32_t cn[8];
-            codes8(cn, D1, off1);               // D1 = 0 past the last group: no loads
+            codes8(cn, off1);                   // past the last group: the padding group at offset 0
             int D2 = 0, off2 = 0;
             if (G + 2 * nwarp < NG) {
                 D2 = __ldg(J.g.gdeg + G + 2 * nwarp);
-                off2 = __ldg(J.g.goff + G + 2 * nwarp);
+                off2 = __ldg(J.goff2 + G + 2 * nwarp);
             }
-            float l0 = 0.f;
-            float2 gm = make_float2(0.f, 0.f);
-            if (j < V) {
-                l0 = __ldg(J.g.L0f + j);
-                gm = gam[j];
-            }
+            const float l0 = __ldg(J.L0p + j);  // both padded to whole groups
+            const float2 gm = gam[j];
             const uint32_t *col = J.ecode2 + off + lane;
             float2 S = make_float2(0.f, 0.f);
             if (D >= 4) {

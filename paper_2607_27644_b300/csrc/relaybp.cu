@@ -85,6 +85,8 @@ struct relaybp_handle {
     int tuned_L = 0, tuned_NB = 0, tuned_threads = 0; // autotuned launch shape (0: heuristic)
     // two-shot lockstep kernel (FP32): row slots and column codes, or NULL
     const uint32_t *rslot2 = nullptr, *ecode2 = nullptr;
+    const int32_t *goff2 = nullptr;                   // group offsets of ecode2 (>= 8 slots per group)
+    const float *L0p = nullptr;                       // FP32 priors padded to whole groups
     int pair_nb = 0;                                  // row slots per lane (template NB)
     int pair_warps = 0;                               // warps per block (0: heuristic)
     int pair_off = 1;                                 // 1: never use it (relaybp_set_kernel)
@@ -544,6 +546,8 @@ int launch_pair_nb(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     J.plan = make_pair_plan(g);
     J.rslot2 = h->rslot2;
     J.ecode2 = h->ecode2;
+    J.goff2 = h->goff2;
+    J.L0p = h->L0p;
     J.syn_in = io.syn;
     J.shot0 = io.shot0;
     J.shots = io.shots;
@@ -562,7 +566,7 @@ int launch_pair_nb(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
     if (per_sm < 1) return 1;
     const int64_t blocks = std::min<int64_t>((int64_t)per_sm * h->num_sms, (io.shots + 1) / 2);
-    const size_t gamma_need = (size_t)blocks * g.V * sizeof(float2);
+    const size_t gamma_need = (size_t)blocks * words(g.V) * 32 * sizeof(float2);
     if (int rc = scratch_reserve(sc, gamma_need, 0)) return rc;
     CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
     if (io.trace)
@@ -909,6 +913,8 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
     for (int nb : kPairNB)
         if (4 * nb >= maxdeg) { pair_nb = nb; break; }
     std::vector<uint32_t> rslot2, ecode2;
+    std::vector<int32_t> goff2;
+    std::vector<float> L0p;
     if (pair_nb > 0) {
         DevDEM tmp{};
         tmp.C = C; tmp.V = V; tmp.K = K; tmp.E = E;
@@ -920,14 +926,18 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
                 rslot2[((size_t)i * kPairLanes + k % kPairLanes) * nbp + k / kPairLanes] =
                     (uint32_t)pl.A2 + 8u * (uint32_t)rvar[rptr[i] + k];
         const uint32_t dummy = ((uint32_t)pl.SG + 32u * (uint32_t)C) << 5;
-        ecode2.assign((size_t)goff[NG] + 8 * 32, dummy);   // + a group's worth: prefetches stay in bounds
+        goff2.assign(NG + 1, 0);
+        for (int32_t G = 0; G < NG; ++G) goff2[G + 1] = goff2[G] + std::max(gdeg[G], 8) * 32;
+        ecode2.assign((size_t)goff2[NG], dummy);
+        L0p.assign((size_t)NG * 32, 0.f);
+        for (int32_t j = 0; j < V; ++j) L0p[j] = (float)std::log((1.0 - priors[j]) / priors[j]);
         for (int32_t j = 0; j < V; ++j) {
             const int32_t G = j / 32, l = j % 32;
             for (int32_t k = 0; k < cptr[j + 1] - cptr[j]; ++k) {
                 const int32_t i = cchk[cptr[j] + k];
                 const int32_t pos = cedge[cptr[j] + k] - rptr[i];
                 const uint32_t sg = (uint32_t)pl.SG + 32u * (uint32_t)i + 8u * (uint32_t)(pos % kPairLanes);
-                ecode2[(size_t)goff[G] + (size_t)k * 32 + l] = (sg << 5) | (uint32_t)(32 - pair_nb + pos / kPairLanes);
+                ecode2[(size_t)goff2[G] + (size_t)k * 32 + l] = (sg << 5) | (uint32_t)(32 - pair_nb + pos / kPairLanes);
             }
         }
     }
@@ -971,7 +981,9 @@ int relaybp_build(const relaybp_csr *H, const double *priors, const relaybp_csr 
         (rc = upload(h, L0f, &g.L0f)) || (rc = upload(h, thr, &g.thr)))
         return bail(rc);
     if (pair_nb > 0) {
-        if ((rc = upload(h, rslot2, &h->rslot2)) || (rc = upload(h, ecode2, &h->ecode2))) return bail(rc);
+        if ((rc = upload(h, rslot2, &h->rslot2)) || (rc = upload(h, ecode2, &h->ecode2)) ||
+            (rc = upload(h, goff2, &h->goff2)) || (rc = upload(h, L0p, &h->L0p)))
+            return bail(rc);
         h->pair_nb = pair_nb;
         h->pair_off = 0;
     }
