@@ -57,6 +57,13 @@ def _args():
     ap.add_argument("--stream-batch", type=int, default=1 << 16, help="stream550: shots per graph batch")
     ap.add_argument("--train-steps", type=int, default=300, help="learned: Adam steps of 512 shots at p=0.2%%")
     ap.add_argument("--learned-msg", default="bf16", choices=["bf16", "f16", "f32"], help="learned: message storage")
+    ap.add_argument("--objective", type=int, default=1, choices=[0, 1],
+                    help="learned: training loss, 0 cross-entropy against the sampled error, 1 soft syndrome")
+    ap.add_argument("--train-T", type=int, default=10, help="learned: unrolled iterations of training")
+    ap.add_argument("--train-lr", type=float, default=3e-3, help="learned: Adam learning rate")
+    ap.add_argument("--no-learned", action="store_true", help="default workload: skip the learned and ablation arms")
+    ap.add_argument("--learned-train-steps", type=int, default=300,
+                    help="default workload: Adam steps of 512 shots training the learned arm")
     ap.add_argument("--mixed-base", type=int, default=2000, help="mixed: shots per unit of the 2:5:10 mix")
     ap.add_argument("--msg", default=None, choices=["f16", "bf16", "f32", "i8"],
                     help="message storage (default: f32 for zsz160, f16 for mixed)")
@@ -320,6 +327,81 @@ def run_ours(a):
                "sync_call_shots_per_s": B / sync_s,
                "sync_call": "relaybp_decode_host, one step, synchronous (copies and decode in one call)"}
 
+    # ---- the metric's learned side: learned vs plain at equal LER ----------
+    # Row-tied weights and knots trained here (soft-syndrome objective, p =
+    # 0.2%, untimed), then the same K steps of fresh shots as the plain arm
+    # decoded by (i) the learned decoder -- learned legs 0..49 with plain legs
+    # after in the same launch, stop after the first solution -- and (ii) the
+    # ablation, plain Relay-BP with the same stop-after-first rule: learned vs
+    # ablation is what the trained parameters gain, learned vs plain also
+    # counts the stopping rule.  FP32, two-shot kernel, same streams.
+    learned = None
+    if not a.no_learned and world == 1:
+        from paper_2607_27644_b300.stats import agree_within
+        from workloads.dem import circuit_dems
+        d_train = circuit_dems(WORKLOAD["code"], [0.002], WORKLOAD["rounds"], WORKLOAD["basis"])[0]
+        wrow, knots, info = train_learned(a, dev, dem, d_train, a.learned_train_steps)
+        arm = {}
+        for kind in ("learned", "ablation"):
+            hk = []
+            for q in range(NS):
+                x = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1)))
+                if kind == "learned":
+                    R.relaybp_set_learned_rows(x, wrow, knots)
+                    R.relaybp_set_learned_legs(x, 50)
+                hk.append(x)
+            cnt_k = torch.zeros(4, dtype=torch.int64, device=dev)
+            it_k = torch.zeros(1, dtype=torch.int64, device=dev)
+
+            def astep(k):
+                q = k % NS
+                s_, b_, h_ = streams[q], bufs[q], hk[q]
+                shot0, _ = shot_range(rank, world, K + W, B, k)
+                with torch.cuda.stream(s_):
+                    flush.fill_(k)
+                    R.relaybp_sample(h_, SAMPLE_SEED, shot0, B, b_["syn"], b_["obs"], None, s_)
+                    R.relaybp_decode_batch(h_, b_["syn"], shot0, B, None, b_["pobs"], b_["stats"], s_)
+                    R.relaybp_count_failures(h_, b_["pobs"], b_["obs"], b_["stats"], B, cnt_k, s_)
+                    it_k.add_(b_["stats"][:, 3].sum())
+
+            for w_ in range(W):
+                astep(K + w_)
+            torch.cuda.synchronize()
+            cnt_k.zero_()
+            it_k.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with ClockSampler(local) as clk_k:
+                e0.record(streams[0])
+                for s_ in streams[1:]:
+                    s_.wait_stream(streams[0])
+                for k in range(K):
+                    astep(k)
+                join()
+                e1.record(streams[0])
+                torch.cuda.synchronize()
+            ms_k = e0.elapsed_time(e1)
+            ck = cnt_k.cpu().tolist()
+            arm[kind] = {"value": B * K / (ms_k / 1e3), "unit": "shots/s", "shots": ck[0], "failures": ck[3],
+                         "nonconverged": ck[1], "logical": ck[2], "block_ler": ck[3] / max(1, ck[0]),
+                         "mean_iterations": float(it_k.item()) / (B * K), "clocks": clk_k.summary()}
+            for x in hk:
+                R.relaybp_destroy(x)
+        cp = cnt.cpu().tolist()
+        lv, ab = arm["learned"], arm["ablation"]
+        learned = dict(lv)
+        learned.update({
+            "decoder": "FP32; learned row-tied weights (first T iterations of a leg, unit after) and memory-strength "
+                       "knots in legs 0-49, plain legs after in the same launch; stop after the first solution",
+            "ablation": ab, "train": info,
+            "speedup_vs_plain": lv["value"] / value, "speedup_vs_ablation": lv["value"] / ab["value"],
+            "mean_iterations_vs_ablation": lv["mean_iterations"] / ab["mean_iterations"],
+            "equal_ler_2sigma_vs_plain": bool(agree_within(lv["failures"], lv["shots"], cp[3], cp[0])),
+            "equal_ler_2sigma_vs_ablation": bool(agree_within(lv["failures"], lv["shots"], ab["failures"],
+                                                              ab["shots"])),
+            "note": "same shots as the plain arm; speedup_vs_plain mostly measures the stopping rule (first solution "
+                    "vs five), speedup_vs_ablation and mean_iterations_vs_ablation what the trained parameters "
+                    "gain at the same rule"})
+
     # ---- roofline of the dominant kernel (relay_decode_kernel) --------------
     sink = torch.zeros(4096, dtype=torch.float32, device=dev)
     with torch.cuda.stream(st):
@@ -344,13 +426,15 @@ def run_ours(a):
     achieved = iters_rank * bytes_per_iter / wall_s / 1e9
     edge_updates = iters_rank * E / wall_s
     hbm_gbs = _measured_peaks().get("hbm_gbs")
-    # DRAM bytes of one 3,000-shot decode launch (ncu, same kernel build), scaled
-    # by shots to one launch of this run: the state stays on chip, DRAM carries
-    # syndromes in and results out
-    traffic = 1.132544e6 * B / 3000 if (msg == "f32" and B >= 3000) else None
+    # DRAM bytes (read + write) of one 3,000-shot decode launch of the two-shot
+    # kernel (ncu, same kernel build), scaled by shots to one launch of this
+    # run: the state stays on chip; DRAM carries syndromes in, results out and
+    # the L2 write-backs of the per-block memory-strength rows
+    traffic = (2633216 + 2473216) * B / 3000 if (msg == "f32" and B >= 3000) else None
     roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
             "traffic": traffic,
-            "kernel": f"relay_decode_kernel<{msg}>",
+            "kernel": ("relay_pair_kernel<23> (two shots per block, FP32)" if msg == "f32"
+                       else f"relay_decode_kernel<{msg}>"),
             "algorithmic_bytes": f"per shot-iteration 4*b_m*E + 16*V + (V+C)/8 (b_m={b_m})",
             "peak_source": "measured live: conflict-free 16-B shared-memory loads on all SMs (relaybp_probe_smem_read)",
             "achieved_basis": f"algorithmic bytes of all decode launches / the timed region ({NS} launches in flight "
@@ -368,7 +452,8 @@ def run_ours(a):
             "config": _config(dem, B, K, world, streams=NS), "clocks": clk.summary(), "gpu_launches": launches * world,
             "roofline": roof, "e2e": e2e,
             "ler": {"shots": c[0], "failures": c[3], "nonconverged": c[1], "logical": c[2],
-                    "block_ler": c[3] / max(1, c[0])}}
+                    "block_ler": c[3] / max(1, c[0])},
+            "learned": learned}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, dt, cores = _cpu_baseline(dem, a.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": "shots/s", "cores": cores, "kind": "oracle",
@@ -492,37 +577,27 @@ def run_mixed(a):
             R.relaybp_destroy(h)
 
 
-def run_learned(a):
-    """Learned Relay-BP (trained on self-sampled shots at p = 0.2%) against
-    plain Relay-BP (paper settings, FP32) on the same fresh shots at p = 0.1%.
-
-    Learned decoder: BF16 messages, learned message weights (T = 30) and
-    memory-strength distribution in legs 0..49, plain legs after that in the
-    same launch (the fallback for shots the learned legs leave unconverged),
-    stop after the first solution.  An ablation runs plain Relay-BP with the
-    same stop-after-one rule."""
+def train_learned(a, dev, d_inf, d_train, steps):
+    """Train row-tied message weights and memory-strength knots on self-sampled
+    shots of d_train with the library's forward and backward kernels; keep the
+    checkpoint with the fewest held-out decoding iterations on d_inf (step 0,
+    unit weights and the uniform interval, included).  Returns (wrow, knots,
+    info)."""
     import numpy as np
     import torch
     from paper_2607_27644_b300 import relaybp as R
     from paper_2607_27644_b300.learned import LearnedParams
-    from paper_2607_27644_b300.stats import agree_within
-    from workloads.dem import circuit_dems
-
-    rank, world, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    d_inf, d_train = circuit_dems(WORKLOAD["code"], [0.001, 0.002], WORKLOAD["rounds"], WORKLOAD["basis"])
     E = d_inf.n_edges
-    # 10 unrolled iterations: the summed cross-entropy over 30 is dominated by
-    # iterations past the map's chaotic horizon (marginals grow without bound)
-    # and training on it raised the held-out loss; over 10 it trains steadily
-    T, BT = 10, 512
+    # T unrolled iterations (default 10: summed over 30 the losses are
+    # dominated by iterations past the map's chaotic horizon, where marginals
+    # grow without bound; over 10 they train steadily)
+    T, BT = a.train_T, 512
     # ---- training (untimed) ---------------------------------------------------
     ht = R.relaybp_build_dem(d_train, R.Params(msg_dtype="f32", **DECODER))
     row_of = np.repeat(np.arange(d_inf.n_det), np.diff(d_inf.H_indptr))
     model = LearnedParams(T, E, DECODER["gamma_min"], DECODER["gamma_max"], device=dev, row_of_edge=row_of,
                           n_rows=d_inf.n_det)
-    opt = torch.optim.Adam(model.parameters(), lr=1e-3)
+    opt = torch.optim.Adam(model.parameters(), lr=a.train_lr)
     syn_t = torch.empty((BT, ht.wc), dtype=torch.int32, device=dev)
     err_t = torch.empty((BT, ht.wv), dtype=torch.int32, device=dev)
     syn_v = torch.empty((2 * BT, ht.wc), dtype=torch.int32, device=dev)
@@ -543,7 +618,7 @@ def run_learned(a):
 
     def held_out():
         with torch.no_grad():
-            return float(model.loss(ht, syn_v, err_v, 9 * 10**8, 0x5EED))
+            return float(model.loss(ht, syn_v, err_v, 9 * 10**8, 0x5EED, a.objective))
 
     def held_out_iterations():
         with torch.no_grad():
@@ -568,16 +643,16 @@ def run_learned(a):
             best_state = {n: t.detach().clone() for n, t in model.state_dict().items()}
 
     checkpoint(0)
-    for k in range(a.train_steps):
+    for k in range(steps):
         R.relaybp_sample(ht, 4, k * BT, BT, syn_t, None, err_t)
         opt.zero_grad()
-        loss = model.loss(ht, syn_t, err_t, k * BT, 0x5EED)
+        loss = model.loss(ht, syn_t, err_t, k * BT, 0x5EED, a.objective)
         loss.backward()
         torch.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
         opt.step()
         with torch.no_grad():
             model.w.clamp_(0.0, 2.0)
-        if (k + 1) % 25 == 0 or k == a.train_steps - 1:
+        if (k + 1) % 25 == 0 or k == steps - 1:
             checkpoint(k + 1)
     model.load_state_dict(best_state)
     R.relaybp_destroy(hsel)
@@ -585,6 +660,42 @@ def run_learned(a):
     train_s = time.perf_counter() - t0
     wrow = model.w.detach().float().contiguous()
     knots = model.knots().detach().float().contiguous()
+    info = {"steps": steps, "batch": BT, "shots": steps * BT, "unrolled_iterations": T,
+            "objective": ["cross-entropy against the sampled error", "soft syndrome"][a.objective],
+            "optimizer": f"Adam {a.train_lr:g}, grad-norm clip 1, weights in [0, 2]",
+            "weights": "tied per check row and iteration; unit past the trained horizon", "seconds": train_s,
+            "held_out_loss_every_25_steps": hist, "held_out_mean_iterations_every_25_steps": sel_hist,
+            "selection": f"fewest held-out mean iterations, clipped at the learned legs' horizon ({NSEL} shots of "
+                         f"the inference DEM, stop after the first solution); kept step {best_step}"}
+    R.relaybp_destroy(ht)
+    return wrow, knots, info
+
+
+def run_learned(a):
+    """Learned Relay-BP (trained on self-sampled shots at p = 0.2%) against
+    plain Relay-BP (paper settings, FP32) on the same fresh shots at p = 0.1%.
+
+    Learned decoder: learned row-tied message weights for the first T
+    iterations of each learned leg (unit weights after them) and a learned
+    memory-strength distribution, in legs 0..49; plain legs after that in the
+    same launch (the fallback for shots the learned legs leave unconverged);
+    stop after the first solution; FP32 messages (the two-shot kernel) and
+    the --learned-msg storage.  Ablations run plain Relay-BP with the same
+    stop-after-one rule at both precisions: what the learned parameters gain
+    is learned vs ablation; learned vs plain also counts the stopping rule."""
+    import numpy as np
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from paper_2607_27644_b300.learned import LearnedParams
+    from paper_2607_27644_b300.stats import agree_within
+    from workloads.dem import circuit_dems
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    d_inf, d_train = circuit_dems(WORKLOAD["code"], [0.001, 0.002], WORKLOAD["rounds"], WORKLOAD["basis"])
+    E = d_inf.n_edges
+    wrow, knots, train_info = train_learned(a, dev, d_inf, d_train, a.train_steps)
     # ---- decoders: one handle set per stream ------------------------------------
     # learned parameters for legs 0..49, then plain legs (unit weights, uniform
     # gamma) up to the paper's 1000 in the same launch: the plain fallback for
@@ -595,12 +706,14 @@ def run_learned(a):
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     H = []
     for q in range(NS):
-        hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype=a.learned_msg, **learned_params))
-        R.relaybp_set_learned_rows(hl, wrow, knots)
-        R.relaybp_set_learned_legs(hl, LEGS)
-        H.append({"learned": hl,
-                  "plain": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **DECODER)),
-                  "ablation": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1)))})
+        hh = {"plain": R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **DECODER))}
+        for msg in ("f32", a.learned_msg):
+            hl = R.relaybp_build_dem(d_inf, R.Params(msg_dtype=msg, **learned_params))
+            R.relaybp_set_learned_rows(hl, wrow, knots)
+            R.relaybp_set_learned_legs(hl, LEGS)
+            hh["learned_" + msg] = hl
+            hh["ablation_" + msg] = R.relaybp_build_dem(d_inf, R.Params(msg_dtype=msg, **learned_params))
+        H.append(hh)
     hp = H[0]["plain"]
     bufs = [dict(syn=torch.empty((B, hp.wc), dtype=torch.int32, device=dev),
                  obs=torch.empty((B, hp.wk), dtype=torch.int32, device=dev),
@@ -620,7 +733,8 @@ def run_learned(a):
             it.add_(b_["stats"][:, 3].sum())
 
     out = {}
-    for kind in ("plain", "learned", "ablation"):
+    kinds = ["plain"] + [f"{x}_{m}" for m in dict.fromkeys(("f32", a.learned_msg)) for x in ("learned", "ablation")]
+    for kind in kinds:
         cnt = torch.zeros(4, dtype=torch.int64, device=dev)
         it = torch.zeros(1, dtype=torch.int64, device=dev)
         for w_ in range(W):
@@ -644,29 +758,35 @@ def run_learned(a):
         out[kind] = {"shots_per_s": B * K / (ms / 1e3), "ms_per_step": ms / K, "shots": c[0], "failures": c[3],
                      "nonconverged": c[1], "logical": c[2], "block_ler": c[3] / max(1, c[0]),
                      "mean_iterations": float(it.item()) / (B * K), "clocks": clk.summary()}
-    lp, ll = out["plain"], out["learned"]
-    equal = agree_within(ll["failures"], ll["shots"], lp["failures"], lp["shots"])
-    line = {"metric": METRIC, "value": ll["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": K, "warmup": W,
-            "ms_per_step": ll["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": a.learned_msg, "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEMs",
+    lp, lm = out["plain"], a.learned_msg
+    arms = {}
+    for m in dict.fromkeys(("f32", lm)):
+        ll, lab = out["learned_" + m], out["ablation_" + m]
+        arms[m] = {"learned": ll, "ablation_plain_stop1": lab,
+                   "speedup_vs_ablation": ll["shots_per_s"] / lab["shots_per_s"],
+                   "mean_iterations_vs_ablation": ll["mean_iterations"] / lab["mean_iterations"],
+                   "speedup_vs_plain": ll["shots_per_s"] / lp["shots_per_s"],
+                   "equal_ler_2sigma_vs_plain": bool(agree_within(ll["failures"], ll["shots"], lp["failures"],
+                                                                  lp["shots"])),
+                   "equal_ler_2sigma_vs_ablation": bool(agree_within(ll["failures"], ll["shots"], lab["failures"],
+                                                                     lab["shots"]))}
+    best = max(arms.values(), key=lambda x: x["learned"]["shots_per_s"])
+    line = {"metric": METRIC, "value": best["learned"]["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": K,
+            "warmup": W, "ms_per_step": best["learned"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEMs",
             "config": {"workload": "learned vs plain Relay-BP, ZSZ-LP-160 d=10, inference p=0.001, training p=0.002",
-                       "train": {"steps": a.train_steps, "batch": BT, "unrolled_iterations": T,
-                                 "optimizer": "Adam 1e-3, grad-norm clip 1, weights in [0, 2]",
-                                 "weights": "tied per check row and iteration", "seconds": train_s,
-                                 "held_out_loss_every_25_steps": hist,
-                                 "held_out_mean_iterations_every_25_steps": sel_hist,
-                                 "selection": f"fewest held-out mean iterations, clipped at the learned legs' "
-                                              f"horizon ({NSEL} shots of the inference DEM, stop after the first "
-                                              f"solution); kept step {best_step}"},
-                       "learned_decoder": f"{a.learned_msg} messages, learned weights + knots in legs 0-49, plain legs "
-                                          "after (in-kernel fallback), stop_nconv=1",
+                       "train": train_info,
+                       "learned_decoder": "learned weights + knots in legs 0-49, plain legs after (in-kernel "
+                                          "fallback), stop_nconv=1; FP32 and " + lm + " message storage",
+                       "ablation": "plain Relay-BP with the same stop_nconv=1 rule at the same storage precision",
                        "pipeline": "3 streams, steps rotate, L2 flushed before every step",
                        "plain_decoder": "FP32, paper settings (stop_nconv=5)", "shots_per_step": B},
-            "plain": lp, "learned": ll, "ablation_plain_stop1": out["ablation"],
-            "speedup_vs_plain": ll["shots_per_s"] / lp["shots_per_s"], "equal_ler_2sigma": bool(equal),
-            "clocks": ll["clocks"]}
+            "plain": lp, "arms": arms,
+            "note": "speedup_vs_plain mostly measures the stopping rule (stop after the first solution vs five); "
+                    "speedup_vs_ablation is what the learned parameters gain at the same rule",
+            "clocks": best["learned"]["clocks"]}
     print(json.dumps(line), flush=True)
-    R.relaybp_destroy(ht)
     for hh in H:
         for x in hh.values():
             R.relaybp_destroy(x)

@@ -123,7 +123,8 @@ int relaybp_set_params(relaybp_handle *h, const relaybp_params *params);
 
 /* Attach learned parameters to a handle for decoding (the learned form of
  * this library; no counterpart in the paper).  d_w [T][E] FP32 message weights
- * indexed by the iteration within each leg (iterations past T use the last),
+ * indexed by the iteration within each leg (iterations past T of a leg use
+ * unit weights: the trained horizon ends there),
  * d_knots [K+1] FP32 nondecreasing memory-strength inverse CDF for legs >= 1
  * (same meaning as in relaybp_learned_forward; u from stream 1 of the leg).
  * Either may be NULL (NULL and NULL restore the plain method).  Device
@@ -293,21 +294,29 @@ int relaybp_group_destroy(relaybp_group *grp);
  *                gamma_seed) of each variable.
  * relaybp_learned_forward runs, for each shot, T iterations of one memory-BP
  * leg from M = L0, nu = 0 with weighted messages and these strengths, writes
- * d_loss[s] = sum_t sum_j BCE(M_j(t), e_j) (e = d_errors, bit j in error with
- * probability sigmoid(-M_j)) and a tape of relaybp_learned_tape_bytes bytes.
+ * the shot's loss d_loss[s], summed over the T iterations, and a tape of
+ * relaybp_learned_tape_bytes bytes.  objective 0: sum_j BCE(M_j(t), e_j)
+ * (e = d_errors, bit j in error with probability sigmoid(-M_j)); objective 1:
+ * the soft syndrome -sum_i log(eps + (1 - 2 eps) P_i(t)), eps = 1e-6,
+ * P_i = (1 + (-1)^{s_i} prod_{j in row i} tanh(M_j / 2)) / 2 the probability
+ * that check i holds its syndrome bit (s = d_syndromes): it rewards
+ * satisfying every check early, which is what ends a decode.
  * relaybp_learned_backward reads the tape and ADDS scale * dLoss/dw and
  * scale * dLoss/dknots (Loss = sum of the shots' losses) into the
- * caller-zeroed d_grad_w [T][E] and d_grad_knots [K+1].  Gradients flow
- * through the argmin and second-argmin of every check (sign products are
- * piecewise constant); the summation order of the atomics is not fixed. */
+ * caller-zeroed d_grad_w [T][E] and d_grad_knots [K+1]; it needs d_errors for
+ * objective 0 and d_syndromes for objective 1.  Gradients flow through the
+ * argmin and second-argmin of every check (sign products are piecewise
+ * constant); the summation order of the atomics is not fixed.  Objectives
+ * other than 0 and 1: RELAYBP_ERR_INVALID. */
 int64_t relaybp_learned_tape_bytes(const relaybp_handle *h, int32_t precision, int32_t T, int64_t shots);
 int relaybp_learned_forward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
-                            const void *d_knots, uint64_t gamma_seed, const uint32_t *d_syndromes,
-                            const uint32_t *d_errors, uint64_t shot0, int64_t shots, void *d_tape, double *d_loss,
-                            void *cuda_stream);
+                            const void *d_knots, uint64_t gamma_seed, int32_t objective,
+                            const uint32_t *d_syndromes, const uint32_t *d_errors, uint64_t shot0, int64_t shots,
+                            void *d_tape, double *d_loss, void *cuda_stream);
 int relaybp_learned_backward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
-                             const void *d_knots, uint64_t gamma_seed, const uint32_t *d_errors, uint64_t shot0,
-                             int64_t shots, const void *d_tape, double scale, void *d_grad_w, void *d_grad_knots,
+                             const void *d_knots, uint64_t gamma_seed, int32_t objective,
+                             const uint32_t *d_syndromes, const uint32_t *d_errors, uint64_t shot0, int64_t shots,
+                             const void *d_tape, double scale, void *d_grad_w, void *d_grad_knots,
                              void *cuda_stream);
 
 /* Number of kernel launches this handle has issued since it was built. */

@@ -81,8 +81,8 @@ def _load():
                                                      ctypes.c_uint64, ctypes.c_int64, P, P, P, P, P, ctypes.c_int32])
         _lib.oracle_relaybp_decode_post.restype = ctypes.c_int
         _lib.oracle_learned_loss.argtypes = ([ctypes.c_int32] * 2 + [P] * 3 + [ctypes.c_int32, P, ctypes.c_int32, P,
-                                             ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64, P, P,
-                                             ctypes.c_int32])
+                                             ctypes.c_uint64, P, P, ctypes.c_uint64, ctypes.c_int64,
+                                             ctypes.c_int32, P, P, ctypes.c_int32])
         _lib.oracle_learned_loss.restype = ctypes.c_int
         _lib.oracle_relaybp_decode_learned.argtypes = ([ctypes.c_int32] * 3 + [P] * 5 +
                                                        [ctypes.POINTER(OracleParams), ctypes.c_int32, P,
@@ -340,11 +340,14 @@ def pack_bits(bits: np.ndarray) -> np.ndarray:
 
 
 def learned_loss(dem, w: np.ndarray, knots: np.ndarray, gamma_seed: int, syndromes: np.ndarray,
-                 errors: np.ndarray, shot0: int = 0, trace: bool = False, n_threads: int = 0):
+                 errors: np.ndarray, shot0: int = 0, trace: bool = False, n_threads: int = 0,
+                 objective: int = 0):
     """Per-shot loss of the learned forward (T = w.shape[0] unrolled iterations).
 
     w: [T, E] message weights in row-major edge order; knots: [K+1] inverse CDF
-    of the memory strengths.  Returns (loss [shots], trace [shots, T, V] or None).
+    of the memory strengths; objective 0: cross-entropy of M against the
+    sampled error, 1: soft syndrome (-log probability that each check holds
+    its syndrome bit).  Returns (loss [shots], trace [shots, T, V] or None).
     """
     lib = _load()
     Hp, Hi, _, _, pr = _dem_arrays(dem)
@@ -357,7 +360,8 @@ def learned_loss(dem, w: np.ndarray, knots: np.ndarray, gamma_seed: int, syndrom
     loss = np.zeros(shots, dtype=np.float64)
     tr = np.zeros((shots, T, dem.n_loc), dtype=np.float64) if trace else None
     rc = lib.oracle_learned_loss(dem.n_det, dem.n_loc, _ptr(Hp), _ptr(Hi), _ptr(pr), T, _ptr(w), K, _ptr(knots),
-                                 gamma_seed, _ptr(syn), _ptr(err), shot0, shots, _ptr(loss), _ptr(tr), n_threads)
+                                 gamma_seed, _ptr(syn), _ptr(err), shot0, shots, objective, _ptr(loss), _ptr(tr),
+                                 n_threads)
     if rc != 0:
         raise ValueError("oracle_learned_loss rejected its input")
     return loss, tr

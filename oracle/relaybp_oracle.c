@@ -250,7 +250,8 @@ static void decode_one(const graph_t *g, const oracle_params *P, const learned_t
                     mu[e] = s;
                 }
             /* a3: min-sum check update, leave-one-out by direct loops */
-            const double *wt = (lleg && LP->w) ? LP->w + (int64_t)((t - 1 < LP->T ? t - 1 : LP->T - 1)) * E : NULL;
+            /* learned weights for the first T iterations of a learned leg, unit weights past them */
+            const double *wt = (lleg && LP->w && t - 1 < LP->T) ? LP->w + (int64_t)(t - 1) * E : NULL;
             for (int32_t i = 0; i < C; ++i) {
                 double ssign = get_bit(syn, i) ? -1.0 : 1.0;
                 for (int32_t e = g->rptr[i]; e < g->rptr[i + 1]; ++e) {
@@ -490,6 +491,16 @@ int oracle_max_threads(void)
  * (the error probability of bit j is sigmoid(-M_j)).  Plain loops, FP64. */
 static double softplus(double x) { return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
 
+/* Second training objective (project choice): the soft syndrome.  With the
+ * bits independent and bit j in error with probability sigmoid(-M_j), check
+ * i holds its syndrome bit s_i with probability
+ *   P_i = (1 + (-1)^{s_i} prod_{j in row i} tanh(M_j / 2)) / 2,
+ * and the loss of iteration t is -sum_i log(eps + (1 - 2 eps) P_i(t)), summed
+ * over the T unrolled iterations: it rewards satisfying every check early,
+ * which is what ends a decode.  eps bounds the loss of a confidently violated
+ * check. */
+#define SOFT_SYN_EPS 1e-6
+
 static double knot_gamma(const double *knots, int32_t K, double u)
 {
     double x = u * (double)K;
@@ -510,9 +521,9 @@ static double draw_u(uint64_t seed, uint64_t shot, int32_t leg, int32_t j, int32
 int oracle_learned_loss(int32_t n_det, int32_t n_loc, const int32_t *H_indptr, const int32_t *H_indices,
                         const double *priors, int32_t T, const double *w, int32_t K, const double *knots,
                         uint64_t gamma_seed, const uint32_t *syndromes, const uint32_t *errors, uint64_t shot0,
-                        int64_t shots, double *loss, double *trace, int32_t n_threads)
+                        int64_t shots, int32_t objective, double *loss, double *trace, int32_t n_threads)
 {
-    if (n_det < 0 || n_loc < 0 || shots < 0 || T < 1 || K < 1) return -1;
+    if (n_det < 0 || n_loc < 0 || shots < 0 || T < 1 || K < 1 || objective < 0 || objective > 1) return -1;
     const int32_t E = H_indptr[n_det];
     int64_t wd = (n_det + 31) / 32, wv = (n_loc + 31) / 32;
     double *L0 = malloc(sizeof(double) * (size_t)(n_loc + 1));
@@ -585,9 +596,16 @@ int oracle_learned_loss(int32_t n_det, int32_t n_loc, const int32_t *H_indptr, c
                     for (int32_t a = cptr[j]; a < cptr[j + 1]; ++a) v += nu[cedge[a]];
                     M[j] = v;
                     int e_j = get_bit(err, j);
-                    acc += e_j ? softplus(v) : softplus(-v);
+                    if (objective == 0) acc += e_j ? softplus(v) : softplus(-v);
                     if (trace) trace[((int64_t)s * T + (t - 1)) * n_loc + j] = v;
                 }
+                if (objective == 1)             /* soft syndrome: -log P(check i satisfied) */
+                    for (int32_t i = 0; i < n_det; ++i) {
+                        double prod = 1.0;
+                        for (int32_t e = H_indptr[i]; e < H_indptr[i + 1]; ++e) prod *= tanh(0.5 * M[H_indices[e]]);
+                        const double sat = 0.5 * (1.0 + (get_bit(syn, i) ? -prod : prod));
+                        acc -= log(SOFT_SYN_EPS + (1.0 - 2.0 * SOFT_SYN_EPS) * sat);
+                    }
             }
             loss[s] = acc;
         }

@@ -611,12 +611,14 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
             bool conv = false;
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: check rows, L lanes per row ---------------------------
+                // learned weights for the first lT iterations of a learned leg,
+                // unit weights (NULL) past them
                 const float *wprev = nullptr, *wcur = nullptr, *wrow = nullptr;
                 if (LW && lleg && p.lw) {
-                    wprev = p.lw + (int64_t)min(t > 0 ? t - 1 : 0, p.lT - 1) * g.E;
-                    wcur = p.lw + (int64_t)min(t, p.lT - 1) * g.E;
+                    if (t > 0 && t - 1 < p.lT) wprev = p.lw + (int64_t)(t - 1) * g.E;
+                    if (t < p.lT) wcur = p.lw + (int64_t)t * g.E;
                 }
-                if (lleg && p.lwrow) wrow = p.lwrow + (int64_t)min(t, p.lT - 1) * g.C;
+                if (lleg && p.lwrow && t < p.lT) wrow = p.lwrow + (int64_t)t * g.C;
                 if (LW) row_pass<S, L, NB, true>(g, A, cs, sgw, syn, warp, nwarp, lane, wprev, wrow, qs);
                 else row_pass<S, L, NB, false>(g, A, cs, sgw, syn, warp, nwarp, lane, nullptr, wrow, qs);
                 __syncthreads();

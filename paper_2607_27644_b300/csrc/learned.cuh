@@ -9,8 +9,17 @@
 //             g(u) = knots[k] + (knots[k+1] - knots[k]) (uK - k), k = floor(uK),
 //             u the 24-bit Philox stream-1 draw of leg 1.
 // Training forward of one shot: T iterations of one memory-BP leg from
-// M = L0, nu = 0, with loss = sum_t sum_j BCE(M_j(t), e_j) (bit j in error with
-// probability sigmoid(-M_j)).
+// M = L0, nu = 0, with one of two losses summed over the iterations t:
+//   objective 0: sum_j BCE(M_j(t), e_j) (bit j in error with probability
+//                sigmoid(-M_j)), the sampled error as the label;
+//   objective 1: the soft syndrome -sum_i log(eps + (1 - 2 eps) P_i(t)),
+//                P_i = (1 + (-1)^{s_i} prod_{j in row i} tanh(M_j / 2)) / 2 the
+//                probability that check i holds its syndrome bit; it rewards
+//                satisfying every check early, which is what ends a decode.
+// Its gradient with respect to M_j(t) is
+//   sum_{i in col j} c_i loo_ij (1 - tanh^2(M_j / 2)) / 2,
+//   c_i = -(1 - 2 eps) (-1)^{s_i} / (2 (eps + (1 - 2 eps) P_i)),
+// loo_ij the product of tanh(M_k / 2) over the row's other variables.
 //
 // Reverse mode.  With B_j(t) = Mbar_j(t) + sum_{col j} mubar(t+1):
 //   Mbar_j(t)   = s (e_j - sigmoid(-M_j(t))) + g_j Lbar_j(t+1)
@@ -37,9 +46,12 @@ struct TapePlan {               // byte offsets within one iteration's tape reco
     int rows, sgn, M, iter;     // iter: bytes of one iteration
 };
 
+constexpr double kSoftSynEps = 1e-6;
+
 struct LearnedDev {
     DevDEM g;
     int T, K;
+    int objective;              // 0: cross-entropy against the sampled error, 1: soft syndrome
     const void *w;              // [T][E] of the arithmetic type
     const void *knots;          // [K+1]
     uint64_t gamma_seed;
@@ -53,8 +65,50 @@ struct LearnedDev {
 };
 
 struct LearnedSmem {            // byte offsets of the per-shot shared state
-    int a, b, c, d, rows, sgn, syn, total;
+    int a, b, c, d, rows, sgn, syn, srow, total;    // srow: soft-syndrome row terms (objective 1)
 };
+
+// Soft-syndrome terms of check row i from the posteriors M: the product of
+// tanh(M_j / 2) over the row's nonzero factors, how many factors are zero,
+// and the coefficient c_i of the gradient; returns the row's loss.
+template <typename T> struct SoftRow {
+    T prod, coef;
+    int zeros;
+};
+template <typename T>
+__device__ __forceinline__ T soft_row(const DevDEM &g, const T *M, const uint32_t *syn, int i, SoftRow<T> &out)
+{
+    T prod = (T)1;
+    int zeros = 0;
+    for (int e = __ldg(g.rptr + i), ee = __ldg(g.rptr + i + 1); e < ee; ++e) {
+        const T th = tanh((T)0.5 * M[__ldg(g.rvar + e)]);
+        if (th == (T)0) ++zeros;
+        else prod *= th;
+    }
+    const T sgn = ((syn[i >> 5] >> (i & 31)) & 1u) ? (T)-1 : (T)1;
+    const T P = (T)0.5 * ((T)1 + sgn * (zeros ? (T)0 : prod));
+    const T q = (T)kSoftSynEps + (T)(1.0 - 2.0 * kSoftSynEps) * P;
+    out.prod = prod;
+    out.zeros = zeros;
+    out.coef = -(T)(1.0 - 2.0 * kSoftSynEps) * sgn / ((T)2 * q);
+    return -log(q);
+}
+
+// d loss / d M_j from the rows' soft-syndrome terms (column j's checks).
+template <typename T>
+__device__ __forceinline__ T soft_grad(const DevDEM &g, const SoftRow<T> *sr, const T *M, int j)
+{
+    const T th = tanh((T)0.5 * M[j]);
+    T acc = (T)0;
+    for (int q = __ldg(g.cptr + j), qe = __ldg(g.cptr + j + 1); q < qe; ++q) {
+        const SoftRow<T> r = sr[__ldg(g.cchk + q)];
+        T loo;
+        if (th != (T)0) loo = r.zeros ? (T)0 : r.prod / th;
+        else loo = (r.zeros == 1) ? r.prod : (T)0;
+        acc += r.coef * loo;
+    }
+    return acc * (T)0.5 * ((T)1 - th * th);
+}
 
 template <typename T>
 __device__ __forceinline__ T knot_gamma(const T *knots, int K, T u)
@@ -222,11 +276,19 @@ learned_forward_kernel(LearnedDev a, LearnedSmem sp, unsigned long long *__restr
                     M[j] = Mn;
                     A[j] = ((T)1 - gj) * l0 + gj * Mn + S;
                     tM[j] = Mn;
-                    const uint32_t ej = (__ldg(err + (j >> 5)) >> (j & 31)) & 1u;
-                    acc += (double)(ej ? softplus<T>(Mn) : softplus<T>(-Mn));
+                    if (a.objective == 0) {
+                        const uint32_t ej = (__ldg(err + (j >> 5)) >> (j & 31)) & 1u;
+                        acc += (double)(ej ? softplus<T>(Mn) : softplus<T>(-Mn));
+                    }
                 }
             }
             __syncthreads();
+            if (a.objective == 1) {             // soft syndrome of this iteration's posteriors
+                for (int i = tid; i < C; i += nthr) {
+                    SoftRow<T> sr;
+                    acc += (double)soft_row<T>(g, M, syn, i, sr);
+                }
+            }
         }
         // per-shot loss: block reduction in FP64
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
@@ -262,6 +324,8 @@ learned_backward_kernel(LearnedDev a, LearnedSmem sp, unsigned long long *__rest
     T *B = reinterpret_cast<T *>(smem + sp.c);
     T *gam = reinterpret_cast<T *>(smem + sp.d);
     BackRow<T> *rec = reinterpret_cast<BackRow<T> *>(smem + sp.rows);
+    SoftRow<T> *srow = reinterpret_cast<SoftRow<T> *>(smem + sp.srow);
+    uint32_t *syn = reinterpret_cast<uint32_t *>(smem + sp.syn);
     __shared__ long long s_shot;
     __shared__ T s_kg[65];
 
@@ -293,6 +357,8 @@ learned_backward_kernel(LearnedDev a, LearnedSmem sp, unsigned long long *__rest
         }
         for (int i = tid; i < C; i += nthr) { rec[i].mb1 = (T)0; rec[i].mb2 = (T)0; rec[i].meta = 0xffffffu; }
         for (int k = tid; k <= a.K; k += nthr) s_kg[k] = (T)0;
+        if (a.objective == 1)
+            for (int w = tid; w < wordsof(C); w += nthr) syn[w] = a.syn[sidx * wordsof(C) + w];
         __syncthreads();
         for (int t = a.T; t >= 1; --t) {
             const unsigned char *it = tape + (size_t)(t - 1) * a.tp.iter;
@@ -301,11 +367,21 @@ learned_backward_kernel(LearnedDev a, LearnedSmem sp, unsigned long long *__rest
             const T *tM = reinterpret_cast<const T *>(it + a.tp.M);
             const T *wcur = W + (int64_t)(t - 1) * E;
             T *gw = grad_w + (int64_t)(t - 1) * E;
+            if (a.objective == 1) {             // the rows' soft-syndrome terms at M(t)
+                for (int i = tid; i < C; i += nthr) soft_row<T>(g, tM, syn, i, srow[i]);
+                __syncthreads();
+            }
             // variable pass A: Mbar(t) and B(t)
             for (int j = tid; j < V; j += nthr) {
                 const T Mt = tM[j];
-                const uint32_t ej = (__ldg(err + (j >> 5)) >> (j & 31)) & 1u;
-                const T mbar = scale * ((T)ej - sigm<T>(-Mt)) + gam[j] * Lbar[j];
+                T src;
+                if (a.objective == 0) {
+                    const uint32_t ej = (__ldg(err + (j >> 5)) >> (j & 31)) & 1u;
+                    src = (T)ej - sigm<T>(-Mt);
+                } else {
+                    src = soft_grad<T>(g, srow, tM, j);
+                }
+                const T mbar = scale * src + gam[j] * Lbar[j];
                 B[j] = mbar + colbar[j];
                 Lbar[j] = mbar;
             }

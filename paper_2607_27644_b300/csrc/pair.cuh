@@ -299,9 +299,9 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
     while (act[0] || act[1]) {
         // ---- a3: check rows of both shots ----------------------------------
         const float *wrow0 = nullptr, *wrow1 = nullptr;
-        if (J.p.lwrow) {
-            if (J.p.llegs < 0 || s_leg[0] < J.p.llegs) wrow0 = J.p.lwrow + (int64_t)min(t[0], J.p.lT - 1) * Cn;
-            if (J.p.llegs < 0 || s_leg[1] < J.p.llegs) wrow1 = J.p.lwrow + (int64_t)min(t[1], J.p.lT - 1) * Cn;
+        if (J.p.lwrow) {                        // first lT iterations of a learned leg; unit past them
+            if ((J.p.llegs < 0 || s_leg[0] < J.p.llegs) && t[0] < J.p.lT) wrow0 = J.p.lwrow + (int64_t)t[0] * Cn;
+            if ((J.p.llegs < 0 || s_leg[1] < J.p.llegs) && t[1] < J.p.lT) wrow1 = J.p.lwrow + (int64_t)t[1] * Cn;
         }
         pair_row_pass<NB>(J, smem, syn(0), syn(1), wrow0, wrow1, warp, nwarp, lane);
         __syncthreads();

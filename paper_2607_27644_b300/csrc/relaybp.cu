@@ -322,15 +322,15 @@ struct JobIO {
 };
 
 // FP64 in the literal evaluation order when one shot's per-edge messages fit
-// in shared memory (at most a quarter of it, so that several shots share an
-// SM); returns 1 if the DEM is too large for this kernel.
+// in shared memory (at most half of it, so that two shots share an SM);
+// returns 1 if the DEM is too large for this kernel.
 int launch_decode_exact(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st)
 {
     const DevDEM &g = h->dem;
     ExactPlan plan = make_exact_plan(g);
     int maxsm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (plan.total > maxsm / 4) return 1;
+    if (plan.total > maxsm / 2) return 1;
     CUDA_TRY(cudaFuncSetAttribute(relay_decode_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
     const int threads = g.E <= 4096 ? 128 : 256;
     int per_sm = 0;
@@ -654,12 +654,13 @@ LearnedSmem learned_smem(const DevDEM &g, int L, bool backward)
     sp.rows = take((backward ? sizeof(BackRow<T>) : sizeof(TapeRow<T>)) * (size_t)g.C);
     sp.sgn = backward ? 0 : take(2 * (size_t)g.C * (size_t)L);
     sp.syn = take(4 * (size_t)words(g.C));
+    sp.srow = backward ? take(sizeof(SoftRow<T>) * (size_t)g.C) : 0;
     sp.total = (int)((off + 15) & ~size_t(15));
     return sp;
 }
 
 struct LearnedCall {
-    int precision, T, K;
+    int precision, T, K, objective;
     const void *w, *knots;
     uint64_t gamma_seed;
     const uint32_t *syn, *err;
@@ -685,6 +686,7 @@ int learned_launch(relaybp_handle *h, const LearnedCall &c, bool backward, cudaS
     a.g = g;
     a.T = c.T;
     a.K = c.K;
+    a.objective = c.objective;
     a.w = c.w;
     a.knots = c.knots;
     a.gamma_seed = c.gamma_seed;
@@ -755,6 +757,9 @@ int learned_check(relaybp_handle *h, const LearnedCall &c, bool backward)
     if (c.precision != RELAYBP_MSG_F32 && c.precision != RELAYBP_MSG_F64)
         return fail(RELAYBP_ERR_UNSUPPORTED, "learned training runs in FP32 or FP64");
     if (c.T < 1 || c.K < 1 || c.K > 64) return fail(RELAYBP_ERR_INVALID, "need T >= 1 and 1 <= K <= 64");
+    if (c.objective != 0 && c.objective != 1) return fail(RELAYBP_ERR_INVALID, "objective must be 0 or 1");
+    if (backward && c.objective == 1 && !c.syn)
+        return fail(RELAYBP_ERR_INVALID, "the soft-syndrome objective needs the syndromes");
     if (c.shots < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
     if (!c.w || !c.knots || !c.err || !c.tape) return fail(RELAYBP_ERR_INVALID, "null pointer");
     if (!backward && (!c.syn || !c.loss)) return fail(RELAYBP_ERR_INVALID, "null pointer");
@@ -776,13 +781,13 @@ int64_t relaybp_learned_tape_bytes(const relaybp_handle *h, int32_t precision, i
 }
 
 int relaybp_learned_forward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
-                            const void *d_knots, uint64_t gamma_seed, const uint32_t *d_syndromes,
-                            const uint32_t *d_errors, uint64_t shot0, int64_t shots, void *d_tape, double *d_loss,
-                            void *cuda_stream)
+                            const void *d_knots, uint64_t gamma_seed, int32_t objective,
+                            const uint32_t *d_syndromes, const uint32_t *d_errors, uint64_t shot0, int64_t shots,
+                            void *d_tape, double *d_loss, void *cuda_stream)
 {
     g_err.clear();
-    LearnedCall c{precision, T, K, d_w, d_knots, gamma_seed, d_syndromes, d_errors, shot0, shots, d_tape, d_loss,
-                  0.0, nullptr, nullptr};
+    LearnedCall c{precision, T, K, objective, d_w, d_knots, gamma_seed, d_syndromes, d_errors, shot0, shots, d_tape,
+                  d_loss, 0.0, nullptr, nullptr};
     if (int rc = learned_check(h, c, false)) return rc;
     if (shots == 0) return 0;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -791,12 +796,13 @@ int relaybp_learned_forward(relaybp_handle *h, int32_t precision, int32_t T, con
 }
 
 int relaybp_learned_backward(relaybp_handle *h, int32_t precision, int32_t T, const void *d_w, int32_t K,
-                             const void *d_knots, uint64_t gamma_seed, const uint32_t *d_errors, uint64_t shot0,
-                             int64_t shots, const void *d_tape, double scale, void *d_grad_w, void *d_grad_knots,
+                             const void *d_knots, uint64_t gamma_seed, int32_t objective,
+                             const uint32_t *d_syndromes, const uint32_t *d_errors, uint64_t shot0, int64_t shots,
+                             const void *d_tape, double scale, void *d_grad_w, void *d_grad_knots,
                              void *cuda_stream)
 {
     g_err.clear();
-    LearnedCall c{precision, T, K, d_w, d_knots, gamma_seed, nullptr, d_errors, shot0, shots,
+    LearnedCall c{precision, T, K, objective, d_w, d_knots, gamma_seed, d_syndromes, d_errors, shot0, shots,
                   const_cast<void *>(d_tape), nullptr, scale, d_grad_w, d_grad_knots};
     if (int rc = learned_check(h, c, true)) return rc;
     if (shots == 0) return 0;
@@ -1215,7 +1221,7 @@ int relaybp_autotune(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t sh
         ExactPlan ep = make_exact_plan(h->dem);
         int maxsm = 0;
         CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-        if (ep.total <= maxsm / 4) return fail(RELAYBP_ERR_UNSUPPORTED, "the literal-order FP64 kernel has no shape to tune");
+        if (ep.total <= maxsm / 2) return fail(RELAYBP_ERR_UNSUPPORTED, "the literal-order FP64 kernel has no shape to tune");
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const RowGeom opts[] = {{4, 4}, {8, 4}, {8, 8}, {8, 12}, {8, 16}, {16, 16}, {32, 16}};

@@ -3,11 +3,15 @@
 Not in arXiv 2607.27644 (which decodes with plain Relay-BP).  The model:
 per-iteration, per-edge weights w[t][e] on the min-sum check-to-variable
 messages and a monotone piecewise-linear inverse CDF of the memory strength
-(K segments) in place of the uniform interval.  The loss is the summed binary
-cross-entropy of the posteriors against the sampled errors over T unrolled
-iterations of one memory-BP leg; forward and backward run in the library's
-CUDA kernels (relaybp_learned_forward / _backward), wrapped here in a
-torch.autograd.Function so torch optimisers can train the parameters.
+(K segments) in place of the uniform interval.  The loss, summed over T
+unrolled iterations of one memory-BP leg, is the binary cross-entropy of the
+posteriors against the sampled errors (objective 0) or the soft syndrome
+(objective 1: -log of the probability that each check holds its syndrome bit
+under the posteriors, which rewards settling early); forward and backward run
+in the library's CUDA kernels (relaybp_learned_forward / _backward), wrapped
+here in a torch.autograd.Function so torch optimisers can train the
+parameters.  Decoding applies the weights to the first T iterations of each
+learned leg and unit weights after them.
 """
 from __future__ import annotations
 
@@ -17,30 +21,32 @@ from . import relaybp as R
 
 
 class LearnedLoss(torch.autograd.Function):
-    """loss = mean over shots of sum_t sum_j BCE(M_j(t), e_j)."""
+    """loss = mean over shots of the summed per-iteration objective."""
 
     @staticmethod
-    def forward(ctx, w, knots, handle, syndromes, errors, shot0: int, gamma_seed: int):
+    def forward(ctx, w, knots, handle, syndromes, errors, shot0: int, gamma_seed: int, objective: int = 0):
         shots = syndromes.shape[0]
         T = w.shape[0]
         prec = R._prec(w.dtype)
         tape = torch.empty(R.relaybp_learned_tape_bytes(handle, prec, T, shots), dtype=torch.uint8,
                            device=w.device)
         loss = torch.empty(shots, dtype=torch.float64, device=w.device)
-        R.relaybp_learned_forward(handle, w, knots, gamma_seed, syndromes, errors, shot0, shots, tape, loss)
-        ctx.save_for_backward(w, knots, errors, tape)
-        ctx.meta = (handle, shot0, gamma_seed, shots)
+        R.relaybp_learned_forward(handle, w, knots, gamma_seed, syndromes, errors, shot0, shots, tape, loss,
+                                  objective=objective)
+        ctx.save_for_backward(w, knots, syndromes, errors, tape)
+        ctx.meta = (handle, shot0, gamma_seed, shots, objective)
         return loss.mean().to(w.dtype)
 
     @staticmethod
     def backward(ctx, grad_out):
-        w, knots, errors, tape = ctx.saved_tensors
-        handle, shot0, gamma_seed, shots = ctx.meta
+        w, knots, syndromes, errors, tape = ctx.saved_tensors
+        handle, shot0, gamma_seed, shots, objective = ctx.meta
         gw = torch.zeros_like(w)
         gk = torch.zeros_like(knots)
         scale = float(grad_out.item()) / shots
-        R.relaybp_learned_backward(handle, w, knots, gamma_seed, errors, shot0, shots, tape, scale, gw, gk)
-        return gw, gk, None, None, None, None, None
+        R.relaybp_learned_backward(handle, w, knots, gamma_seed, errors, shot0, shots, tape, scale, gw, gk,
+                                   objective=objective, d_syndromes=syndromes)
+        return gw, gk, None, None, None, None, None, None
 
 
 class LearnedParams(torch.nn.Module):
@@ -74,6 +80,6 @@ class LearnedParams(torch.nn.Module):
     def edge_weights(self):
         return self.w if self.row_of_edge is None else self.w.index_select(1, self.row_of_edge)
 
-    def loss(self, handle, syndromes, errors, shot0: int, gamma_seed: int):
+    def loss(self, handle, syndromes, errors, shot0: int, gamma_seed: int, objective: int = 0):
         return LearnedLoss.apply(self.edge_weights().contiguous(), self.knots(), handle, syndromes, errors, shot0,
-                                 gamma_seed)
+                                 gamma_seed, objective)

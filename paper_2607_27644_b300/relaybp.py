@@ -66,9 +66,9 @@ def _load() -> ctypes.CDLL:
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
         "relaybp_learned_tape_bytes": ([P, I32, I32, I64], I64),
-        "relaybp_learned_forward": ([P, I32, I32, P, I32, P, U64, P, P, U64, I64, P, P, P], ctypes.c_int),
-        "relaybp_learned_backward": ([P, I32, I32, P, I32, P, U64, P, U64, I64, P, ctypes.c_double, P, P, P],
-                                     ctypes.c_int),
+        "relaybp_learned_forward": ([P, I32, I32, P, I32, P, U64, I32, P, P, U64, I64, P, P, P], ctypes.c_int),
+        "relaybp_learned_backward": ([P, I32, I32, P, I32, P, U64, I32, P, P, U64, I64, P, ctypes.c_double, P, P,
+                                      P], ctypes.c_int),
         "relaybp_autotune": ([P, P, U64, I64, P, P, P, P, P], ctypes.c_int),
         "relaybp_group_create": ([P, I32, ctypes.POINTER(P)], ctypes.c_int),
         "relaybp_group_decode": ([P, P, P, P, P, P, P, P], ctypes.c_int),
@@ -308,19 +308,21 @@ def relaybp_learned_tape_bytes(h: Handle, precision: int, T: int, shots: int) ->
 
 
 def relaybp_learned_forward(h: Handle, w, knots, gamma_seed: int, d_syndromes, d_errors, shot0: int, shots: int,
-                            d_tape, d_loss, stream=None):
+                            d_tape, d_loss, stream=None, objective: int = 0):
     T, K = w.shape[0], knots.shape[0] - 1
-    _check(_lib.relaybp_learned_forward(h.ptr, _prec(w.dtype), T, _ptr(w), K, _ptr(knots), gamma_seed,
+    _check(_lib.relaybp_learned_forward(h.ptr, _prec(w.dtype), T, _ptr(w), K, _ptr(knots), gamma_seed, objective,
                                         _ptr(d_syndromes), _ptr(d_errors), shot0, shots, _ptr(d_tape), _ptr(d_loss),
                                         _stream(stream)), "relaybp_learned_forward")
 
 
 def relaybp_learned_backward(h: Handle, w, knots, gamma_seed: int, d_errors, shot0: int, shots: int, d_tape,
-                             scale: float, d_grad_w, d_grad_knots, stream=None):
+                             scale: float, d_grad_w, d_grad_knots, stream=None, objective: int = 0,
+                             d_syndromes=None):
     T, K = w.shape[0], knots.shape[0] - 1
-    _check(_lib.relaybp_learned_backward(h.ptr, _prec(w.dtype), T, _ptr(w), K, _ptr(knots), gamma_seed,
-                                         _ptr(d_errors), shot0, shots, _ptr(d_tape), scale, _ptr(d_grad_w),
-                                         _ptr(d_grad_knots), _stream(stream)), "relaybp_learned_backward")
+    _check(_lib.relaybp_learned_backward(h.ptr, _prec(w.dtype), T, _ptr(w), K, _ptr(knots), gamma_seed, objective,
+                                         _ptr(d_syndromes), _ptr(d_errors), shot0, shots, _ptr(d_tape), scale,
+                                         _ptr(d_grad_w), _ptr(d_grad_knots), _stream(stream)),
+           "relaybp_learned_backward")
 
 
 def relaybp_autotune(h: Handle, d_syndromes, shot0: int, shots: int, stream=None) -> dict:

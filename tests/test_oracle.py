@@ -639,3 +639,56 @@ def test_carry_messages_two_check_recurrence():
                     want.append((M1, M2))
             assert np.allclose(r["trace"][0], np.array(want), rtol=1e-12, atol=1e-12), (carry, g)
             assert r["stats"][0, 0] == 0 and r["stats"][0, 2] == legs
+
+
+def test_soft_syndrome_objective_against_enumeration():
+    """The soft-syndrome training objective (objective 1): for each iteration
+    and check, the probability that independent bits, bit j in error with
+    probability sigmoid(-M_j), have the row's syndrome parity -- computed here
+    by enumerating every error pattern on the row's variables -- enters the
+    loss as -log(eps + (1 - 2 eps) P); summed over checks and the T
+    iterations of the forward (whose posteriors the trace gives)."""
+    pr = [0.1, 0.3, 0.2, 0.05, 0.4]
+    H = np.array([[1, 1, 0, 1, 0], [0, 1, 1, 0, 1], [1, 0, 1, 1, 1]], dtype=np.uint8)
+    D = dem_from_dense(H, pr)
+    T = 3
+    w = np.random.default_rng(5).uniform(0.6, 1.2, (T, D.n_edges))
+    knots = np.linspace(-0.1, 0.5, 9)
+    syn = pack_bits(np.array([[1, 0, 1], [0, 0, 0], [1, 1, 0]]))
+    err = pack_bits(np.zeros((3, 5), dtype=np.uint8))
+    loss, tr = oracle.learned_loss(D, w, knots, 13, syn, err, trace=True, objective=1)
+    eps = 1e-6
+    S = unpack_bits(syn, 3)
+    for s_ in range(3):
+        want = 0.0
+        for t in range(T):
+            q = 1.0 / (1.0 + np.exp(tr[s_, t]))          # P(bit in error) = sigmoid(-M)
+            for i in range(3):
+                vars_ = np.nonzero(H[i])[0]
+                P = 0.0
+                for bits in itertools.product((0, 1), repeat=len(vars_)):
+                    pb = np.prod([q[v] if b else 1 - q[v] for v, b in zip(vars_, bits)])
+                    if sum(bits) % 2 == S[s_, i]:
+                        P += pb
+                want -= math.log(eps + (1 - 2 * eps) * P)
+        assert math.isclose(loss[s_], want, rel_tol=1e-10), (s_, loss[s_], want)
+    # the cross-entropy objective on the same run is a different number
+    l0, _ = oracle.learned_loss(D, w, knots, 13, syn, err, objective=0)
+    assert not np.allclose(l0, loss)
+
+
+def test_learned_weights_end_at_the_trained_horizon():
+    """Learned weights apply to the first T iterations of a leg; later
+    iterations use unit weights: with w[T-1] = 0.5 and more iterations than T,
+    the decode equals the one whose weight table is extended by ones, and
+    differs from the one that repeats w[T-1]."""
+    D = circuit_dem("ZSZ-LP-60", 0.006, 3, "Z")
+    syn, _, _ = oracle.sample(D, 29, 0, 24)
+    P = DecodeParams(num_sets=4, pre_iter=30, max_iterations=20, seed=4)
+    T = 3
+    w = np.random.default_rng(6).uniform(0.5, 0.9, (T, D.n_edges))
+    a = oracle.decode(D, P, syn, w=w, trace_iters=12)
+    b = oracle.decode(D, P, syn, w=np.vstack([w, np.ones((40, D.n_edges))]), trace_iters=12)
+    c = oracle.decode(D, P, syn, w=np.vstack([w, np.repeat(w[-1:], 40, axis=0)]), trace_iters=12)
+    assert np.array_equal(a["trace"], b["trace"], equal_nan=True) and np.array_equal(a["stats"], b["stats"])
+    assert not np.array_equal(a["trace"], c["trace"])
