@@ -83,3 +83,108 @@ class LearnedParams(torch.nn.Module):
     def loss(self, handle, syndromes, errors, shot0: int, gamma_seed: int, objective: int = 0):
         return LearnedLoss.apply(self.edge_weights().contiguous(), self.knots(), handle, syndromes, errors, shot0,
                                  gamma_seed, objective)
+
+
+def train_rows(d_inf, d_train, decoder: dict, steps: int, T: int = 10, lr: float = 3e-3, objective: int = 1,
+               device="cuda", batch: int = 512, select_shots: int = 8192, learned_legs: int = 50,
+               sample_seed: int = 4, select_seed: int = 5):
+    """Train row-tied message weights [T, C] and memory-strength knots on
+    self-sampled shots of d_train (the training DEM: the same detectors and
+    faults as d_inf at another noise strength) with the library's forward and
+    backward kernels and Adam; every 25 steps the current parameters decode
+    select_shots held-out shots of d_inf (stop after the first solution,
+    learned legs 0..learned_legs-1, plain legs after), and the checkpoint with
+    the fewest mean iterations -- clipped at the learned legs' horizon, so a
+    shot left to the plain legs counts once -- is kept; step 0 (unit weights,
+    the uniform interval) is a candidate, so the result never decodes slower
+    than no training on that sample.  decoder: Relay-BP parameters (Params
+    fields).  Returns (wrow, knots, info) with wrow and knots FP32 device
+    tensors for relaybp_set_learned_rows."""
+    import numpy as np
+    import time
+    from . import relaybp as R
+    dev = torch.device(device) if isinstance(device, str) else device
+    E = d_inf.n_edges
+    DECODER = dict(decoder)
+    # T unrolled iterations (default 10: summed over 30 the losses are
+    # dominated by iterations past the map's chaotic horizon, where marginals
+    # grow without bound; over 10 they train steadily)
+    BT = batch
+    # ---- training (untimed) ---------------------------------------------------
+    ht = R.relaybp_build_dem(d_train, R.Params(msg_dtype="f32", **DECODER))
+    row_of = np.repeat(np.arange(d_inf.n_det), np.diff(d_inf.H_indptr))
+    model = LearnedParams(T, E, DECODER["gamma_min"], DECODER["gamma_max"], device=dev, row_of_edge=row_of,
+                          n_rows=d_inf.n_det)
+    opt = torch.optim.Adam(model.parameters(), lr=lr)
+    syn_t = torch.empty((BT, ht.wc), dtype=torch.int32, device=dev)
+    err_t = torch.empty((BT, ht.wv), dtype=torch.int32, device=dev)
+    syn_v = torch.empty((2 * BT, ht.wc), dtype=torch.int32, device=dev)
+    err_v = torch.empty((2 * BT, ht.wv), dtype=torch.int32, device=dev)
+    R.relaybp_sample(ht, sample_seed, 9 * 10**8, 2 * BT, syn_v, None, err_v)     # held-out shots
+    # model selection on the decoding objective: every 25 steps the current
+    # parameters decode held-out shots of the inference DEM (stop after the
+    # first solution, learned legs only); the checkpoint with the fewest mean
+    # iterations is kept.  Step 0 (unit weights, uniform gamma) is a
+    # candidate, so selection never keeps parameters slower than no training.
+    NSEL, SEL0 = select_shots, 8 * 10**8
+    hsel = R.relaybp_build_dem(d_inf, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1)))
+    syn_s = torch.empty((NSEL, hsel.wc), dtype=torch.int32, device=dev)
+    st_s = torch.empty((NSEL, 6), dtype=torch.int32, device=dev)
+    R.relaybp_sample(hsel, select_seed, SEL0, NSEL, syn_s, None, None)
+    t0 = time.perf_counter()
+    hist, sel_hist, best, best_state, best_step = [], [], float("inf"), None, 0
+
+    def held_out():
+        with torch.no_grad():
+            return float(model.loss(ht, syn_v, err_v, 9 * 10**8, 0x5EED, objective))
+
+    def held_out_iterations():
+        with torch.no_grad():
+            w_ = model.w.detach().float().contiguous()          # the handle keeps these pointers:
+            k_ = model.knots().detach().float().contiguous()    # hold them until the decode is read
+            R.relaybp_set_learned_rows(hsel, w_, k_)
+            R.relaybp_set_learned_legs(hsel, learned_legs)
+            R.relaybp_decode_batch(hsel, syn_s, SEL0, NSEL, None, None, st_s)
+            # iterations clipped at the learned legs' horizon: a shot left to
+            # the plain legs counts once, not by its full run
+            horizon = DECODER["pre_iter"] + learned_legs * DECODER["max_iterations"]
+            it = float(st_s[:, 3].clamp(max=horizon).double().mean())
+            del w_, k_
+            return it
+
+    def checkpoint(k):
+        nonlocal best, best_state, best_step
+        hist.append(round(held_out(), 3))
+        it = held_out_iterations()
+        sel_hist.append(round(it, 3))
+        if it < best:
+            best, best_step = it, k
+            best_state = {n: t.detach().clone() for n, t in model.state_dict().items()}
+
+    checkpoint(0)
+    for k in range(steps):
+        R.relaybp_sample(ht, sample_seed, k * BT, BT, syn_t, None, err_t)
+        opt.zero_grad()
+        loss = model.loss(ht, syn_t, err_t, k * BT, 0x5EED, objective)
+        loss.backward()
+        torch.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
+        opt.step()
+        with torch.no_grad():
+            model.w.clamp_(0.0, 2.0)
+        if (k + 1) % 25 == 0 or k == steps - 1:
+            checkpoint(k + 1)
+    model.load_state_dict(best_state)
+    R.relaybp_destroy(hsel)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    wrow = model.w.detach().float().contiguous()
+    knots = model.knots().detach().float().contiguous()
+    info = {"steps": steps, "batch": BT, "shots": steps * BT, "unrolled_iterations": T,
+            "objective": ["cross-entropy against the sampled error", "soft syndrome"][objective],
+            "optimizer": f"Adam {lr:g}, grad-norm clip 1, weights in [0, 2]",
+            "weights": "tied per check row and iteration; unit past the trained horizon", "seconds": train_s,
+            "held_out_loss_every_25_steps": hist, "held_out_mean_iterations_every_25_steps": sel_hist,
+            "selection": f"fewest held-out mean iterations, clipped at the learned legs' horizon ({NSEL} shots of "
+                         f"the inference DEM, stop after the first solution); kept step {best_step}"}
+    R.relaybp_destroy(ht)
+    return wrow, knots, info
