@@ -236,6 +236,40 @@ int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
 int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
                         uint32_t *h_pred_obs, relaybp_shot_stats *h_stats, void *cuda_stream);
 
+/* relaybp_decode_batch that also hands over the shots it leaves unresolved
+ * (no solution in any leg; the paper's outlook, Sec. 7, names them as the
+ * failures that dominate and OSD as their post-processing): each such shot
+ * takes the next slot of *d_flag_count (uint32, caller-zeroed, device
+ * memory; it counts every flagged shot even past max_flagged) and, if the
+ * slot is below max_flagged, writes its index within this batch to
+ * d_flag_idx[slot] (int64) and its final posteriors M (the marginals after
+ * its last iteration, FP64 whatever the storage precision) to
+ * d_flag_post[slot][V].  Slots are taken in completion order, which varies
+ * between runs; their contents do not.  Other arguments as for
+ * relaybp_decode_batch. */
+int relaybp_decode_flagged(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                           uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
+                           int64_t max_flagged, int64_t *d_flag_idx, double *d_flag_post, uint32_t *d_flag_count,
+                           void *cuda_stream);
+
+/* Ordered-statistics decoding (the paper's outlook, Sec. 7) of n shots from
+ * their posteriors: for shot f, the syndrome row d_idx[f] of d_syndromes and
+ * the posteriors d_post[f][V] (as relaybp_decode_flagged writes them).  The
+ * columns of H are ordered by posterior ascending (the most likely error
+ * first; ties by column index); the first rank(H) linearly independent ones
+ * over GF(2) form the information set, on which H e = s is solved (OSD-0).
+ * With lambda > 0 every flip of one or two of the first lambda columns
+ * outside the information set is also tried, keeping the candidate of least
+ * FP64 weight sum_j e_j L0_j (OSD-0 on ties, else the first candidate in
+ * u-major order).  Outputs: d_out_e [n][ceil(V/32)] and d_out_valid[n] = 0
+ * when s is not in the column space of H.  Limits: V <= 16,384 columns,
+ * lambda <= 64, and the C x C elimination state in shared memory (C up to
+ * about 1,300 checks); beyond them RELAYBP_ERR_UNSUPPORTED.  One thread
+ * block per shot; the handle keeps a column-order scratch (allocated on
+ * first use). */
+int relaybp_osd(relaybp_handle *h, const uint32_t *d_syndromes, const double *d_post, const int64_t *d_idx, int64_t n,
+                int32_t lambda, uint32_t *d_out_e, int32_t *d_out_valid, void *cuda_stream);
+
 /* Failure accounting (paper Sec. 7, Outlook, "Improved decoding": failures
  * are either flagged nonconvergences or undetected logical errors).  Adds to
  * d_counters[0] the shots counted, [1] shots that did not converge, [2]

@@ -78,6 +78,17 @@ struct DecodeParamsDev {
     float qscale;               // int8 storage: value of one step
 };
 
+// Flagged nonconvergences (optional output): a shot that ends without a
+// solution takes the next slot of *count and, if slot < max, writes its shot
+// index and its final posteriors M (FP64) -- the soft input of OSD
+// post-processing of exactly the shots Relay-BP leaves unresolved.
+struct FlagOut {
+    long long *idx;             // [max] shot index within the batch
+    double *post;               // [max][V]
+    unsigned int *count;        // shots flagged (may exceed max)
+    long long max;
+};
+
 struct StatsDev {               // mirrors relaybp_shot_stats
     int32_t converged, nsol, legs, iters;
     double weight;
@@ -326,7 +337,7 @@ __device__ __forceinline__ uint32_t sign_word(const uint32_t (&bal)[NB], int w, 
         const uint32_t hi = __byte_perm(at(4 * w + 2), at(4 * w + 3), sel);
         return __byte_perm(lo, hi, 0x5410u);
     }
-    constexpr uint32_t GM = (1u << L) - 1u;
+    constexpr uint32_t GM = (L >= 32) ? 0xffffffffu : ((1u << (L & 31)) - 1u);
     uint32_t word = 0u;
 #pragma unroll
     for (int t = 0; t < P; ++t) word |= ((at(w * P + t) >> (r * L)) & GM) << (t * L);
@@ -462,6 +473,7 @@ struct DecodeJob {
     double *trace;
     int trace_iters;
     uint64_t *times_out;        // [shots][2] device clock (ns) at shot start and retire, or NULL
+    FlagOut flag;               // flagged nonconvergences (flag.post NULL: not written)
 };
 
 constexpr int kMaxJobs = 16;
@@ -491,7 +503,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *gblk = GS ? gstate + (size_t)blockIdx.x * state_stride : nullptr;
 
-    __shared__ long long s_shot;
+    __shared__ long long s_shot, s_fslot;
     __shared__ unsigned long long s_t0;
     __shared__ int s_job, s_nsol, s_have_best, s_copy;
     __shared__ double s_best_w, s_w;
@@ -740,8 +752,13 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                 }
             }
             s_w = w;
+            s_fslot = (!have && J.flag.post) ? (long long)atomicAdd(J.flag.count, 1u) : -1;
         }
         __syncthreads();
+        if (s_fslot >= 0 && s_fslot < J.flag.max) {
+            if (tid == 0) J.flag.idx[s_fslot] = sidx;
+            for (int j = tid; j < V; j += nthr) J.flag.post[s_fslot * V + j] = (double)Prec<S>::ld(M[j], qs);
+        }
         if (pobs_out)
             for (int w = tid; w < WK; w += nthr) pobs_out[sidx * WK + w] = obsacc[w];
         if (stats_out && tid == 0) {
@@ -791,7 +808,7 @@ relay_decode_exact_kernel(DevDEM g, DecodeParamsDev p, ExactPlan plan,
                           const uint32_t *__restrict__ syn_in, uint64_t shot0, int64_t shots,
                           uint32_t *__restrict__ corr_out, uint32_t *__restrict__ pobs_out,
                           StatsDev *__restrict__ stats_out, unsigned long long *__restrict__ work,
-                          double *__restrict__ trace, int trace_iters)
+                          double *__restrict__ trace, int trace_iters, FlagOut flag)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     double *mu = reinterpret_cast<double *>(smem + plan.mu);
@@ -805,7 +822,7 @@ relay_decode_exact_kernel(DevDEM g, DecodeParamsDev p, ExactPlan plan,
     uint32_t *syn = reinterpret_cast<uint32_t *>(smem + plan.syn);
     uint32_t *obsacc = reinterpret_cast<uint32_t *>(smem + plan.obsacc);
 
-    __shared__ long long s_shot;
+    __shared__ long long s_shot, s_fslot;
     __shared__ int s_nsol, s_have_best, s_copy;
     __shared__ double s_best_w, s_w;
 
@@ -985,8 +1002,13 @@ relay_decode_exact_kernel(DevDEM g, DecodeParamsDev p, ExactPlan plan,
                 }
             }
             s_w = w;
+            s_fslot = (!have && flag.post) ? (long long)atomicAdd(flag.count, 1u) : -1;
         }
         __syncthreads();
+        if (s_fslot >= 0 && s_fslot < flag.max) {
+            if (tid == 0) flag.idx[s_fslot] = sidx;
+            for (int j = tid; j < V; j += nthr) flag.post[s_fslot * V + j] = M[j];
+        }
         if (pobs_out)
             for (int w = tid; w < WK; w += nthr) pobs_out[sidx * WK + w] = obsacc[w];
         if (stats_out && tid == 0) {

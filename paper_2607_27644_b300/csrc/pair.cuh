@@ -62,6 +62,7 @@ struct PairJob {
     double *trace;
     int trace_iters;
     uint64_t *times_out;
+    FlagOut flag;               // flagged nonconvergences (flag.post NULL: not written)
 };
 
 __device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
@@ -217,6 +218,7 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
     __shared__ unsigned long long s_t0[2];
     __shared__ int s_leg[2], s_T[2], s_legs[2], s_nsol[2], s_have[2], s_copy[2];
     __shared__ double s_bestw[2], s_w[2];
+    __shared__ long long s_fslot[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = blockDim.x, nwarp = nthr >> 5;
@@ -493,6 +495,7 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
                         }
                     }
                     s_w[s] = w;
+                    s_fslot[s] = (!s_have[s] && J.flag.post) ? (long long)atomicAdd(J.flag.count, 1u) : -1;
                 }
             } else if (newleg[s]) {
                 // a6: next leg -- fresh strengths, marginals carried over
@@ -533,6 +536,12 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
                 const long long sidx = s_sidx[s];
                 if (J.pobs_out)
                     for (int w = tid; w < WK; w += nthr) J.pobs_out[sidx * WK + w] = obsacc(s)[w];
+                const long long fs = s_fslot[s];
+                if (fs >= 0 && fs < J.flag.max) {
+                    if (tid == 0) J.flag.idx[fs] = sidx;
+                    const float *M1 = reinterpret_cast<const float *>(M2) + s;
+                    for (int j = tid; j < V; j += nthr) J.flag.post[fs * V + j] = (double)M1[2 * j];
+                }
                 if (tid == 0) {
                     if (J.stats_out) {
                         StatsDev st;

@@ -20,6 +20,7 @@
 #include "kernels.cuh"
 #include "learned.cuh"
 #include "pair.cuh"
+#include "osd.cuh"
 
 using namespace relaybp;
 
@@ -97,6 +98,8 @@ struct relaybp_handle {
     unsigned long long *d_lwork = nullptr;
     void *d_lgbar = nullptr;
     size_t lgbar_bytes = 0;
+    int32_t *d_osd_order = nullptr;                   // OSD: per-block column order scratch
+    size_t osd_order_bytes = 0;
 };
 
 struct relaybp_group {
@@ -319,6 +322,7 @@ struct JobIO {
     double *trace;
     int trace_iters;
     uint64_t *times = nullptr;
+    FlagOut flag{};
 };
 
 // FP64 in the literal evaluation order when one shot's per-edge messages fit
@@ -342,7 +346,7 @@ int launch_decode_exact(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStr
     CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
     relay_decode_exact_kernel<<<(unsigned)blocks, threads, plan.total, st>>>(
         g, dev_params(h->params), plan, io.syn, io.shot0, io.shots, io.corr, io.pobs, io.stats, sc.work, io.trace,
-        io.trace_iters);
+        io.trace_iters, io.flag);
     CUDA_TRY(cudaGetLastError());
     h->launches += 1;
     return 0;
@@ -385,6 +389,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         J.trace = io[d].trace;
         J.trace_iters = io[d].trace_iters;
         J.times_out = io[d].times;
+        J.flag = io[d].flag;
         tab.start[d] = total;
         total += io[d].shots;
         plan_max = std::max(plan_max, J.plan.total);
@@ -557,6 +562,7 @@ int launch_pair_nb(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     J.trace = io.trace;
     J.trace_iters = io.trace_iters;
     J.times_out = io.times;
+    J.flag = io.flag;
     const int warps = std::min(h->pair_warps > 0 ? h->pair_warps : pair_warps_heuristic(h),
                                pair_max_threads(NB) / 32);
     const int threads = 32 * warps;
@@ -1152,6 +1158,76 @@ int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
     return decode_single(h, h->scratch, io, static_cast<cudaStream_t>(cuda_stream), false);
 }
 
+int relaybp_decode_flagged(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                           uint32_t *d_corrections, uint32_t *d_pred_obs, relaybp_shot_stats *d_stats,
+                           int64_t max_flagged, int64_t *d_flag_idx, double *d_flag_post, uint32_t *d_flag_count,
+                           void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
+    if (shots < 0 || max_flagged < 0) return fail(RELAYBP_ERR_INVALID, "negative size");
+    if (shots == 0) return 0;
+    if (!d_syndromes || !d_flag_count || (max_flagged > 0 && (!d_flag_idx || !d_flag_post)))
+        return fail(RELAYBP_ERR_INVALID, "null pointer");
+    JobIO io{d_syndromes, shot0, shots, d_corrections, d_pred_obs, reinterpret_cast<StatsDev *>(d_stats), nullptr, 0};
+    io.flag = FlagOut{reinterpret_cast<long long *>(d_flag_idx), d_flag_post, d_flag_count, max_flagged};
+    return decode_single(h, h->scratch, io, static_cast<cudaStream_t>(cuda_stream), false);
+}
+
+int relaybp_osd(relaybp_handle *h, const uint32_t *d_syndromes, const double *d_post, const int64_t *d_idx, int64_t n,
+                int32_t lambda, uint32_t *d_out_e, int32_t *d_out_valid, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
+    if (n < 0) return fail(RELAYBP_ERR_INVALID, "negative shot count");
+    if (lambda < 0 || lambda > kOsdMaxLambda) return fail(RELAYBP_ERR_INVALID, "lambda must be in 0..%d", kOsdMaxLambda);
+    if (n == 0) return 0;
+    if (!d_syndromes || !d_post || !d_idx || !d_out_e || !d_out_valid) return fail(RELAYBP_ERR_INVALID, "null pointer");
+    const DevDEM &g = h->dem;
+    if (g.V > kOsdSortMax)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "OSD sorts at most %d columns in shared memory (DEM has %d)", kOsdSortMax,
+                    g.V);
+    int NP = 1;
+    while (NP < g.V) NP <<= 1;
+    const size_t WC = (size_t)words(g.C), WV = (size_t)words(g.V);
+    const size_t sort_bytes = 12 * (size_t)NP;
+    const size_t elim_bytes = 4 * ((size_t)g.C * WC + 2 * WC + (size_t)g.C + WV + kOsdMaxLambda +
+                                   (size_t)kOsdMaxLambda * WC);
+    const size_t dyn = std::max(sort_bytes, elim_bytes);
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (dyn + 1024 > (size_t)maxsm)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "OSD state (%zu bytes for %d checks) exceeds shared memory", dyn, g.C);
+    const int64_t blocks = std::min<int64_t>(n, h->num_sms);
+    const size_t need = (size_t)blocks * g.V * sizeof(int32_t);
+    if (h->osd_order_bytes < need) {
+        cudaFree(h->d_osd_order);
+        h->d_osd_order = nullptr;
+        h->osd_order_bytes = 0;
+        CUDA_TRY(cudaMalloc(&h->d_osd_order, need));
+        h->osd_order_bytes = need;
+    }
+    OsdJob J{};
+    J.g = g;
+    J.syn = d_syndromes;
+    J.post = d_post;
+    J.idx = reinterpret_cast<const long long *>(d_idx);
+    J.n = n;
+    J.lambda = lambda;
+    J.NP = NP;
+    J.out_e = d_out_e;
+    J.out_valid = d_out_valid;
+    J.order = h->d_osd_order;
+    CUDA_TRY(cudaFuncSetAttribute(osd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    const int threads = 1024;
+    osd_kernel<<<(unsigned)blocks, threads, dyn, static_cast<cudaStream_t>(cuda_stream)>>>(J);
+    CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+    return 0;
+}
+
 int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
                         uint32_t *h_pred_obs, relaybp_shot_stats *h_stats, void *cuda_stream)
 {
@@ -1388,6 +1464,7 @@ int relaybp_destroy(relaybp_handle *h)
     scratch_free(h->scratch);
     cudaFree(h->d_lwork);
     cudaFree(h->d_lgbar);
+    cudaFree(h->d_osd_order);
     cudaFree(h->d_stage_syn);
     cudaFree(h->d_stage_pobs);
     cudaFree(h->d_stage_stats);

@@ -63,6 +63,8 @@ def _load() -> ctypes.CDLL:
         "relaybp_decode_trace": ([P, P, U64, I64, I32, P, P, P], ctypes.c_int),
         "relaybp_decode_batch_noalloc": ([P, P, U64, I64, P, P, P, P], ctypes.c_int),
         "relaybp_decode_host": ([P, P, U64, I64, P, P, P], ctypes.c_int),
+        "relaybp_decode_flagged": ([P, P, U64, I64, P, P, P, I64, P, P, P, P], ctypes.c_int),
+        "relaybp_osd": ([P, P, P, P, I64, I32, P, P, P], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
         "relaybp_learned_tape_bytes": ([P, I32, I32, I64], I64),
@@ -89,7 +91,7 @@ _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows",
             "relaybp_set_learned_legs", "relaybp_set_pair_kernel", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
-            "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_count_failures", "relaybp_launch_count",
+            "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_decode_flagged", "relaybp_osd", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
             "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
@@ -251,6 +253,22 @@ def relaybp_decode_timed(h: Handle, d_syndromes, shot0: int, shots: int, d_times
     into d_times [shots][2] (int64 tensor, nanoseconds)."""
     _check(_lib.relaybp_decode_timed(h.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections), _ptr(d_pred_obs),
                                      _ptr(d_stats), _ptr(d_times), _stream(stream)), "relaybp_decode_timed")
+
+
+def relaybp_decode_flagged(h: Handle, d_syndromes, shot0: int, shots: int, max_flagged: int, d_flag_idx, d_flag_post,
+                           d_flag_count, d_corrections=None, d_pred_obs=None, d_stats=None, stream=None):
+    """relaybp_decode_batch plus the unresolved shots' indices (int64) and final
+    posteriors (float64 [max_flagged, V]); d_flag_count (int32 [1], zeroed)
+    counts them."""
+    _check(_lib.relaybp_decode_flagged(h.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections), _ptr(d_pred_obs),
+                                       _ptr(d_stats), max_flagged, _ptr(d_flag_idx), _ptr(d_flag_post),
+                                       _ptr(d_flag_count), _stream(stream)), "relaybp_decode_flagged")
+
+
+def relaybp_osd(h: Handle, d_syndromes, d_post, d_idx, n: int, lam: int, d_out_e, d_out_valid, stream=None):
+    """OSD-lam of n shots (syndrome rows d_idx of d_syndromes, posteriors d_post)."""
+    _check(_lib.relaybp_osd(h.ptr, _ptr(d_syndromes), _ptr(d_post), _ptr(d_idx), n, lam, _ptr(d_out_e),
+                            _ptr(d_out_valid), _stream(stream)), "relaybp_osd")
 
 
 def relaybp_decode_batch_noalloc(h: Handle, d_syndromes, shot0: int, shots: int, d_corrections=None,
