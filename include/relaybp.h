@@ -105,6 +105,7 @@ typedef struct {
 
 typedef struct relaybp_handle relaybp_handle;
 typedef struct relaybp_group relaybp_group;
+typedef struct relaybp_spa relaybp_spa;
 
 /* Build a decoder for one DEM on the current CUDA device.
  * H: detector x fault check matrix (C rows, V columns); every row has 0 or at
@@ -376,6 +377,36 @@ int relaybp_probe_smem_read(int32_t reps, float *d_sink, double *bytes_read, voi
  * general kernel.  RELAYBP_ERR_UNSUPPORTED when enable = 1 and the DEM's
  * rows are too long; RELAYBP_ERR_INVALID for warps outside 0..32. */
 int relaybp_set_pair_kernel(relaybp_handle *h, int32_t enable, int32_t warps);
+
+/* Classical channel coding (paper Sec. 6.2): BPSK over AWGN and flooding
+ * sum-product belief propagation for classical codes such as the ZSZ-2BGA
+ * seed codes of Table 2.
+ *   relaybp_spa_create: copy a parity-check matrix H (CSR, host memory,
+ *     1..4096 columns) to the current device.
+ *   relaybp_spa_llr: channel LLRs d_llr [shots][n] (FP64 or FP32 per
+ *     `precision`, RELAYBP_MSG_F64 / _F32) of frames shot0.. at noise
+ *     deviation sigma: bit c_i is sent as (-1)^{c_i} (d_codewords
+ *     [shots][ceil(n/32)], or NULL for the all-zero codeword), y_i = x_i +
+ *     sigma z_i with z_i the Box-Muller transform of words 2i, 2i+1 of Philox
+ *     stream 2 under key `seed` (u = (w + 0.5) / 2^32, z = sqrt(-2 ln u1)
+ *     cos(2 pi u2)), L_i = clip(2 y_i / sigma^2, +-llr_max).  The Gaussian
+ *     is computed in FP64 and rounded to `precision`.
+ *   relaybp_spa_decode: at most max_iter flooding iterations per frame, the
+ *     check update nu = prod sgn(mu) * phi(sum phi(|mu|)) over the row's other
+ *     entries, phi(x) = -log tanh(x / 2), every message clipped to
+ *     +-llr_max; with early_stop a frame stops at the first iteration whose
+ *     hard decision [M < 0] satisfies every check.  Outputs: d_bits
+ *     [shots][ceil(n/32)] hard decisions, d_iters[shots], d_valid[shots]
+ *     (1 if the decision satisfies every check), d_post [shots][n] final
+ *     posteriors (may be NULL).  One warp per frame.
+ * Errors as elsewhere; sizes beyond the limits: RELAYBP_ERR_UNSUPPORTED. */
+int relaybp_spa_create(const relaybp_csr *H, relaybp_spa **out);
+int relaybp_spa_llr(relaybp_spa *h, int32_t precision, const uint32_t *d_codewords, double sigma, double llr_max,
+                    uint64_t seed, uint64_t shot0, int64_t shots, void *d_llr, void *cuda_stream);
+int relaybp_spa_decode(relaybp_spa *h, int32_t precision, const void *d_llr, int64_t shots, int32_t max_iter,
+                       double llr_max, int32_t early_stop, uint32_t *d_bits, int32_t *d_iters, int32_t *d_valid,
+                       void *d_post, void *cuda_stream);
+int relaybp_spa_destroy(relaybp_spa *h);
 
 /* Free the handle and every device allocation it owns (synchronises its
  * device first).  NULL is accepted. */

@@ -21,6 +21,7 @@
 #include "learned.cuh"
 #include "pair.cuh"
 #include "osd.cuh"
+#include "spa.cuh"
 
 using namespace relaybp;
 
@@ -1225,6 +1226,141 @@ int relaybp_osd(relaybp_handle *h, const uint32_t *d_syndromes, const double *d_
     osd_kernel<<<(unsigned)blocks, threads, dyn, static_cast<cudaStream_t>(cuda_stream)>>>(J);
     CUDA_TRY(cudaGetLastError());
     h->launches += 1;
+    return 0;
+}
+
+}  // extern "C"
+
+struct relaybp_spa {
+    int device = 0, num_sms = 0;
+    SpaCode code{};
+    std::vector<void *> allocs;
+};
+
+namespace {
+template <typename T>
+int spa_upload(relaybp_spa *h, const std::vector<T> &v, const T **dst)
+{
+    void *p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, std::max<size_t>(1, v.size()) * sizeof(T)));
+    h->allocs.push_back(p);
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = static_cast<const T *>(p);
+    return 0;
+}
+int spa_check(const relaybp_spa *h, int32_t precision)
+{
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    int cur = -1;
+    CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != h->device) return fail(RELAYBP_ERR_INVALID, "the handle's device %d is not current", h->device);
+    if (precision != RELAYBP_MSG_F64 && precision != RELAYBP_MSG_F32)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "sum-product runs in FP64 or FP32");
+    return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int relaybp_spa_create(const relaybp_csr *H, relaybp_spa **out)
+{
+    g_err.clear();
+    if (!out) return fail(RELAYBP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (int rc = check_csr(H, "H")) return rc;
+    const int32_t m = H->rows, n = H->cols;
+    const int64_t E = H->indptr[m];
+    if (n < 1 || n > 4096 || E > (int64_t)1 << 20)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "sum-product codes of 1..4096 bits (one warp per frame)");
+    relaybp_spa *h = new relaybp_spa();
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (ce != cudaSuccess) { delete h; return fail(RELAYBP_ERR_CUDA, "device query: %s", cudaGetErrorString(ce)); }
+    std::vector<int32_t> rptr(H->indptr, H->indptr + m + 1), rvar(H->indices, H->indices + E);
+    std::vector<int32_t> cptr(n + 1, 0), cedge(E), fillc(n, 0);
+    for (int64_t e = 0; e < E; ++e) cptr[rvar[e] + 1]++;
+    for (int32_t j = 0; j < n; ++j) cptr[j + 1] += cptr[j];
+    for (int32_t i = 0; i < m; ++i)
+        for (int32_t e = rptr[i]; e < rptr[i + 1]; ++e) cedge[cptr[rvar[e]] + fillc[rvar[e]]++] = e;
+    h->code.m = m;
+    h->code.n = n;
+    h->code.E = E;
+    int rc = 0;
+    if ((rc = spa_upload(h, rptr, &h->code.rptr)) || (rc = spa_upload(h, rvar, &h->code.rvar)) ||
+        (rc = spa_upload(h, cptr, &h->code.cptr)) || (rc = spa_upload(h, cedge, &h->code.cedge))) {
+        relaybp_spa_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return 0;
+}
+
+int relaybp_spa_llr(relaybp_spa *h, int32_t precision, const uint32_t *d_codewords, double sigma, double llr_max,
+                    uint64_t seed, uint64_t shot0, int64_t shots, void *d_llr, void *cuda_stream)
+{
+    g_err.clear();
+    if (int rc = spa_check(h, precision)) return rc;
+    if (shots < 0 || !(sigma > 0.0) || !(llr_max > 0.0)) return fail(RELAYBP_ERR_INVALID, "bad size or noise level");
+    if (shots == 0) return 0;
+    if (!d_llr) return fail(RELAYBP_ERR_INVALID, "d_llr is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int threads = 256;
+    const int64_t total = shots * (int64_t)h->code.n;
+    const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)h->num_sms * 16);
+    if (precision == RELAYBP_MSG_F64)
+        awgn_llr_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(h->code.n, d_codewords, sigma, llr_max, seed,
+                                                                       shot0, shots, static_cast<double *>(d_llr));
+    else
+        awgn_llr_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(h->code.n, d_codewords, sigma, llr_max, seed,
+                                                                      shot0, shots, static_cast<float *>(d_llr));
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int relaybp_spa_decode(relaybp_spa *h, int32_t precision, const void *d_llr, int64_t shots, int32_t max_iter,
+                       double llr_max, int32_t early_stop, uint32_t *d_bits, int32_t *d_iters, int32_t *d_valid,
+                       void *d_post, void *cuda_stream)
+{
+    g_err.clear();
+    if (int rc = spa_check(h, precision)) return rc;
+    if (shots < 0 || max_iter < 1 || !(llr_max > 0.0)) return fail(RELAYBP_ERR_INVALID, "bad size or limit");
+    if (shots == 0) return 0;
+    if (!d_llr || !d_bits || !d_iters || !d_valid) return fail(RELAYBP_ERR_INVALID, "null pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t tsz = precision == RELAYBP_MSG_F64 ? 8 : 4;
+    const size_t per = (2 * (size_t)h->code.E * tsz + 4 * (size_t)words(h->code.n) + 15) & ~(size_t)15;
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    int warps = 8;
+    while (warps > 1 && per * warps > (size_t)maxsm) warps >>= 1;
+    if (per * warps > (size_t)maxsm) return fail(RELAYBP_ERR_UNSUPPORTED, "one frame's messages exceed shared memory");
+    const size_t dyn = per * warps;
+    const int64_t blocks = std::min<int64_t>((shots + warps - 1) / warps, (int64_t)h->num_sms * 8);
+    if (precision == RELAYBP_MSG_F64) {
+        CUDA_TRY(cudaFuncSetAttribute(spa_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        spa_kernel<double><<<(unsigned)blocks, 32 * warps, dyn, st>>>(h->code, static_cast<const double *>(d_llr), shots,
+                                                                      max_iter, llr_max, early_stop, d_bits, d_iters,
+                                                                      d_valid, static_cast<double *>(d_post));
+    } else {
+        CUDA_TRY(cudaFuncSetAttribute(spa_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        spa_kernel<float><<<(unsigned)blocks, 32 * warps, dyn, st>>>(h->code, static_cast<const float *>(d_llr), shots,
+                                                                     max_iter, (float)llr_max, early_stop, d_bits,
+                                                                     d_iters, d_valid, static_cast<float *>(d_post));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int relaybp_spa_destroy(relaybp_spa *h)
+{
+    if (!h) return 0;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (void *p : h->allocs) cudaFree(p);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete h;
     return 0;
 }
 

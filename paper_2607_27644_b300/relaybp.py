@@ -65,6 +65,10 @@ def _load() -> ctypes.CDLL:
         "relaybp_decode_host": ([P, P, U64, I64, P, P, P], ctypes.c_int),
         "relaybp_decode_flagged": ([P, P, U64, I64, P, P, P, I64, P, P, P, P], ctypes.c_int),
         "relaybp_osd": ([P, P, P, P, I64, I32, P, P, P], ctypes.c_int),
+        "relaybp_spa_create": ([ctypes.POINTER(relaybp_csr), ctypes.POINTER(P)], ctypes.c_int),
+        "relaybp_spa_llr": ([P, I32, P, ctypes.c_double, ctypes.c_double, U64, U64, I64, P, P], ctypes.c_int),
+        "relaybp_spa_decode": ([P, I32, P, I64, I32, ctypes.c_double, I32, P, P, P, P, P], ctypes.c_int),
+        "relaybp_spa_destroy": ([P], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
         "relaybp_learned_tape_bytes": ([P, I32, I32, I64], I64),
@@ -91,7 +95,8 @@ _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows",
             "relaybp_set_learned_legs", "relaybp_set_pair_kernel", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
-            "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_decode_flagged", "relaybp_osd", "relaybp_count_failures", "relaybp_launch_count",
+            "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_decode_flagged", "relaybp_osd", "relaybp_spa_create", "relaybp_spa_llr",
+            "relaybp_spa_decode", "relaybp_spa_destroy", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
             "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
@@ -269,6 +274,50 @@ def relaybp_osd(h: Handle, d_syndromes, d_post, d_idx, n: int, lam: int, d_out_e
     """OSD-lam of n shots (syndrome rows d_idx of d_syndromes, posteriors d_post)."""
     _check(_lib.relaybp_osd(h.ptr, _ptr(d_syndromes), _ptr(d_post), _ptr(d_idx), n, lam, _ptr(d_out_e),
                             _ptr(d_out_valid), _stream(stream)), "relaybp_osd")
+
+
+class Spa:
+    """A classical code on the device for BPSK-AWGN sum-product decoding."""
+
+    def __init__(self, indptr, indices, m: int, n: int):
+        ip = np.ascontiguousarray(indptr, dtype=np.int32)
+        ix = np.ascontiguousarray(indices, dtype=np.int32)
+        H = relaybp_csr(m, n, _ptr(ip), _ptr(ix))
+        out = ctypes.c_void_p()
+        _check(_lib.relaybp_spa_create(ctypes.byref(H), ctypes.byref(out)), "relaybp_spa_create")
+        self.ptr, self.m, self.n = out, m, n
+
+    def llr(self, sigma: float, seed: int, shot0: int, shots: int, d_llr, llr_max: float = 20.0, d_codewords=None,
+            stream=None):
+        _check(_lib.relaybp_spa_llr(self.ptr, _prec(d_llr.dtype), _ptr(d_codewords), sigma, llr_max, seed, shot0, shots,
+                                    _ptr(d_llr), _stream(stream)), "relaybp_spa_llr")
+
+    def decode(self, d_llr, shots: int, d_bits, d_iters, d_valid, d_post=None, max_iter: int = 100,
+               llr_max: float = 20.0, early_stop: bool = True, stream=None):
+        _check(_lib.relaybp_spa_decode(self.ptr, _prec(d_llr.dtype), _ptr(d_llr), shots, max_iter, llr_max,
+                                       int(early_stop), _ptr(d_bits), _ptr(d_iters), _ptr(d_valid), _ptr(d_post),
+                                       _stream(stream)), "relaybp_spa_decode")
+
+    def destroy(self):
+        if self.ptr:
+            _lib.relaybp_spa_destroy(self.ptr)
+            self.ptr = None
+
+
+def relaybp_spa_create(indptr, indices, m: int, n: int) -> Spa:
+    return Spa(indptr, indices, m, n)
+
+
+def relaybp_spa_llr(spa: Spa, *a, **k):
+    spa.llr(*a, **k)
+
+
+def relaybp_spa_decode(spa: Spa, *a, **k):
+    spa.decode(*a, **k)
+
+
+def relaybp_spa_destroy(spa: Spa):
+    spa.destroy()
 
 
 def relaybp_decode_batch_noalloc(h: Handle, d_syndromes, shot0: int, shots: int, d_corrections=None,
