@@ -106,6 +106,7 @@ typedef struct {
 typedef struct relaybp_handle relaybp_handle;
 typedef struct relaybp_group relaybp_group;
 typedef struct relaybp_spa relaybp_spa;
+typedef struct relaybp_windows relaybp_windows;
 
 /* Build a decoder for one DEM on the current CUDA device.
  * H: detector x fault check matrix (C rows, V columns); every row has 0 or at
@@ -407,6 +408,50 @@ int relaybp_spa_decode(relaybp_spa *h, int32_t precision, const void *d_llr, int
                        double llr_max, int32_t early_stop, uint32_t *d_bits, int32_t *d_iters, int32_t *d_valid,
                        void *d_post, void *cuda_stream);
 int relaybp_spa_destroy(relaybp_spa *h);
+
+/* Sliding-window decoding with a commit region of one round (Sec. 6.1,
+ * decoding-latency paragraph: a real-time decoder decodes about d rounds of
+ * syndromes once per syndrome-extraction round; the paper names the scheme
+ * and does not spell the steps out).  The reading implemented:
+ *   - each detector i has a round det_round[i] >= 0 (R = 1 + the largest; a
+ *     memory experiment's final data-readout detectors form the last round),
+ *     each fault column the least round of its detectors (a column with no
+ *     detector is never decoded: its bit of e^ stays 0);
+ *   - window t = 0, 1, ... holds the rows of rounds [t, t + window) and the
+ *     columns of those rounds; it decodes the residual syndrome r restricted
+ *     to its rows with an ordinary handle built from that restriction of H
+ *     (same priors, same parameters, same global shot indices -- so each
+ *     window draws the memory strengths a whole-DEM decode of that
+ *     restriction would);
+ *   - the columns of round t are committed (all of the window's columns in
+ *     the last window, the first with t + window >= R): their bits join e^
+ *     and their detector sets are XORed into r, which clears round t whenever
+ *     the window converged.
+ * max(R - window, 0) + 1 windows; window >= R is one whole-DEM decode.
+ *
+ * relaybp_windows_create: H, priors, obs, params as relaybp_build (the whole
+ *   DEM, host memory); det_round [C] host.  Builds every window's handle now
+ *   (RELAYBP_ERR_INVALID naming the window if a window has no row or no
+ *   column, or if a row of a window keeps a single entry).
+ * relaybp_windows_decode: d_syndromes [shots][ceil(C/32)] device; shot indices
+ *   shot0 .. shot0 + shots - 1.  Outputs (device, each may be NULL):
+ *   d_corrections [shots][ceil(V/32)] the committed e^; d_pred_obs
+ *   [shots][ceil(K/32)] O e^; d_residual [shots][ceil(C/32)] H e^ + s (zero
+ *   when every window converged); d_converged [shots] 1 iff every window
+ *   converged.  Per window: one gather launch, the window's decode launch(es)
+ *   and one commit launch, all on cuda_stream; scratch grows on demand.
+ * relaybp_windows_handle: borrow window t's handle (owned by the windows
+ *   object), e.g. to choose its kernel; relaybp_windows_info: window and
+ *   round counts. */
+int relaybp_windows_create(const relaybp_csr *H, const double *priors, const relaybp_csr *obs,
+                           const int32_t *det_round, int32_t window, const relaybp_params *params,
+                           relaybp_windows **out);
+int relaybp_windows_info(const relaybp_windows *w, int32_t *n_windows, int32_t *n_rounds);
+int relaybp_windows_handle(relaybp_windows *w, int32_t t, relaybp_handle **out);
+int relaybp_windows_decode(relaybp_windows *w, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                           uint32_t *d_corrections, uint32_t *d_pred_obs, uint32_t *d_residual,
+                           int32_t *d_converged, void *cuda_stream);
+int relaybp_windows_destroy(relaybp_windows *w);
 
 /* Free the handle and every device allocation it owns (synchronises its
  * device first).  NULL is accepted. */

@@ -22,6 +22,7 @@
 #include "pair.cuh"
 #include "osd.cuh"
 #include "spa.cuh"
+#include "windows.cuh"
 
 using namespace relaybp;
 
@@ -326,16 +327,16 @@ struct JobIO {
     FlagOut flag{};
 };
 
-// FP64 in the literal evaluation order when one shot's per-edge messages fit
-// in shared memory (at most half of it, so that two shots share an SM);
-// returns 1 if the DEM is too large for this kernel.
+// FP64 in the literal evaluation order whenever one shot's per-edge messages
+// fit in one block's shared memory (FP64 is the parity form: evaluation order
+// before occupancy); returns 1 if the DEM is too large for this kernel.
 int launch_decode_exact(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st)
 {
     const DevDEM &g = h->dem;
     ExactPlan plan = make_exact_plan(g);
     int maxsm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (plan.total > maxsm / 2) return 1;
+    if (plan.total > maxsm) return 1;
     CUDA_TRY(cudaFuncSetAttribute(relay_decode_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total));
     const int threads = g.E <= 4096 ? 128 : 256;
     int per_sm = 0;
@@ -1364,6 +1365,280 @@ int relaybp_spa_destroy(relaybp_spa *h)
     return 0;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sliding-window decoding (relaybp_windows_*): one ordinary handle per window,
+// built from the DEM restricted to the window's rows and columns, and the
+// gather / commit / observable kernels of windows.cuh between them.
+// ---------------------------------------------------------------------------
+struct relaybp_windows {
+    int device = 0, num_sms = 0;
+    int32_t C = 0, V = 0, K = 0, R = 0, w = 0;
+    std::vector<relaybp_handle *> hs;                  // window t's decoder
+    std::vector<int32_t> nrows, ncommit;               // per window
+    std::vector<const int32_t *> rows, clocal, cfull;  // device: window rows, committed columns
+    const int32_t *cptr = nullptr, *crow = nullptr;    // device: H by columns
+    const int32_t *optr = nullptr, *oidx = nullptr;    // device: O by columns
+    std::vector<void *> allocs;
+    // scratch grown on demand
+    uint32_t *wsyn = nullptr, *wcorr = nullptr, *resid = nullptr, *corr = nullptr;
+    StatsDev *wstats = nullptr;
+    int64_t cap = 0;
+    int wcw_max = 0, wvw_max = 0;
+};
+
+namespace {
+template <typename T>
+int win_upload(relaybp_windows *W, const std::vector<T> &v, const T **dst)
+{
+    void *p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, std::max<size_t>(1, v.size()) * sizeof(T)));
+    W->allocs.push_back(p);
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = static_cast<const T *>(p);
+    return 0;
+}
+
+int win_build(relaybp_windows *W, const relaybp_csr *H, const double *priors, const relaybp_csr *obs,
+              const int32_t *det_round, const relaybp_params *params)
+{
+    const int32_t C = W->C, V = W->V, R = W->R, w = W->w;
+    const int64_t E = H->indptr[C];
+    // column rounds: the least round of the column's detectors (R + 1: none)
+    std::vector<int32_t> col_round(V, R + 1), cptr(V + 1, 0), crow(E), fill(V, 0);
+    for (int32_t i = 0; i < C; ++i)
+        for (int32_t e = H->indptr[i]; e < H->indptr[i + 1]; ++e) {
+            const int32_t j = H->indices[e];
+            col_round[j] = std::min(col_round[j], det_round[i]);
+            cptr[j + 1]++;
+        }
+    for (int32_t j = 0; j < V; ++j) cptr[j + 1] += cptr[j];
+    for (int32_t i = 0; i < C; ++i)
+        for (int32_t e = H->indptr[i]; e < H->indptr[i + 1]; ++e) {
+            const int32_t j = H->indices[e];
+            crow[cptr[j] + fill[j]++] = i;
+        }
+    std::vector<int32_t> optr(V + 1, 0), oidx;
+    if (obs) {
+        const int64_t EO = obs->indptr[obs->rows];
+        oidx.resize(EO);
+        std::vector<int32_t> of(V, 0);
+        for (int64_t e = 0; e < EO; ++e) optr[obs->indices[e] + 1]++;
+        for (int32_t j = 0; j < V; ++j) optr[j + 1] += optr[j];
+        for (int32_t k = 0; k < obs->rows; ++k)
+            for (int32_t e = obs->indptr[k]; e < obs->indptr[k + 1]; ++e) {
+                const int32_t j = obs->indices[e];
+                oidx[optr[j] + of[j]++] = k;
+            }
+    }
+    int rc = 0;
+    if ((rc = win_upload(W, cptr, &W->cptr)) || (rc = win_upload(W, crow, &W->crow)) ||
+        (rc = win_upload(W, optr, &W->optr)) || (rc = win_upload(W, oidx, &W->oidx)))
+        return rc;
+    std::vector<int32_t> local(V, -1);
+    for (int32_t t = 0;; ++t) {
+        const bool last = t + w >= R;
+        std::vector<int32_t> rows, cols;
+        for (int32_t i = 0; i < C; ++i)
+            if (det_round[i] >= t && det_round[i] < t + w) rows.push_back(i);
+        for (int32_t j = 0; j < V; ++j)
+            if (col_round[j] >= t && col_round[j] < t + w) cols.push_back(j);
+        if (rows.empty() || cols.empty())
+            return fail(RELAYBP_ERR_INVALID, "window %d (rounds %d..%d) has no %s", t, t, t + w - 1,
+                        rows.empty() ? "detector" : "fault column");
+        std::fill(local.begin(), local.end(), -1);
+        for (size_t k = 0; k < cols.size(); ++k) local[cols[k]] = (int32_t)k;
+        // the restriction: the window's rows, in order, over its columns, in order
+        std::vector<int32_t> sp(1, 0), si;
+        for (int32_t i : rows) {
+            for (int32_t e = H->indptr[i]; e < H->indptr[i + 1]; ++e)
+                if (local[H->indices[e]] >= 0) si.push_back(local[H->indices[e]]);
+            sp.push_back((int32_t)si.size());
+        }
+        std::vector<double> sprior(cols.size());
+        for (size_t k = 0; k < cols.size(); ++k) sprior[k] = priors[cols[k]];
+        relaybp_csr sub{(int32_t)rows.size(), (int32_t)cols.size(), sp.data(), si.data()};
+        relaybp_handle *h = nullptr;
+        if ((rc = relaybp_build(&sub, sprior.data(), nullptr, params, &h))) {
+            const std::string msg = g_err;
+            return fail(rc, "window %d (rounds %d..%d): %s", t, t, t + w - 1, msg.c_str());
+        }
+        W->hs.push_back(h);
+        std::vector<int32_t> cl, cf;
+        for (size_t k = 0; k < cols.size(); ++k)
+            if (last || col_round[cols[k]] == t) {
+                cl.push_back((int32_t)k);
+                cf.push_back(cols[k]);
+            }
+        const int32_t *drows = nullptr, *dcl = nullptr, *dcf = nullptr;
+        if ((rc = win_upload(W, rows, &drows)) || (rc = win_upload(W, cl, &dcl)) || (rc = win_upload(W, cf, &dcf)))
+            return rc;
+        W->rows.push_back(drows);
+        W->clocal.push_back(dcl);
+        W->cfull.push_back(dcf);
+        W->nrows.push_back((int32_t)rows.size());
+        W->ncommit.push_back((int32_t)cl.size());
+        W->wcw_max = std::max(W->wcw_max, words((int64_t)rows.size()));
+        W->wvw_max = std::max(W->wvw_max, words((int64_t)cols.size()));
+        if (last) break;
+    }
+    return 0;
+}
+
+int win_check(const relaybp_windows *W)
+{
+    if (!W) return fail(RELAYBP_ERR_INVALID, "windows handle is NULL");
+    int cur = -1;
+    CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != W->device) return fail(RELAYBP_ERR_INVALID, "the windows' device %d is not current", W->device);
+    return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int relaybp_windows_create(const relaybp_csr *H, const double *priors, const relaybp_csr *obs,
+                           const int32_t *det_round, int32_t window, const relaybp_params *params,
+                           relaybp_windows **out)
+{
+    g_err.clear();
+    if (!out) return fail(RELAYBP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (int rc = check_csr(H, "H")) return rc;
+    if (obs) {
+        if (int rc = check_csr(obs, "obs")) return rc;
+        if (obs->cols != H->cols) return fail(RELAYBP_ERR_INVALID, "obs has %d columns, H has %d", obs->cols, H->cols);
+    }
+    if (!priors || !det_round) return fail(RELAYBP_ERR_INVALID, "priors or det_round is NULL");
+    if (window < 1) return fail(RELAYBP_ERR_INVALID, "window = %d rounds; need >= 1", window);
+    if (int rc = check_params(params)) return rc;
+    int32_t R = 0;
+    for (int32_t i = 0; i < H->rows; ++i) {
+        if (det_round[i] < 0) return fail(RELAYBP_ERR_INVALID, "detector %d has round %d < 0", i, det_round[i]);
+        R = std::max(R, det_round[i] + 1);
+    }
+    if (R == 0) return fail(RELAYBP_ERR_INVALID, "no detectors");
+    relaybp_windows *W = new relaybp_windows();
+    W->C = H->rows;
+    W->V = H->cols;
+    W->K = obs ? obs->rows : 0;
+    W->R = R;
+    W->w = window;
+    cudaError_t ce = cudaGetDevice(&W->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&W->num_sms, cudaDevAttrMultiProcessorCount, W->device);
+    if (ce != cudaSuccess) { delete W; return fail(RELAYBP_ERR_CUDA, "device query: %s", cudaGetErrorString(ce)); }
+    if (int rc = win_build(W, H, priors, obs, det_round, params)) {
+        const std::string msg = g_err;
+        relaybp_windows_destroy(W);
+        return fail(rc, "%s", msg.c_str());
+    }
+    *out = W;
+    return 0;
+}
+
+int relaybp_windows_info(const relaybp_windows *W, int32_t *n_windows, int32_t *n_rounds)
+{
+    if (!W) return fail(RELAYBP_ERR_INVALID, "windows handle is NULL");
+    if (n_windows) *n_windows = (int32_t)W->hs.size();
+    if (n_rounds) *n_rounds = W->R;
+    return 0;
+}
+
+int relaybp_windows_handle(relaybp_windows *W, int32_t t, relaybp_handle **out)
+{
+    if (!W || !out) return fail(RELAYBP_ERR_INVALID, "NULL argument");
+    if (t < 0 || t >= (int32_t)W->hs.size())
+        return fail(RELAYBP_ERR_INVALID, "window %d of %d", t, (int)W->hs.size());
+    *out = W->hs[t];
+    return 0;
+}
+
+int relaybp_windows_decode(relaybp_windows *W, const uint32_t *d_syndromes, uint64_t shot0, int64_t shots,
+                           uint32_t *d_corrections, uint32_t *d_pred_obs, uint32_t *d_residual,
+                           int32_t *d_converged, void *cuda_stream)
+{
+    g_err.clear();
+    if (int rc = win_check(W)) return rc;
+    if (shots < 0) return fail(RELAYBP_ERR_INVALID, "shots < 0");
+    if (shots == 0) return 0;
+    if (!d_syndromes) return fail(RELAYBP_ERR_INVALID, "d_syndromes is NULL");
+    if (d_pred_obs && W->K == 0) return fail(RELAYBP_ERR_INVALID, "d_pred_obs given but the DEM has no observables");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int wcf = words(W->C), wvf = words(W->V), wk = words(W->K);
+    if (shots > W->cap) {
+        CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(W->wsyn);
+        cudaFree(W->wcorr);
+        cudaFree(W->wstats);
+        cudaFree(W->resid);
+        cudaFree(W->corr);
+        W->wsyn = W->wcorr = W->resid = W->corr = nullptr;
+        W->wstats = nullptr;
+        W->cap = 0;
+        CUDA_TRY(cudaMalloc(&W->wsyn, (size_t)shots * W->wcw_max * 4));
+        CUDA_TRY(cudaMalloc(&W->wcorr, (size_t)shots * W->wvw_max * 4));
+        CUDA_TRY(cudaMalloc(&W->wstats, (size_t)shots * sizeof(StatsDev)));
+        CUDA_TRY(cudaMalloc(&W->resid, (size_t)shots * wcf * 4));
+        CUDA_TRY(cudaMalloc(&W->corr, (size_t)shots * wvf * 4));
+        W->cap = shots;
+    }
+    uint32_t *resid = d_residual ? d_residual : W->resid;
+    uint32_t *corr = d_corrections ? d_corrections : W->corr;
+    CUDA_TRY(cudaMemcpyAsync(resid, d_syndromes, (size_t)shots * wcf * 4, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(corr, 0, (size_t)shots * wvf * 4, st));
+    if (d_converged) {
+        // every shot starts converged; each window ANDs its own flag in
+        fill_i32_kernel<<<std::max(1, std::min<int>(W->num_sms * 4, (int)((shots + 255) / 256))), 256, 0, st>>>(
+            d_converged, 1, shots);
+        CUDA_TRY(cudaGetLastError());
+    }
+    const int g_blocks = W->num_sms * 8;
+    for (size_t t = 0; t < W->hs.size(); ++t) {
+        relaybp_handle *h = W->hs[t];
+        const int wcw = words(W->nrows[t]), wvw = words(h->dem.V);
+        win_gather_kernel<<<g_blocks, 256, 0, st>>>(resid, wcf, W->rows[t], W->nrows[t], W->wsyn, wcw, shots);
+        CUDA_TRY(cudaGetLastError());
+        if (int rc = relaybp_decode_batch(h, W->wsyn, shot0, shots, W->wcorr, nullptr,
+                                          reinterpret_cast<relaybp_shot_stats *>(W->wstats), st)) {
+            const std::string msg = g_err;
+            return fail(rc, "window %d: %s", (int)t, msg.c_str());
+        }
+        win_commit_kernel<<<g_blocks, 256, 0, st>>>(W->wcorr, wvw, W->clocal[t], W->cfull[t], W->ncommit[t], W->cptr,
+                                                     W->crow, corr, wvf, resid, wcf, W->wstats, d_converged, shots);
+        CUDA_TRY(cudaGetLastError());
+    }
+    if (d_pred_obs) {
+        CUDA_TRY(cudaMemsetAsync(d_pred_obs, 0, (size_t)shots * wk * 4, st));
+        win_obs_kernel<<<g_blocks, 256, 0, st>>>(corr, wvf, W->V, W->optr, W->oidx, d_pred_obs, wk, shots);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return 0;
+}
+
+int relaybp_windows_destroy(relaybp_windows *W)
+{
+    if (!W) return 0;
+    for (relaybp_handle *h : W->hs) relaybp_destroy(h);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(W->device);
+    cudaDeviceSynchronize();
+    for (void *p : W->allocs) cudaFree(p);
+    cudaFree(W->wsyn);
+    cudaFree(W->wcorr);
+    cudaFree(W->wstats);
+    cudaFree(W->resid);
+    cudaFree(W->corr);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete W;
+    return 0;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
                         uint32_t *h_pred_obs, relaybp_shot_stats *h_stats, void *cuda_stream)
 {
@@ -1433,7 +1708,7 @@ int relaybp_autotune(relaybp_handle *h, const uint32_t *d_syndromes, uint64_t sh
         ExactPlan ep = make_exact_plan(h->dem);
         int maxsm = 0;
         CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-        if (ep.total <= maxsm / 2) return fail(RELAYBP_ERR_UNSUPPORTED, "the literal-order FP64 kernel has no shape to tune");
+        if (ep.total <= maxsm) return fail(RELAYBP_ERR_UNSUPPORTED, "the literal-order FP64 kernel has no shape to tune");
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const RowGeom opts[] = {{4, 4}, {8, 4}, {8, 8}, {8, 12}, {8, 16}, {16, 16}, {32, 16}};

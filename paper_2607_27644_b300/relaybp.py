@@ -69,6 +69,12 @@ def _load() -> ctypes.CDLL:
         "relaybp_spa_llr": ([P, I32, P, ctypes.c_double, ctypes.c_double, U64, U64, I64, P, P], ctypes.c_int),
         "relaybp_spa_decode": ([P, I32, P, I64, I32, ctypes.c_double, I32, P, P, P, P, P], ctypes.c_int),
         "relaybp_spa_destroy": ([P], ctypes.c_int),
+        "relaybp_windows_create": ([ctypes.POINTER(relaybp_csr), P, ctypes.POINTER(relaybp_csr), P, I32,
+                                    ctypes.POINTER(relaybp_params), ctypes.POINTER(P)], ctypes.c_int),
+        "relaybp_windows_info": ([P, P, P], ctypes.c_int),
+        "relaybp_windows_handle": ([P, I32, ctypes.POINTER(P)], ctypes.c_int),
+        "relaybp_windows_decode": ([P, P, U64, I64, P, P, P, P, P], ctypes.c_int),
+        "relaybp_windows_destroy": ([P], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
         "relaybp_learned_tape_bytes": ([P, I32, I32, I64], I64),
@@ -96,7 +102,8 @@ _lib = _load()
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows",
             "relaybp_set_learned_legs", "relaybp_set_pair_kernel", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_decode_flagged", "relaybp_osd", "relaybp_spa_create", "relaybp_spa_llr",
-            "relaybp_spa_decode", "relaybp_spa_destroy", "relaybp_count_failures", "relaybp_launch_count",
+            "relaybp_spa_decode", "relaybp_spa_destroy", "relaybp_windows_create", "relaybp_windows_info",
+            "relaybp_windows_handle", "relaybp_windows_decode", "relaybp_windows_destroy", "relaybp_count_failures", "relaybp_launch_count",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
             "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
@@ -318,6 +325,91 @@ def relaybp_spa_decode(spa: Spa, *a, **k):
 
 def relaybp_spa_destroy(spa: Spa):
     spa.destroy()
+
+
+class Windows:
+    """Sliding-window decoder with a commit region of one round: one device
+    handle per window, built at construction."""
+
+    def __init__(self, H_indptr, H_indices, n_det: int, n_loc: int, priors, det_round, window: int,
+                 O_indptr=None, O_indices=None, n_obs: int = 0, params: Params | None = None):
+        params = params or Params()
+        Hp = np.ascontiguousarray(H_indptr, dtype=np.int32)
+        Hi = np.ascontiguousarray(H_indices, dtype=np.int32)
+        pr = np.ascontiguousarray(priors, dtype=np.float64)
+        dr = np.ascontiguousarray(det_round, dtype=np.int32)
+        if dr.shape != (n_det,):
+            raise ValueError(f"det_round has shape {dr.shape}, expected ({n_det},)")
+        H = relaybp_csr(n_det, n_loc, _ptr(Hp), _ptr(Hi))
+        O = None
+        if O_indptr is not None and n_obs > 0:
+            Op = np.ascontiguousarray(O_indptr, dtype=np.int32)
+            Oi = np.ascontiguousarray(O_indices, dtype=np.int32)
+            O = relaybp_csr(n_obs, n_loc, _ptr(Op), _ptr(Oi))
+        out = ctypes.c_void_p()
+        cp = params.c()
+        _check(_lib.relaybp_windows_create(ctypes.byref(H), _ptr(pr), ctypes.byref(O) if O is not None else None,
+                                           _ptr(dr), window, ctypes.byref(cp), ctypes.byref(out)),
+               "relaybp_windows_create")
+        self.ptr = out
+        self.n_det, self.n_loc, self.n_obs = n_det, n_loc, n_obs
+        nw, nr = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.relaybp_windows_info(self.ptr, ctypes.byref(nw), ctypes.byref(nr)), "relaybp_windows_info")
+        self.n_windows, self.n_rounds = nw.value, nr.value
+
+    @property
+    def wc(self):
+        return (self.n_det + 31) // 32
+
+    @property
+    def wv(self):
+        return (self.n_loc + 31) // 32
+
+    @property
+    def wk(self):
+        return max(1, (self.n_obs + 31) // 32)
+
+    def handle(self, t: int) -> Handle:
+        """Window t's decoder (owned by this object: never relaybp_destroy it)."""
+        out = ctypes.c_void_p()
+        _check(_lib.relaybp_windows_handle(self.ptr, t, ctypes.byref(out)), "relaybp_windows_handle")
+        h = Handle(out, 0, 0, 0, 0)
+        h.n_det, h.n_loc, h.n_obs, h.n_edges = relaybp_sizes(h)
+        return h
+
+    def decode(self, d_syndromes, shot0: int, shots: int, d_corrections=None, d_pred_obs=None, d_residual=None,
+               d_converged=None, stream=None):
+        _check(_lib.relaybp_windows_decode(self.ptr, _ptr(d_syndromes), shot0, shots, _ptr(d_corrections),
+                                           _ptr(d_pred_obs), _ptr(d_residual), _ptr(d_converged), _stream(stream)),
+               "relaybp_windows_decode")
+
+    def destroy(self):
+        if self.ptr:
+            _lib.relaybp_windows_destroy(self.ptr)
+            self.ptr = None
+
+
+def relaybp_windows_create(dem, det_round, window: int, params: Params | None = None) -> Windows:
+    """relaybp_windows_create from a workloads.dem.DEM and its detector rounds."""
+    return Windows(dem.H_indptr, dem.H_indices, dem.n_det, dem.n_loc, dem.priors, det_round, window, dem.O_indptr,
+                   dem.O_indices, dem.n_obs, params)
+
+
+def relaybp_windows_info(w: Windows) -> tuple[int, int]:
+    """(windows, rounds)."""
+    return w.n_windows, w.n_rounds
+
+
+def relaybp_windows_handle(w: Windows, t: int) -> Handle:
+    return w.handle(t)
+
+
+def relaybp_windows_decode(w: Windows, *a, **k):
+    w.decode(*a, **k)
+
+
+def relaybp_windows_destroy(w: Windows):
+    w.destroy()
 
 
 def relaybp_decode_batch_noalloc(h: Handle, d_syndromes, shot0: int, shots: int, d_corrections=None,

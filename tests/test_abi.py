@@ -91,7 +91,8 @@ _HANDLE_CALLS = ["relaybp_set_params", "relaybp_set_learned", "relaybp_set_learn
                  "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch", "relaybp_decode_timed",
                  "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host",
                  "relaybp_count_failures", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
-                 "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_decode"]
+                 "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_decode", "relaybp_windows_info",
+                 "relaybp_windows_handle", "relaybp_windows_decode"]
 
 
 @pytest.mark.parametrize("name", _HANDLE_CALLS)
@@ -107,6 +108,30 @@ def test_every_handle_call_rejects_a_null_handle(name):
         else:
             args.append(None)
     assert fn(*args) < 0
+    assert R.relaybp_last_error()
+
+
+@pytest.mark.parametrize("case", ["window0", "negative_round", "no_rounds", "params"])
+def test_windows_create_validates_before_any_device_work(case):
+    from paper_2607_27644_b300 import relaybp as R
+    H, keep = _csr(2, 3, [0, 2, 4], [0, 1, 1, 2])
+    pr = np.full(3, 0.1)
+    rounds = np.array([0, 1], dtype=np.int32)
+    window, p = 1, R.Params(num_sets=3)
+    if case == "window0":
+        window = 0
+    elif case == "negative_round":
+        rounds = np.array([0, -1], dtype=np.int32)
+    elif case == "no_rounds":
+        H, keep = _csr(0, 3, [0], [])
+        rounds = np.zeros(0, dtype=np.int32)
+    elif case == "params":
+        p = R.Params(pre_iter=0)
+    out = ctypes.c_void_p()
+    rc = R._lib.relaybp_windows_create(ctypes.byref(H), pr.ctypes.data_as(ctypes.c_void_p), None,
+                                       rounds.ctypes.data_as(ctypes.c_void_p), window, ctypes.byref(p.c()),
+                                       ctypes.byref(out))
+    assert rc == -1 and out.value is None
     assert R.relaybp_last_error()
 
 

@@ -306,6 +306,17 @@ def _set_bits_by_fault(R: np.ndarray, nloc: int) -> tuple[np.ndarray, np.ndarray
     return fault[order], row[order]
 
 
+def detector_rounds(dem) -> np.ndarray:
+    """Round of each detector of a d-round memory DEM: the 2l detectors of
+    round r (0 <= r < d) come r-th, the final data-readout detectors form round
+    d (Table 5: N_det = 2 l (d + 1))."""
+    rounds = int(dem.meta["rounds"])
+    per, rem = divmod(dem.n_det, rounds + 1)
+    if rem:
+        raise ValueError(f"{dem.n_det} detectors do not split into {rounds + 1} equal rounds")
+    return (np.arange(dem.n_det) // per).astype(np.int32)
+
+
 def circuit_dem(code_name: str, p: float, rounds: int | None = None, basis: str = "Z",
                 chunk: int = 1 << 17) -> DEM:
     """Circuit-level DEM of a d-round memory experiment (Sec. 6.1, App. E).
