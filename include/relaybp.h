@@ -379,6 +379,24 @@ int relaybp_probe_smem_read(int32_t reps, float *d_sink, double *bytes_read, voi
  * rows are too long; RELAYBP_ERR_INVALID for warps outside 0..32. */
 int relaybp_set_pair_kernel(relaybp_handle *h, int32_t enable, int32_t warps);
 
+/* Latency mode (Sec. 6.1, Table 5; App. F, Table 12 measure decoding latency
+ * one shot at a time): decode each shot with a thread-block cluster of
+ * `cluster` CTAs (1..16; 0 turns it off) instead of one block.  CTA c of a
+ * cluster owns a contiguous 1/cluster of the check rows and of the 32-variable
+ * groups and keeps their state in its shared memory; the other CTAs read it
+ * through distributed shared memory.  The iteration is the one-block FP32
+ * kernel's, operation for operation, so outputs are equal bit for bit.
+ * Applies to FP32 handles without learned parameters, in relaybp_decode_batch,
+ * relaybp_decode_batch_noalloc, relaybp_decode_timed and relaybp_decode_host
+ * (trace and flagged decodes keep the one-block kernels).  A launch runs as
+ * many clusters as fit on the GPU, each taking the next shot from the work
+ * counter.  Builds the cluster's row-slot and column-code layout now (device
+ * memory ~ 4 * (cluster * rows_per_cta_rounded * 32 * ceil(max row degree / 32)
+ * + nnz) bytes).  RELAYBP_ERR_UNSUPPORTED if the handle is not FP32, a row has
+ * more than 256 entries, or a CTA's share of the state does not fit in shared
+ * memory. */
+int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster);
+
 /* Classical channel coding (paper Sec. 6.2): BPSK over AWGN and flooding
  * sum-product belief propagation for classical codes such as the ZSZ-2BGA
  * seed codes of Table 2.

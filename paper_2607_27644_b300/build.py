@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "librelaybp.so")
 SOURCES = [os.path.join(HERE, "csrc", "relaybp.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "learned.cuh", "philox.cuh", "pair.cuh", "osd.cuh", "spa.cuh", "windows.cuh")] + \
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("kernels.cuh", "learned.cuh", "philox.cuh", "pair.cuh", "osd.cuh", "spa.cuh", "windows.cuh", "cluster.cuh")] + \
     [os.path.join(ROOT, "include", "relaybp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -6,6 +6,7 @@
 // prior LLRs in FP64 and FP32, and the sampler thresholds floor(p_j 2^32).  The handle owns every device
 // allocation and a small scratch area: the persistent kernel's work counter,
 // failure counters and a per-block buffer for the leg's memory strengths.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -23,6 +24,7 @@
 #include "osd.cuh"
 #include "spa.cuh"
 #include "windows.cuh"
+#include "cluster.cuh"
 
 using namespace relaybp;
 
@@ -102,6 +104,12 @@ struct relaybp_handle {
     size_t lgbar_bytes = 0;
     int32_t *d_osd_order = nullptr;                   // OSD: per-block column order scratch
     size_t osd_order_bytes = 0;
+    // cluster (latency) kernel: codes for cl_nc CTAs per shot, or cl_nc == 0
+    int cl_nc = 0, cl_nb = 0, cl_clusters = 0;
+    ClusterJob cl{};                                  // layout part (codes, sizes, plan)
+    uint16_t *cl_rslot = nullptr;
+    uint32_t *cl_ecode = nullptr;
+    uint32_t *cl_halo[2] = {nullptr, nullptr};        // A-halo and row-halo source lists
 };
 
 struct relaybp_group {
@@ -607,8 +615,73 @@ int launch_pair(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st
 
 // Single-DEM decode: the literal-order FP64 kernel when it applies, the
 // two-shot FP32 kernel when it applies, else one job of the general kernel.
+// Cluster (latency) kernel: NB = row slots per lane (32 lanes per row).
+constexpr int kClusterNB[] = {1, 2, 3, 4, 6, 8};
+
+template <int NB>
+int launch_cluster_nb(relaybp_handle *h, Scratch &sc, const ClusterJob &job, cudaStream_t st)
+{
+    auto kern = relay_cluster_kernel<NB>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, job.plan.total));
+    if (job.nc > 8) CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)job.nc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = (size_t)job.plan.total;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (h->cl_clusters == 0) {
+        cfg.gridDim = dim3((unsigned)job.nc);
+        int n = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, kern, &cfg));
+        if (n < 1) return fail(RELAYBP_ERR_UNSUPPORTED, "no cluster of %d CTAs with %d bytes of shared memory fits",
+                               job.nc, job.plan.total);
+        h->cl_clusters = n;
+    }
+    const int64_t clusters = std::min<int64_t>(h->cl_clusters, job.shots);
+    cfg.gridDim = dim3((unsigned)(clusters * job.nc));
+    if (int rc = scratch_reserve(sc, 0, 0)) return rc;
+    CUDA_TRY(cudaMemsetAsync(sc.work, 0, sizeof(unsigned long long), st));
+    CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, job, sc.work));
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st)
+{
+    ClusterJob job = h->cl;
+    job.g = h->dem;
+    job.p = dev_params(h->params);
+    job.syn_in = io.syn;
+    job.shot0 = io.shot0;
+    job.shots = io.shots;
+    job.corr_out = io.corr;
+    job.pobs_out = io.pobs;
+    job.stats_out = io.stats;
+    job.times_out = io.times;
+    int rc;
+    switch (h->cl_nb) {
+    case 1: rc = launch_cluster_nb<1>(h, sc, job, st); break;
+    case 2: rc = launch_cluster_nb<2>(h, sc, job, st); break;
+    case 3: rc = launch_cluster_nb<3>(h, sc, job, st); break;
+    case 4: rc = launch_cluster_nb<4>(h, sc, job, st); break;
+    case 6: rc = launch_cluster_nb<6>(h, sc, job, st); break;
+    case 8: rc = launch_cluster_nb<8>(h, sc, job, st); break;
+    default: return fail(RELAYBP_ERR_UNSUPPORTED, "cluster kernel: %d row slots per lane", h->cl_nb);
+    }
+    if (rc == 0) h->launches += 1;
+    return rc;
+}
+
 int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, bool on_chip_only)
 {
+    if (h->cl_nc > 0 && !h->lw && !h->lknots && !h->lwrow && !io.trace && !io.flag.post)
+        return launch_cluster(h, sc, io, st);
     if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots && !h->lwrow && !io.times) {
         int rc = launch_decode_exact(h, sc, io, st);
         if (rc <= 0) return rc;
@@ -1050,6 +1123,158 @@ int relaybp_set_learned_rows(relaybp_handle *h, const float *d_wrow, int32_t T, 
     h->lT = d_wrow ? T : 0;
     h->lknots = d_knots;
     h->lK = d_knots ? K : 0;
+    return 0;
+}
+
+int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (cluster < 0 || cluster > 16) return fail(RELAYBP_ERR_INVALID, "cluster = %d; need 0 (off) or 1..16", cluster);
+    if (int rc = check_device(h)) return rc;
+    cudaFree(h->cl_rslot);
+    cudaFree(h->cl_ecode);
+    cudaFree(h->cl_halo[0]);
+    cudaFree(h->cl_halo[1]);
+    h->cl_rslot = nullptr;
+    h->cl_ecode = h->cl_halo[0] = h->cl_halo[1] = nullptr;
+    h->cl_nc = h->cl_nb = h->cl_clusters = 0;
+    if (cluster == 0) return 0;
+    if (h->params.msg_dtype != RELAYBP_MSG_F32)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "the cluster kernel decodes FP32 messages");
+    const DevDEM &g = h->dem;
+    const int32_t C = g.C, V = g.V, NG = (V + 31) / 32, lg = g.lg_rsp;
+    int nb = 0;
+    for (int x : kClusterNB)
+        if (32 * x >= h->max_row_deg) { nb = x; break; }
+    if (!nb) return fail(RELAYBP_ERR_UNSUPPORTED, "rows of %d entries exceed the cluster kernel's 256", h->max_row_deg);
+    if (!g.rslot) return fail(RELAYBP_ERR_UNSUPPORTED, "the DEM has no row-slot layout");
+    const int32_t nc = cluster;
+    const int32_t Cc = (C + nc - 1) / nc;
+    int32_t lgcs = 1;
+    while ((1 << lgcs) < Cc) ++lgcs;
+    const int32_t NGc = (NG + nc - 1) / nc, Vc = NGc * 32;
+    int32_t lgv = 1;
+    while ((1 << lgv) < Vc) ++lgv;
+    if (lgv + 4 > 32 || lgcs + 4 > 32) return fail(RELAYBP_ERR_UNSUPPORTED, "cluster codes do not fit 32 bits");
+    // host copies of the row lists and the sliced-ELL column codes
+    std::vector<int32_t> rptr(C + 1), rvar(g.E), goff(NG), gdeg(NG);
+    CUDA_TRY(cudaMemcpy(rptr.data(), g.rptr, (C + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(rvar.data(), g.rvar, g.E * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(goff.data(), g.goff, NG * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(gdeg.data(), g.gdeg, NG * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const size_t nell = (size_t)goff[NG - 1] + (size_t)gdeg[NG - 1] * 32;
+    std::vector<uint32_t> ecode(nell);
+    CUDA_TRY(cudaMemcpy(ecode.data(), g.ecode, nell * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    const int RS = 32 * nb;
+    const uint32_t pmask = (1u << lg) - 1u;
+    // per CTA: the A halo (variables its rows touch) and the row halo (rows
+    // its variables touch), both ascending -- hence sorted by owner, then by
+    // the owner's local index
+    std::vector<uint16_t> rs((size_t)nc * Cc * RS, 0);
+    std::vector<uint32_t> ec(nell, 0), ahs, rhs;
+    ClusterJob &J = h->cl;
+    J = ClusterJob{};
+    int HAmax = 0, HRmax = 0;
+    std::vector<int32_t> hidx(std::max(V, C), -1);
+    for (int32_t c = 0; c < nc; ++c) {
+        const int32_t i0 = std::min(C, c * Cc), i1 = std::min(C, (c + 1) * Cc);
+        std::vector<int32_t> cols;
+        for (int32_t i = i0; i < i1; ++i) cols.insert(cols.end(), rvar.begin() + rptr[i], rvar.begin() + rptr[i + 1]);
+        std::sort(cols.begin(), cols.end());
+        cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+        const int HA = (int)cols.size();
+        if (HA > 65535) return fail(RELAYBP_ERR_UNSUPPORTED, "cluster of %d: %d halo variables in one CTA", nc, HA);
+        J.ha_off[c] = (int)ahs.size();
+        J.ha_cnt[c] = HA;
+        for (int k = 0; k < HA; ++k) {
+            const int32_t j = cols[k], oc = (j / 32) / NGc;
+            hidx[j] = k;
+            ahs.push_back(((uint32_t)oc << lgv) | (uint32_t)(j - oc * Vc));
+        }
+        for (int32_t i = i0; i < i1; ++i)
+            for (int32_t k = 0; k < RS; ++k)
+                rs[((size_t)c * Cc + (i - i0)) * RS + k] =
+                    (uint16_t)(k < rptr[i + 1] - rptr[i] ? hidx[rvar[rptr[i] + k]] : HA);
+        for (int32_t j : cols) hidx[j] = -1;
+        const int32_t G0 = std::min(NG, c * NGc), G1 = std::min(NG, (c + 1) * NGc);
+        std::vector<int32_t> rows;
+        for (int32_t G = G0; G < G1; ++G)
+            for (size_t x = (size_t)goff[G]; x < (size_t)goff[G] + (size_t)gdeg[G] * 32; ++x)
+                if ((ecode[x] >> lg) < (uint32_t)C) rows.push_back((int32_t)(ecode[x] >> lg));
+        std::sort(rows.begin(), rows.end());
+        rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+        const int HR = (int)rows.size();
+        J.hr_off[c] = (int)rhs.size();
+        J.hr_cnt[c] = HR;
+        for (int k = 0; k < HR; ++k) {
+            hidx[rows[k]] = k;
+            rhs.push_back(((uint32_t)(rows[k] / Cc) << lgcs) | (uint32_t)(rows[k] % Cc));
+        }
+        for (int32_t G = G0; G < G1; ++G)
+            for (size_t x = (size_t)goff[G]; x < (size_t)goff[G] + (size_t)gdeg[G] * 32; ++x) {
+                const uint32_t i = ecode[x] >> lg;
+                ec[x] = (i < (uint32_t)C) ? ((uint32_t)hidx[i] << lg) | (ecode[x] & pmask) : (uint32_t)HR << lg;
+            }
+        for (int32_t i : rows) hidx[i] = -1;
+        if (((uint64_t)HR + 1) << lg > 0xffffffffull)
+            return fail(RELAYBP_ERR_UNSUPPORTED, "cluster codes do not fit 32 bits");
+        HAmax = std::max(HAmax, HA);
+        HRmax = std::max(HRmax, HR);
+    }
+    const int RWd = g.rw;
+    ClusterPlan pl{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 15) & ~size_t(15);
+        const size_t at = off;
+        off += bytes;
+        return (int)at;
+    };
+    pl.A = take(4 * (size_t)Vc);
+    pl.M = take(4 * (size_t)Vc);
+    pl.gam = take(4 * (size_t)Vc);
+    pl.Ah = take(4 * (size_t)(HAmax + 1));
+    pl.cs0 = take(16 * (size_t)Cc);
+    pl.cs1 = take(16 * (size_t)Cc);
+    pl.sg0 = take(4 * (size_t)Cc * RWd);
+    pl.sg1 = take(4 * (size_t)Cc * RWd);
+    pl.csh = take(16 * (size_t)(HRmax + 1));
+    pl.sgh = take(4 * (size_t)(HRmax + 1) * RWd);
+    pl.ahs = take(4 * (size_t)HAmax);
+    pl.rhs = take(4 * (size_t)HRmax);
+    pl.ehat = take(4 * (size_t)NGc);
+    pl.best = take(4 * (size_t)NGc);
+    pl.res = take(4 * (size_t)((Cc + 31) / 32));
+    pl.syn = take(4 * (size_t)((Cc + 31) / 32));
+    pl.lst = take(4 * (size_t)Vc);
+    pl.obsacc = take(4 * (size_t)std::max(1, (g.K + 31) / 32));
+    pl.flags = take(4 * 32);
+    pl.total = (int)((off + 15) & ~size_t(15));
+    int maxsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (pl.total + 64 > maxsm)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "cluster of %d: %d bytes of shared memory per CTA (limit %d)", nc,
+                    pl.total, maxsm);
+    uint32_t *d_ahs = nullptr, *d_rhs = nullptr;
+    CUDA_TRY(cudaMalloc(&h->cl_rslot, rs.size() * 2));
+    CUDA_TRY(cudaMemcpy(h->cl_rslot, rs.data(), rs.size() * 2, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&h->cl_ecode, ec.size() * 4));
+    CUDA_TRY(cudaMemcpy(h->cl_ecode, ec.data(), ec.size() * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&d_ahs, std::max<size_t>(1, ahs.size()) * 4));
+    h->cl_halo[0] = d_ahs;
+    CUDA_TRY(cudaMemcpy(d_ahs, ahs.data(), ahs.size() * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&d_rhs, std::max<size_t>(1, rhs.size()) * 4));
+    h->cl_halo[1] = d_rhs;
+    CUDA_TRY(cudaMemcpy(d_rhs, rhs.data(), rhs.size() * 4, cudaMemcpyHostToDevice));
+    J.plan = pl;
+    J.rslot = h->cl_rslot;
+    J.ecode = h->cl_ecode;
+    J.ahs = d_ahs;
+    J.rhs = d_rhs;
+    J.nc = nc; J.Cc = Cc; J.lgcs = lgcs; J.NGc = NGc; J.Vc = Vc; J.lgv = lgv;
+    h->cl_nc = nc;
+    h->cl_nb = nb;
     return 0;
 }
 
@@ -1876,6 +2101,10 @@ int relaybp_destroy(relaybp_handle *h)
     cudaFree(h->d_lwork);
     cudaFree(h->d_lgbar);
     cudaFree(h->d_osd_order);
+    cudaFree(h->cl_rslot);
+    cudaFree(h->cl_ecode);
+    cudaFree(h->cl_halo[0]);
+    cudaFree(h->cl_halo[1]);
     cudaFree(h->d_stage_syn);
     cudaFree(h->d_stage_pobs);
     cudaFree(h->d_stage_stats);
