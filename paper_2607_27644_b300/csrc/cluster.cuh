@@ -25,10 +25,14 @@
 // buffers; if iteration t converged, that buffer is dropped.
 //
 // Codes (built on the host for one NC, per CTA):
-//   row slot   index into the A halo (padding: the halo's dummy entry, +inf)
+//   row slot   index into the A halo (padding: the halo's dummy entry, +inf);
+//              the row pass is the one-block kernels' (16 lanes per row) on
+//              the CTA's rows, numbered locally, with a zero dummy row after
+//              the last
 //   column     (row-halo index << lg) | position (padding: the row halo's
 //              dummy entry, all zero)
-//   argmin     the position alone (the row is known from where it is kept)
+//   argmin     compared by position alone (the row is known from where its
+//              state is kept)
 //   halo src   (owner << lgv) | owner-local variable, (owner << lgcs) | row
 #pragma once
 #include "kernels.cuh"
@@ -43,10 +47,10 @@ struct ClusterJob {
     DevDEM g;
     DecodeParamsDev p;
     ClusterPlan plan;
-    const uint16_t *rslot;      // [NC][Cc][32 * NB] row slots: A-halo indices
+    const int32_t *rslot;       // [NC][CPc][kRowStride] row slots: A-halo indices (padding: the dummy)
     const uint32_t *ecode;      // sliced ELL (g.goff / g.gdeg): (row-halo index << lg) | position
     const uint32_t *ahs, *rhs;  // halo source lists of all CTAs (at ha_off / hr_off)
-    int nc, Cc, lgcs, NGc, Vc, lgv;
+    int nc, Cc, CPc, lgcs, NGc, Vc, lgv;
     int ha_off[16], ha_cnt[16], hr_off[16], hr_cnt[16];
     const uint32_t *syn_in;
     uint64_t shot0;
@@ -100,73 +104,6 @@ __device__ __forceinline__ void cl_xor(uint32_t a, uint32_t v)
 __device__ __forceinline__ void cl_sync()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// Row pass of CTA `rank` over its own rows, one warp per row (32 lanes, NB
-// slots per lane: positions b * 32 + lane).  Reads check states / sign words
-// from buffer (csr, sgr), writes (csw, sgw).
-template <int NB>
-__device__ __forceinline__ void cl_row_pass(const ClusterJob &J, uint32_t rank, int nrow, const float *Ah,
-                                            const CheckState<float> *csr, const uint32_t *sgr,
-                                            CheckState<float> *csw, uint32_t *sgw, const uint32_t *syn, int warp,
-                                            int nwarp, int lane)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int RW = J.g.rw;
-    const uint16_t *rs0 = J.rslot + (size_t)rank * J.Cc * (32 * NB) + lane;
-    uint32_t cn[NB];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) cn[b] = (warp < nrow) ? __ldg(rs0 + (size_t)warp * (32 * NB) + b * 32) : 0u;
-    for (int r = warp; r < nrow; r += nwarp) {
-        float av[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) av[b] = Ah[cn[b]];
-        const int rn = r + nwarp;                       // the next row's slots load meanwhile
-#pragma unroll
-        for (int b = 0; b < NB; ++b) cn[b] = (rn < nrow) ? __ldg(rs0 + (size_t)rn * (32 * NB) + b * 32) : 0u;
-        const CheckState<float> o = csr[r];
-        const int q = (int)o.meta - lane;               // slot b holds the argmin iff q == 32 b
-        float b1 = __int_as_float(0x7f800000), b2 = b1;
-        int bs = 0;
-        uint32_t bal[NB], X = 0u;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const uint32_t x = (b < RW) ? sgr[r * RW + b] : 0u;
-            const uint32_t sb = __funnelshift_l(x, x, lane) & 0x80000000u;
-            const float mag = (q == b * 32) ? o.m2 : o.m1;
-            const float m = add_rn(av[b], -xsign(mag, sb));
-            bal[b] = __ballot_sync(FULL, m < 0.f);
-            X ^= bal[b];
-            const float a = vabs2(m);
-            b2 = vmin2(b2, vmax2(b1, a));
-            bs = (a < b1) ? b : bs;
-            b1 = vmin2(b1, a);
-        }
-        int bi = bs * 32 + lane;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float o1 = __shfl_xor_sync(FULL, b1, off);
-            const float o2 = __shfl_xor_sync(FULL, b2, off);
-            const int oi = __shfl_xor_sync(FULL, bi, off);
-            if (o1 < b1 || (o1 == b1 && oi < bi)) { b2 = vmin2(b1, o2); b1 = o1; bi = oi; }
-            else { b2 = vmin2(b2, o1); }
-            b1 = vmin2(b1, o1);
-        }
-        const uint32_t par = (uint32_t)(__popc(X) & 1);
-        uint32_t mine = 0u;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) mine = (lane == b) ? bal[b] : mine;
-        if (lane < NB && lane < RW) sgw[r * RW + lane] = __brev(mine);
-        if (lane == 0) {
-            const uint32_t sb = (syn[r >> 5] >> (r & 31)) & 1u;
-            const bool neg = (par ^ sb) != 0u;
-            CheckState<float> n;
-            n.m1 = neg ? -b1 : b1;
-            n.m2 = neg ? -b2 : b2;
-            n.meta = (uint32_t)bi;
-            csw[r] = n;
-        }
-    }
 }
 
 // Ordered FP64 weight sum_j e_j L0_j over the cluster's bit vector `bits`
@@ -237,6 +174,7 @@ template <int NB>
 __global__ void __launch_bounds__(1024, 1)
 relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *__restrict__ work)
 {
+    constexpr int L = 16;                               // lanes per row in the row pass
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_shot;
     __shared__ unsigned long long s_t0;
@@ -255,6 +193,10 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
     const int r0 = (int)rank * J.Cc, nrow = max(0, min(Cn - r0, J.Cc));
     const int g0 = (int)rank * J.NGc, g1 = min(NG, g0 + J.NGc), ngr = max(0, g1 - g0);
     const int HA = J.ha_cnt[rank], HR = J.hr_cnt[rank];
+    DevDEM gl = g;                                      // the row pass's view: own rows, local numbering
+    gl.C = nrow;
+    gl.rslot = J.rslot + (size_t)rank * J.CPc * kRowStride;
+    const QScale qs{0.f};
     float *A = reinterpret_cast<float *>(smem + pl.A);          // own variables (read by the others)
     float *M = reinterpret_cast<float *>(smem + pl.M);
     float *gam = reinterpret_cast<float *>(smem + pl.gam);
@@ -346,13 +288,13 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
                 A[jl] = finf;
             }
         }
-        for (int i = tid; i < nrow; i += nthr) {
+        for (int i = tid; i <= nrow; i += nthr) {      // row nrow: the row pass's dummy
             CheckState<float> z;
             z.m1 = 0.f; z.m2 = 0.f; z.meta = 0u;
             cs0[i] = z;
             cs1[i] = z;
         }
-        for (int w = tid; w < nrow * RW; w += nthr) { sg0[w] = 0u; sg1[w] = 0u; }
+        for (int w = tid; w < (nrow + 1) * RW; w += nthr) { sg0[w] = 0u; sg1[w] = 0u; }
         for (int w = tid; w < ngr; w += nthr) { ehat[w] = 0u; best[w] = 0u; }
         for (int w = warp; w < (J.Cc + 31) / 32; w += nwarp) {
             const int r = w * 32 + lane, i = r0 + r;
@@ -397,7 +339,8 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
             bool conv = false;
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: own rows; for t > 0 also speculative past iteration t-1
-                cl_row_pass<NB>(J, rank, nrow, Ah, CS(cur), SG(cur), CS(cur ^ 1), SG(cur ^ 1), syn, warp, nwarp, lane);
+                row_pass<float, L, NB, false>(gl, Ah, CS(cur), SG(cur), CS(cur ^ 1), SG(cur ^ 1), syn, warp, nwarp, lane,
+                                              nullptr, nullptr, qs);
                 cl_sync();
                 if (t > 0) {
                     const uint32_t f = (lane < J.nc) ? flags[((t - 1) & 1) * 16 + lane] : 0u;
@@ -425,7 +368,7 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
                             const uint32_t hr = c[u] >> lg;
                             const CheckState<float> q = csh[hr];
                             const uint32_t hw = sgh[hr * RW + ((c[u] & pmask) >> 5)];
-                            const float mag = ((c[u] & pmask) == q.meta) ? q.m2 : q.m1;
+                            const float mag = ((c[u] & pmask) == (q.meta & pmask)) ? q.m2 : q.m1;
                             Ssum = add_rn(Ssum, xsign(mag, __funnelshift_l(hw, hw, c[u]) & 0x80000000u));
                         }
                     }
@@ -433,7 +376,7 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
                         const uint32_t c = __ldg(col + k * 32), hr = c >> lg;
                         const CheckState<float> q = csh[hr];
                         const uint32_t hw = sgh[hr * RW + ((c & pmask) >> 5)];
-                        const float mag = ((c & pmask) == q.meta) ? q.m2 : q.m1;
+                        const float mag = ((c & pmask) == (q.meta & pmask)) ? q.m2 : q.m1;
                         Ssum = add_rn(Ssum, xsign(mag, __funnelshift_l(hw, hw, c) & 0x80000000u));
                     }
                     uint32_t dec = 0u;

@@ -353,10 +353,13 @@ __device__ __forceinline__ uint32_t sign_word(const uint32_t (&bal)[NB], int w, 
 // position p in bit 31 - p % 32 of word p / 32 (reversed, so that a funnel
 // shift by the column code brings it to bit 31).  The P rows of a warp step
 // gather their bits from one ballot per slot.
+// The check states and sign words are read from (csr, sgr) and written to
+// (cs, sgw); the one-shot kernels pass the same arrays, the cluster kernel
+// two buffers.
 template <typename S, int L, int NB, bool LW>
-__device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState<S> *cs, uint32_t *sgw,
-                                         const uint32_t *syn, int warp, int nwarp, int lane, const float *wprev,
-                                         const float *wrow_new, const QScale &qs)
+__device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, const CheckState<S> *csr, const uint32_t *sgr,
+                                         CheckState<S> *cs, uint32_t *sgw, const uint32_t *syn, int warp, int nwarp,
+                                         int lane, const float *wprev, const float *wrow_new, const QScale &qs)
 {
     static_assert(32 % L == 0 && NB <= 16, "row geometry");
     using C = typename Prec<S>::C;
@@ -385,14 +388,14 @@ __device__ __forceinline__ void row_pass(const DevDEM &g, const S *A, CheckState
 #pragma unroll
             for (int b = 0; b < NB; ++b) nidx[b] = __ldg(rs + b * L);
         }
-        const CheckState<S> o = cs[il];
+        const CheckState<S> o = csr[il];
         const C om1 = Prec<S>::ld(o.m1, qs), om2 = Prec<S>::ld(o.m2, qs);     // weighted when learned
         // slot b holds the argmin iff q == b * L
         const int q = (int)o.meta - (il << lg) - l;
         uint32_t W[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            const uint32_t x = (w < RW) ? sgw[il * RW + w] : 0u;
+            const uint32_t x = (w < RW) ? sgr[il * RW + w] : 0u;
             W[w] = __funnelshift_l(x, x, l);
         }
         int e0 = 0, deg = 0;
@@ -631,8 +634,8 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                     if (t < p.lT) wcur = p.lw + (int64_t)t * g.E;
                 }
                 if (lleg && p.lwrow && t < p.lT) wrow = p.lwrow + (int64_t)t * g.C;
-                if (LW) row_pass<S, L, NB, true>(g, A, cs, sgw, syn, warp, nwarp, lane, wprev, wrow, qs);
-                else row_pass<S, L, NB, false>(g, A, cs, sgw, syn, warp, nwarp, lane, nullptr, wrow, qs);
+                if (LW) row_pass<S, L, NB, true>(g, A, cs, sgw, cs, sgw, syn, warp, nwarp, lane, wprev, wrow, qs);
+                else row_pass<S, L, NB, false>(g, A, cs, sgw, cs, sgw, syn, warp, nwarp, lane, nullptr, wrow, qs);
                 __syncthreads();
                 // ---- a4: variables, one lane per variable, ELL slices --------
                 for (int G = warp; G < NG; G += nwarp) {

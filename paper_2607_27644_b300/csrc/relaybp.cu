@@ -107,7 +107,7 @@ struct relaybp_handle {
     // cluster (latency) kernel: codes for cl_nc CTAs per shot, or cl_nc == 0
     int cl_nc = 0, cl_nb = 0, cl_clusters = 0;
     ClusterJob cl{};                                  // layout part (codes, sizes, plan)
-    uint16_t *cl_rslot = nullptr;
+    int32_t *cl_rslot = nullptr;
     uint32_t *cl_ecode = nullptr;
     uint32_t *cl_halo[2] = {nullptr, nullptr};        // A-halo and row-halo source lists
 };
@@ -616,7 +616,7 @@ int launch_pair(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st
 // Single-DEM decode: the literal-order FP64 kernel when it applies, the
 // two-shot FP32 kernel when it applies, else one job of the general kernel.
 // Cluster (latency) kernel: NB = row slots per lane (32 lanes per row).
-constexpr int kClusterNB[] = {1, 2, 3, 4, 6, 8};
+constexpr int kClusterNB[] = {2, 4, 6, 8, 12, 16};     // slots per lane, 16 lanes per row
 
 template <int NB>
 int launch_cluster_nb(relaybp_handle *h, Scratch &sc, const ClusterJob &job, cudaStream_t st)
@@ -666,12 +666,12 @@ int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     job.times_out = io.times;
     int rc;
     switch (h->cl_nb) {
-    case 1: rc = launch_cluster_nb<1>(h, sc, job, st); break;
     case 2: rc = launch_cluster_nb<2>(h, sc, job, st); break;
-    case 3: rc = launch_cluster_nb<3>(h, sc, job, st); break;
     case 4: rc = launch_cluster_nb<4>(h, sc, job, st); break;
     case 6: rc = launch_cluster_nb<6>(h, sc, job, st); break;
     case 8: rc = launch_cluster_nb<8>(h, sc, job, st); break;
+    case 12: rc = launch_cluster_nb<12>(h, sc, job, st); break;
+    case 16: rc = launch_cluster_nb<16>(h, sc, job, st); break;
     default: return fail(RELAYBP_ERR_UNSUPPORTED, "cluster kernel: %d row slots per lane", h->cl_nb);
     }
     if (rc == 0) h->launches += 1;
@@ -1146,7 +1146,7 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
     const int32_t C = g.C, V = g.V, NG = (V + 31) / 32, lg = g.lg_rsp;
     int nb = 0;
     for (int x : kClusterNB)
-        if (32 * x >= h->max_row_deg) { nb = x; break; }
+        if (16 * x >= h->max_row_deg) { nb = x; break; }
     if (!nb) return fail(RELAYBP_ERR_UNSUPPORTED, "rows of %d entries exceed the cluster kernel's 256", h->max_row_deg);
     if (!g.rslot) return fail(RELAYBP_ERR_UNSUPPORTED, "the DEM has no row-slot layout");
     const int32_t nc = cluster;
@@ -1166,12 +1166,12 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
     const size_t nell = (size_t)goff[NG - 1] + (size_t)gdeg[NG - 1] * 32;
     std::vector<uint32_t> ecode(nell);
     CUDA_TRY(cudaMemcpy(ecode.data(), g.ecode, nell * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-    const int RS = 32 * nb;
+    const int32_t CPc = (Cc + 1 + 31) / 32 * 32;      // rows per CTA in the row-slot table (dummy rows after)
     const uint32_t pmask = (1u << lg) - 1u;
     // per CTA: the A halo (variables its rows touch) and the row halo (rows
     // its variables touch), both ascending -- hence sorted by owner, then by
     // the owner's local index
-    std::vector<uint16_t> rs((size_t)nc * Cc * RS, 0);
+    std::vector<int32_t> rs((size_t)nc * CPc * kRowStride, 0);
     std::vector<uint32_t> ec(nell, 0), ahs, rhs;
     ClusterJob &J = h->cl;
     J = ClusterJob{};
@@ -1184,7 +1184,6 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
         std::sort(cols.begin(), cols.end());
         cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
         const int HA = (int)cols.size();
-        if (HA > 65535) return fail(RELAYBP_ERR_UNSUPPORTED, "cluster of %d: %d halo variables in one CTA", nc, HA);
         J.ha_off[c] = (int)ahs.size();
         J.ha_cnt[c] = HA;
         for (int k = 0; k < HA; ++k) {
@@ -1192,10 +1191,12 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
             hidx[j] = k;
             ahs.push_back(((uint32_t)oc << lgv) | (uint32_t)(j - oc * Vc));
         }
-        for (int32_t i = i0; i < i1; ++i)
-            for (int32_t k = 0; k < RS; ++k)
-                rs[((size_t)c * Cc + (i - i0)) * RS + k] =
-                    (uint16_t)(k < rptr[i + 1] - rptr[i] ? hidx[rvar[rptr[i] + k]] : HA);
+        for (int32_t r = 0; r < CPc; ++r) {
+            const int32_t i = i0 + r;
+            const int32_t deg = (i < i1) ? rptr[i + 1] - rptr[i] : 0;
+            for (int32_t k = 0; k < kRowStride; ++k)
+                rs[((size_t)c * CPc + r) * kRowStride + k] = (k < deg) ? hidx[rvar[rptr[i] + k]] : HA;
+        }
         for (int32_t j : cols) hidx[j] = -1;
         const int32_t G0 = std::min(NG, c * NGc), G1 = std::min(NG, (c + 1) * NGc);
         std::vector<int32_t> rows;
@@ -1235,10 +1236,10 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
     pl.M = take(4 * (size_t)Vc);
     pl.gam = take(4 * (size_t)Vc);
     pl.Ah = take(4 * (size_t)(HAmax + 1));
-    pl.cs0 = take(16 * (size_t)Cc);
-    pl.cs1 = take(16 * (size_t)Cc);
-    pl.sg0 = take(4 * (size_t)Cc * RWd);
-    pl.sg1 = take(4 * (size_t)Cc * RWd);
+    pl.cs0 = take(16 * (size_t)(Cc + 1));
+    pl.cs1 = take(16 * (size_t)(Cc + 1));
+    pl.sg0 = take(4 * (size_t)(Cc + 1) * RWd);
+    pl.sg1 = take(4 * (size_t)(Cc + 1) * RWd);
     pl.csh = take(16 * (size_t)(HRmax + 1));
     pl.sgh = take(4 * (size_t)(HRmax + 1) * RWd);
     pl.ahs = take(4 * (size_t)HAmax);
@@ -1257,8 +1258,8 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
         return fail(RELAYBP_ERR_UNSUPPORTED, "cluster of %d: %d bytes of shared memory per CTA (limit %d)", nc,
                     pl.total, maxsm);
     uint32_t *d_ahs = nullptr, *d_rhs = nullptr;
-    CUDA_TRY(cudaMalloc(&h->cl_rslot, rs.size() * 2));
-    CUDA_TRY(cudaMemcpy(h->cl_rslot, rs.data(), rs.size() * 2, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&h->cl_rslot, rs.size() * 4));
+    CUDA_TRY(cudaMemcpy(h->cl_rslot, rs.data(), rs.size() * 4, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&h->cl_ecode, ec.size() * 4));
     CUDA_TRY(cudaMemcpy(h->cl_ecode, ec.data(), ec.size() * 4, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&d_ahs, std::max<size_t>(1, ahs.size()) * 4));
@@ -1272,7 +1273,7 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
     J.ecode = h->cl_ecode;
     J.ahs = d_ahs;
     J.rhs = d_rhs;
-    J.nc = nc; J.Cc = Cc; J.lgcs = lgcs; J.NGc = NGc; J.Vc = Vc; J.lgv = lgv;
+    J.nc = nc; J.Cc = Cc; J.CPc = CPc; J.lgcs = lgcs; J.NGc = NGc; J.Vc = Vc; J.lgv = lgv;
     h->cl_nc = nc;
     h->cl_nb = nb;
     return 0;
