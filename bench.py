@@ -48,11 +48,16 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--streams", type=int, default=3, help="zsz160: streams (handle sets) the steps rotate over")
     ap.add_argument("--workload", default="zsz160",
-                    choices=["zsz160", "mixed", "learned", "stream550", "gamma_sweep"],
+                    choices=["zsz160", "mixed", "learned", "stream550", "gamma_sweep", "latency"],
                     help="zsz160: the headline workload; mixed: nine DEMs in one persistent launch; "
                          "learned: train, then learned vs plain Relay-BP at equal LER; stream550: ZSZ-LP-550 "
                          "d=18 in CUDA-graph batches with int8 storage and per-shot latency; gamma_sweep: "
-                         "Table 9's gamma-interval grid search and the XZ-averaged LER-vs-p curve")
+                         "Table 9's gamma-interval grid search and the XZ-averaged LER-vs-p curve; latency: "
+                         "Table 5's single-shot latency of ZSZ-LP-320/390/550, one thread-block cluster per shot")
+    ap.add_argument("--latency-shots", type=int, default=2000, help="latency: timed shots per code and basis")
+    ap.add_argument("--latency-max-shots", type=int, default=5,
+                    help="latency: shots per code and basis timed with every relay leg run (max latency)")
+    ap.add_argument("--cluster", type=int, default=16, help="latency: CTAs per thread-block cluster")
     ap.add_argument("--sweep-shots", type=int, default=200_000, help="gamma_sweep: shots per point and basis")
     ap.add_argument("--stream-batch", type=int, default=1 << 16, help="stream550: shots per graph batch")
     ap.add_argument("--train-steps", type=int, default=300, help="learned: Adam steps of 512 shots at p=0.2%%")
@@ -820,6 +825,125 @@ def run_stream550(a):
         R.relaybp_destroy(x)
 
 
+# Table 5 (L40S): mean / p99 / p99.9 / max single-shot latency in ms, and
+# Table 12 (ZSZ-LP-390 on a B200): mean / p99 / p99.9.
+PAPER_LATENCY = {"ZSZ-LP-320": (1.2, 2.0, 3.2, 201.0), "ZSZ-LP-390": (1.5, 2.6, 3.9, 260.0),
+                 "ZSZ-LP-550": (2.2, 3.3, 4.6, 393.0)}
+PAPER_LATENCY_B200_390 = (2.068, 3.554, 5.248)
+
+
+def run_latency(a):
+    """Single-shot decoding latency (Sec. 6.1, Table 5; App. F, Table 12):
+    the ZSZ-LP-320/390/550 circuit-level X- and Z-memory DEMs at p = 0.1%
+    (d = 14/16/18) with the paper's decoder settings and Table 9 gamma in
+    FP32, one shot per call, each decoded by one thread-block cluster of
+    --cluster CTAs.  Per-shot time between CUDA events around the call (the
+    launch included): mean, p50, p99, p99.9, averaged over X and Z like the
+    paper; max latency with every relay leg run (the paper's stopping rule
+    'All'); e2e: the same shots through relaybp_decode_host (host syndrome
+    in, host prediction out, synchronised per shot)."""
+    import numpy as np
+    import torch
+    from paper_2607_27644_b300 import relaybp as R
+    from workloads.dem import circuit_dem
+
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, W, NM = a.latency_shots, max(3, a.warmup), a.latency_max_shots
+    per, launches, e2e_ms, h2d, d2h = {}, 0, [], 0, 0
+    pct = lambda x, q: float(np.percentile(x, q))
+    with ClockSampler(local) as clk:
+        for code, rounds, (gmin, gmax) in MIXED_CODES:
+            res = {}
+            for basis in ("Z", "X"):
+                t_build = time.perf_counter()
+                dem = circuit_dem(code, 0.001, rounds, basis)
+                t_build = time.perf_counter() - t_build
+                prm = dict(DECODER, gamma_min=gmin, gamma_max=gmax)
+                h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **prm))
+                R.relaybp_set_cluster_kernel(h, a.cluster)
+                syn = torch.zeros((N + W, h.wc), dtype=torch.int32, device=dev)
+                R.relaybp_sample(h, SAMPLE_SEED, 0, N + W, syn)
+                corr = torch.zeros((1, h.wv), dtype=torch.int32, device=dev)
+                pobs = torch.zeros((1, h.wk), dtype=torch.int32, device=dev)
+                stats = torch.zeros((N + W, 6), dtype=torch.int32, device=dev)
+                for i in range(W):
+                    R.relaybp_decode_batch(h, syn[i:i + 1], i, 1, corr, pobs, stats[i:i + 1])
+                torch.cuda.synchronize()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(N)]
+                for i in range(N):
+                    s_ = W + i
+                    ev[i][0].record()
+                    R.relaybp_decode_batch(h, syn[s_:s_ + 1], s_, 1, corr, pobs, stats[s_:s_ + 1])
+                    ev[i][1].record()
+                torch.cuda.synchronize()
+                launches += N
+                ms = np.array([x.elapsed_time(y) for x, y in ev])
+                st = stats[W:].cpu().numpy()
+                # end to end through the host-buffer entry point (a sample of the same shots)
+                ne = min(N, 200)
+                h_syn = syn[W:W + ne].cpu().pin_memory()
+                h_pobs = torch.zeros((1, h.wk), dtype=torch.int32).pin_memory()
+                h_st = torch.zeros((1, 6), dtype=torch.int32).pin_memory()
+                te = []
+                for i in range(ne):
+                    t0 = time.perf_counter()
+                    R.relaybp_decode_host(h, h_syn[i:i + 1], W + i, 1, h_pobs, h_st)
+                    te.append((time.perf_counter() - t0) * 1e3)
+                launches += ne
+                e2e_ms += te
+                h2d, d2h = h.wc * 4, h.wk * 4 + 24
+                # worst case: every relay leg run
+                mx = []
+                if NM > 0:
+                    R.relaybp_set_params(h, R.Params(msg_dtype="f32", stop_all=True, **prm))
+                    for i in range(NM):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        R.relaybp_decode_batch(h, syn[W + i:W + i + 1], W + i, 1, corr, pobs, stats[W + i:W + i + 1])
+                        e1.record()
+                        torch.cuda.synchronize()
+                        mx.append(e0.elapsed_time(e1))
+                    launches += NM
+                res[basis] = {"dem": [dem.n_det, dem.n_loc], "edges": int(h.n_edges), "dem_build_s": t_build,
+                              "mean": float(ms.mean()), "p50": pct(ms, 50), "p99": pct(ms, 99),
+                              "p99.9": pct(ms, 99.9), "max_seen": float(ms.max()),
+                              "max_all_legs": float(np.mean(mx)) if mx else None,
+                              "e2e_mean": float(np.mean(te)), "mean_iterations": float(st[:, 3].mean()),
+                              "mean_legs": float(st[:, 2].mean()), "converged": float(st[:, 0].mean())}
+                R.relaybp_destroy(h)
+            xz = {k: (res["X"][k] + res["Z"][k]) / 2 for k in ("mean", "p99", "p99.9", "e2e_mean")}
+            xz["max_all_legs"] = ((res["X"]["max_all_legs"] + res["Z"]["max_all_legs"]) / 2
+                                  if res["X"]["max_all_legs"] is not None else None)
+            pm = PAPER_LATENCY[code]
+            per[code] = {"d": rounds, "X": res["X"], "Z": res["Z"], "xz": xz,
+                         "paper_l40s": {"mean": pm[0], "p99": pm[1], "p99.9": pm[2], "max": pm[3]},
+                         "mean_vs_paper": xz["mean"] / pm[0]}
+    v = per["ZSZ-LP-390"]["xz"]["mean"]
+    line = {"metric": "single-shot decoding latency, ZSZ-LP-390 circuit level p=0.1%, XZ-averaged mean",
+            "value": v, "unit": "ms", "n_gpus": 1, "steps": N, "warmup": W, "ms_per_step": v,
+            "higher_is_better": False, "scaling": "none (one shot at a time)",
+            "vs_baseline": v / PAPER_LATENCY["ZSZ-LP-390"][0], "dtype": "f32",
+            "data": "synthetic: Philox-sampled faults of the circuit DEMs (no dataset)",
+            "config": {"workload": "Table 5: ZSZ-LP-320/390/550 circuit-level X- and Z-memory, d = 14/16/18, "
+                                   "p = 0.001, paper decoder settings, Table 9 gamma, one shot per call",
+                       "kernel": f"relay_cluster_kernel, {a.cluster} CTAs (one per SM) per shot, state in "
+                                 "distributed shared memory",
+                       "timing": "CUDA events around each single-shot call (launch included); L2 not flushed "
+                                 "(a real-time decoder keeps its DEM resident)"},
+            "per_code": per,
+            "paper_b200_390": dict(zip(("mean", "p99", "p99.9"), PAPER_LATENCY_B200_390)),
+            "e2e": {"value": float(np.mean(e2e_ms)), "unit": "ms", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "definition": "relaybp_decode_host per shot: pinned host syndrome in, prediction and "
+                                  "statistics out, synchronised (mean over all codes and bases)"},
+            "clocks": clk.summary(), "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def run_gamma_sweep(a):
     """ZSZ-LP-160: the gamma-interval grid search of Table 9 at p_sweep = 0.2%
     (X- and Z-memory, fewest pooled failures), then the XZ-averaged LER per
@@ -873,6 +997,8 @@ def main():
         run_stream550(a)
     elif a.workload == "gamma_sweep":
         run_gamma_sweep(a)
+    elif a.workload == "latency":
+        run_latency(a)
     else:
         run_ours(a)
 
