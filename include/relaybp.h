@@ -234,7 +234,13 @@ int relaybp_decode_trace(relaybp_handle *h, const uint32_t *d_syndromes, uint64_
 /* Same as relaybp_decode_batch with host buffers: copies h_syndromes to the
  * device, decodes, copies the results back, and synchronises the stream before
  * returning.  Staging buffers are owned by the handle and grow on demand.
- * h_pred_obs and h_stats may be NULL. */
+ * h_pred_obs and h_stats may be NULL.  The whole batch is one persistent
+ * launch: a synchronous call lasts as long as its slowest shot (a shot that
+ * runs every relay leg), and one launch keeps every other shot decoding in
+ * that shot's shadow; cutting the batch into chunks on several streams made
+ * the call slower (measured), the copies being small beside the decode.
+ * Callers that stream many batches overlap their tails by issuing
+ * relaybp_decode_batch on several streams with one handle each. */
 int relaybp_decode_host(relaybp_handle *h, const uint32_t *h_syndromes, uint64_t shot0, int64_t shots,
                         uint32_t *h_pred_obs, relaybp_shot_stats *h_stats, void *cuda_stream);
 
