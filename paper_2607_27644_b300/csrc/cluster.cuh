@@ -58,6 +58,7 @@ struct ClusterJob {
     uint32_t *corr_out, *pobs_out;
     StatsDev *stats_out;
     uint64_t *times_out;
+    TailOut tail;               // resume: decode the shots the two-shot kernel handed over (rec != NULL)
 };
 
 __device__ __forceinline__ uint32_t cl_rank()
@@ -272,8 +273,13 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
             s_t0 = globaltimer_ns();
         }
         cl_sync();
-        const long long sidx = s_shot;
-        if (sidx >= J.shots) break;
+        // resume mode: work index -> hand-over record (its count was written
+        // by the kernel before this one on the stream)
+        const bool rsm = J.tail.rec != nullptr;
+        const long long nwork = rsm ? min((long long)*J.tail.count, J.tail.max) : J.shots;
+        if (s_shot >= nwork) break;
+        const long long qrec = s_shot;
+        const long long sidx = rsm ? J.tail.rec[qrec].sidx : s_shot;
         const uint64_t shot = J.shot0 + (uint64_t)sidx;
 
         // ---- shot start -------------------------------------------------------
@@ -281,8 +287,8 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
             const int j = g0 * 32 + jl;
             if (j < V) {
                 const float l0 = __ldg(g.L0f + j), gm = (float)p.gamma0;
-                M[jl] = l0;
-                gam[jl] = gm;
+                M[jl] = rsm ? J.tail.M[qrec * V + j] : l0;
+                gam[jl] = gm;                           // resumed shots: redrawn at their leg start
                 A[jl] = memprior<float>(gm, l0, l0);
             } else {
                 A[jl] = finf;
@@ -295,7 +301,10 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
             cs1[i] = z;
         }
         for (int w = tid; w < (nrow + 1) * RW; w += nthr) { sg0[w] = 0u; sg1[w] = 0u; }
-        for (int w = tid; w < ngr; w += nthr) { ehat[w] = 0u; best[w] = 0u; }
+        for (int w = tid; w < ngr; w += nthr) {
+            ehat[w] = 0u;                               // e^ = 0 with residual s: consistent for the incremental residual
+            best[w] = rsm ? J.tail.best[qrec * WV + g0 + w] : 0u;
+        }
         for (int w = warp; w < (J.Cc + 31) / 32; w += nwarp) {
             const int r = w * 32 + lane, i = r0 + r;
             const uint32_t bit = (r < nrow) ? (J.syn_in[(size_t)sidx * WC + (i >> 5)] >> (i & 31)) & 1u : 0u;
@@ -303,13 +312,22 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
             if (lane == 0) { syn[w] = word; res[w] = word; }
         }
         if (rank == 0) for (int w = tid; w < WK; w += nthr) obsacc[w] = 0u;
-        int nsol = 0, have = 0, legs = 0, iters = 0, cur = 0;
-        if (tid == 0) s_best_w = 0.0;
+        int nsol = 0, have = 0, legs = 0, iters = 0, cur = 0, leg0 = 0;
+        if (rsm) {
+            const TailRec rec = J.tail.rec[qrec];
+            nsol = rec.nsol;
+            have = rec.have;
+            legs = rec.legs;
+            iters = rec.iters;
+            leg0 = rec.next_leg;
+        }
+        if (tid == 0) s_best_w = rsm ? J.tail.rec[qrec].bestw : 0.0;
+        if (rsm && tid == 0) s_t0 = J.tail.rec[qrec].t0;
         cl_sync();
         pull_A();
         __syncthreads();
 
-        for (int leg = 0; leg <= p.num_sets; ++leg) {
+        for (int leg = leg0; leg <= p.num_sets; ++leg) {
             ++legs;
             if (leg > 0) {
                 for (int jl = tid; jl < ngr * 32; jl += nthr) {

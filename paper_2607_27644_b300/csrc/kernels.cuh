@@ -89,6 +89,30 @@ struct FlagOut {
     long long max;
 };
 
+// Tail hand-over (optional output of the two-shot kernel, input of the
+// cluster kernel): a shot that is about to start relay leg >= legs leaves the
+// kernel at that leg boundary and takes the next slot of *count; if slot <
+// max, rec[slot] keeps what the next legs need -- the shot, the leg to start,
+// the counters and the best solution so far -- with its marginals M in
+// M[slot][V] and the best solution's bits in best[slot][ceil(V/32)].  A new
+// leg restarts the messages at zero (without message carry-over), so nothing
+// else is needed; the cluster kernel continues from there with the same
+// operations.  Past max, shots stay in the two-shot kernel.
+struct TailRec {
+    long long sidx;             // shot index within the batch
+    int next_leg, legs, iters, nsol, have, pad;
+    double bestw;
+    unsigned long long t0;
+};
+struct TailOut {
+    TailRec *rec;
+    float *M;
+    uint32_t *best;
+    unsigned int *count;        // NULL: no hand-over
+    long long max;
+    int legs;                   // first leg that hands a shot over
+};
+
 struct StatsDev {               // mirrors relaybp_shot_stats
     int32_t converged, nsol, legs, iters;
     double weight;

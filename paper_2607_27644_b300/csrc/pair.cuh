@@ -63,6 +63,7 @@ struct PairJob {
     int trace_iters;
     uint64_t *times_out;
     FlagOut flag;               // flagged nonconvergences (flag.post NULL: not written)
+    TailOut tail;               // shots handed over at a leg boundary (tail.count NULL: never)
 };
 
 __device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
@@ -219,6 +220,7 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
     __shared__ int s_leg[2], s_T[2], s_legs[2], s_nsol[2], s_have[2], s_copy[2];
     __shared__ double s_bestw[2], s_w[2];
     __shared__ long long s_fslot[2];
+    __shared__ int s_defer[2];          // hand-over slot of a shot leaving at this leg boundary (< 0: none)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = blockDim.x, nwarp = nthr >> 5;
@@ -429,6 +431,7 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 s_copy[s] = 0;
+                s_defer[s] = -1;
                 if (!conv[s]) continue;
                 const uint32_t *eh = ehat(s);
                 double w = 0.0;
@@ -445,23 +448,53 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
                 s_copy[s] = better;
                 s_nsol[s] += 1;
             }
+            // tail hand-over: a shot about to start leg >= tail.legs leaves
+            // for the cluster kernel while hand-over slots last
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const bool stop = (!J.p.stop_all && s_nsol[s] >= J.p.stop_nconv) || s_leg[s] == J.p.num_sets;
+                if (trans[s] && !stop && J.tail.count && s_leg[s] + 1 >= J.tail.legs) {
+                    const unsigned q = atomicAdd(J.tail.count, 1u);
+                    if ((long long)q < J.tail.max) s_defer[s] = (int)q;
+                }
+            }
         }
         __syncthreads();
-        bool retire[2], newleg[2];
+        bool retire[2], newleg[2], defer[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (s_copy[s])
                 for (int w = tid; w < WV; w += nthr) best(s)[w] = ehat(s)[w];
             const bool stop = (!J.p.stop_all && s_nsol[s] >= J.p.stop_nconv) || s_leg[s] == J.p.num_sets;
             retire[s] = trans[s] && stop;
-            newleg[s] = trans[s] && !stop;
+            defer[s] = trans[s] && !stop && s_defer[s] >= 0;
+            newleg[s] = trans[s] && !stop && !defer[s];
             if (retire[s])
                 for (int w = tid; w < WK; w += nthr) obsacc(s)[w] = 0u;
         }
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            if (retire[s]) {
+            if (defer[s]) {
+                // hand the shot over at the leg boundary: its marginals, best
+                // solution and counters (messages restart at zero in a new leg)
+                const long long q = s_defer[s];
+                const float *M1 = reinterpret_cast<const float *>(M2) + s;
+                for (int j = tid; j < V; j += nthr) J.tail.M[q * V + j] = M1[2 * j];
+                for (int w = tid; w < WV; w += nthr) J.tail.best[q * WV + w] = best(s)[w];
+                if (tid == 0) {
+                    TailRec rec;
+                    rec.sidx = s_sidx[s];
+                    rec.next_leg = s_leg[s] + 1;
+                    rec.legs = s_legs[s];
+                    rec.iters = iters[s];
+                    rec.nsol = s_nsol[s];
+                    rec.have = s_have[s];
+                    rec.bestw = s_bestw[s];
+                    rec.t0 = s_t0[s];
+                    J.tail.rec[q] = rec;
+                }
+            } else if (retire[s]) {
                 // outputs: the best solution (or the last decisions), observables
                 const long long sidx = s_sidx[s];
                 const uint32_t *out = s_have[s] ? best(s) : ehat(s);
@@ -529,7 +562,7 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
                 }
             }
         }
-        if (retire[0] || retire[1]) {
+        if (retire[0] || retire[1] || defer[0] || defer[1]) {
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 if (!retire[s]) continue;
@@ -560,13 +593,13 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
             }
             __syncthreads();
             if (tid == 0) {
-                if (retire[0]) grab(0);
-                if (retire[1]) grab(1);
+                if (retire[0] || defer[0]) grab(0);
+                if (retire[1] || defer[1]) grab(1);
             }
             __syncthreads();
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                if (!retire[s]) continue;
+                if (!retire[s] && !defer[s]) continue;
                 act[s] = s_sidx[s] >= 0;
                 t[s] = 0;
                 iters[s] = 0;

@@ -104,8 +104,16 @@ struct relaybp_handle {
     size_t lgbar_bytes = 0;
     int32_t *d_osd_order = nullptr;                   // OSD: per-block column order scratch
     size_t osd_order_bytes = 0;
-    // cluster (latency) kernel: codes for cl_nc CTAs per shot, or cl_nc == 0
-    int cl_nc = 0, cl_nb = 0, cl_clusters = 0;
+    // cluster kernel: codes for cl_nc CTAs per shot (cl_nc == 0: none);
+    // cl_mode 1 decodes every shot with it, 2 only the shots the two-shot
+    // kernel hands over at leg tail_legs (tail offload)
+    int cl_nc = 0, cl_nb = 0, cl_clusters = 0, cl_mode = 0;
+    int tail_legs = 0;
+    long long tail_max = 0;
+    TailRec *tail_rec = nullptr;
+    float *tail_M = nullptr;
+    uint32_t *tail_best = nullptr;
+    unsigned int *tail_count = nullptr;
     ClusterJob cl{};                                  // layout part (codes, sizes, plan)
     int32_t *cl_rslot = nullptr;
     uint32_t *cl_ecode = nullptr;
@@ -333,6 +341,7 @@ struct JobIO {
     int trace_iters;
     uint64_t *times = nullptr;
     FlagOut flag{};
+    TailOut tail{};             // two-shot kernel: hand long shots over (count NULL: no)
 };
 
 // FP64 in the literal evaluation order whenever one shot's per-edge messages
@@ -573,6 +582,7 @@ int launch_pair_nb(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     J.trace_iters = io.trace_iters;
     J.times_out = io.times;
     J.flag = io.flag;
+    J.tail = io.tail;
     const int warps = std::min(h->pair_warps > 0 ? h->pair_warps : pair_warps_heuristic(h),
                                pair_max_threads(NB) / 32);
     const int threads = 32 * warps;
@@ -664,6 +674,10 @@ int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     job.pobs_out = io.pobs;
     job.stats_out = io.stats;
     job.times_out = io.times;
+    if (io.tail.count) {                                // resume the handed-over shots
+        job.tail = io.tail;
+        job.shots = io.tail.max;
+    }
     int rc;
     switch (h->cl_nb) {
     case 2: rc = launch_cluster_nb<2>(h, sc, job, st); break;
@@ -678,18 +692,36 @@ int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     return rc;
 }
 
+// Tail offload applies to plain legs of plain decodes without per-shot
+// diagnostics (trace, flagged posteriors, times) or message carry-over.
+bool tail_applies(const relaybp_handle *h, const JobIO &io)
+{
+    if (h->cl_mode != 2 || io.trace || io.flag.post || io.times || h->params.carry_messages || h->lw) return false;
+    if ((h->lknots || h->lwrow) && (h->llegs < 0 || h->tail_legs < h->llegs)) return false;
+    return true;
+}
+
 int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st, bool on_chip_only)
 {
-    if (h->cl_nc > 0 && !h->lw && !h->lknots && !h->lwrow && !io.trace && !io.flag.post)
+    if (h->cl_mode == 1 && !h->lw && !h->lknots && !h->lwrow && !io.trace && !io.flag.post)
         return launch_cluster(h, sc, io, st);
     if (h->params.msg_dtype == RELAYBP_MSG_F64 && !h->lw && !h->lknots && !h->lwrow && !io.times) {
         int rc = launch_decode_exact(h, sc, io, st);
         if (rc <= 0) return rc;
     }
     {
-        int rc = launch_pair(h, sc, io, st);
+        JobIO io2 = io;
+        const bool tail = tail_applies(h, io);
+        if (tail) {
+            CUDA_TRY(cudaMemsetAsync(h->tail_count, 0, sizeof(unsigned int), st));
+            io2.tail = TailOut{h->tail_rec, h->tail_M, h->tail_best, h->tail_count, h->tail_max, h->tail_legs};
+        }
+        int rc = launch_pair(h, sc, io2, st);
         if (rc <= 0) {
-            if (rc == 0) h->launches += 1;
+            if (rc == 0) {
+                h->launches += 1;
+                if (tail) rc = launch_cluster(h, sc, io2, st);     // the handed-over shots, same stream
+            }
             return rc;
         }
     }
@@ -1138,7 +1170,7 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
     cudaFree(h->cl_halo[1]);
     h->cl_rslot = nullptr;
     h->cl_ecode = h->cl_halo[0] = h->cl_halo[1] = nullptr;
-    h->cl_nc = h->cl_nb = h->cl_clusters = 0;
+    h->cl_nc = h->cl_nb = h->cl_clusters = h->cl_mode = 0;
     if (cluster == 0) return 0;
     if (h->params.msg_dtype != RELAYBP_MSG_F32)
         return fail(RELAYBP_ERR_UNSUPPORTED, "the cluster kernel decodes FP32 messages");
@@ -1276,6 +1308,43 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
     J.nc = nc; J.Cc = Cc; J.CPc = CPc; J.lgcs = lgcs; J.NGc = NGc; J.Vc = Vc; J.lgv = lgv;
     h->cl_nc = nc;
     h->cl_nb = nb;
+    h->cl_mode = 1;
+    return 0;
+}
+
+int relaybp_set_tail_offload(relaybp_handle *h, int32_t legs, int32_t cluster, int64_t max_shots)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (legs < 0 || max_shots < 0) return fail(RELAYBP_ERR_INVALID, "legs and max_shots must be >= 0");
+    if (int rc = check_device(h)) return rc;
+    if (legs == 0) {                                    // off; the cluster layout stays for later use
+        if (h->cl_mode == 2) h->cl_mode = 0;
+        return 0;
+    }
+    if (h->params.carry_messages)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "tail offload restarts messages at a leg boundary (no carry-over)");
+    if (!h->rslot2) return fail(RELAYBP_ERR_UNSUPPORTED, "tail offload hands shots over from the two-shot kernel");
+    if (h->cl_nc != cluster || h->cl_mode == 0) {
+        if (int rc = relaybp_set_cluster_kernel(h, cluster)) return rc;
+    }
+    const long long mx = max_shots > 0 ? max_shots : 256;
+    if (mx != h->tail_max) {
+        cudaFree(h->tail_rec);
+        cudaFree(h->tail_M);
+        cudaFree(h->tail_best);
+        h->tail_rec = nullptr;
+        h->tail_M = nullptr;
+        h->tail_best = nullptr;
+        h->tail_max = 0;
+        CUDA_TRY(cudaMalloc(&h->tail_rec, (size_t)mx * sizeof(TailRec)));
+        CUDA_TRY(cudaMalloc(&h->tail_M, (size_t)mx * h->dem.V * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&h->tail_best, (size_t)mx * words(h->dem.V) * sizeof(uint32_t)));
+        h->tail_max = mx;
+    }
+    if (!h->tail_count) CUDA_TRY(cudaMalloc(&h->tail_count, sizeof(unsigned int)));
+    h->tail_legs = legs;
+    h->cl_mode = 2;
     return 0;
 }
 
@@ -2106,6 +2175,10 @@ int relaybp_destroy(relaybp_handle *h)
     cudaFree(h->cl_ecode);
     cudaFree(h->cl_halo[0]);
     cudaFree(h->cl_halo[1]);
+    cudaFree(h->tail_rec);
+    cudaFree(h->tail_M);
+    cudaFree(h->tail_best);
+    cudaFree(h->tail_count);
     cudaFree(h->d_stage_syn);
     cudaFree(h->d_stage_pobs);
     cudaFree(h->d_stage_stats);

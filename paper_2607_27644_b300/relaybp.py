@@ -76,6 +76,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_windows_decode": ([P, P, U64, I64, P, P, P, P, P], ctypes.c_int),
         "relaybp_windows_destroy": ([P], ctypes.c_int),
         "relaybp_set_cluster_kernel": ([P, I32], ctypes.c_int),
+        "relaybp_set_tail_offload": ([P, I32, I32, I64], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
         "relaybp_learned_tape_bytes": ([P, I32, I32, I64], I64),
@@ -101,7 +102,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 
 EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relaybp_set_learned_rows",
-            "relaybp_set_learned_legs", "relaybp_set_pair_kernel", "relaybp_set_cluster_kernel", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
+            "relaybp_set_learned_legs", "relaybp_set_pair_kernel", "relaybp_set_cluster_kernel", "relaybp_set_tail_offload", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_decode_flagged", "relaybp_osd", "relaybp_spa_create", "relaybp_spa_llr",
             "relaybp_spa_decode", "relaybp_spa_destroy", "relaybp_windows_create", "relaybp_windows_info",
             "relaybp_windows_handle", "relaybp_windows_decode", "relaybp_windows_destroy", "relaybp_count_failures", "relaybp_launch_count",
@@ -240,6 +241,12 @@ def relaybp_set_learned_rows(h: Handle, d_wrow=None, d_knots=None):
 def relaybp_set_cluster_kernel(h: Handle, cluster: int):
     """Decode each shot with a cluster of `cluster` CTAs (0: off)."""
     _check(_lib.relaybp_set_cluster_kernel(h.ptr, cluster), "relaybp_set_cluster_kernel")
+
+
+def relaybp_set_tail_offload(h: Handle, legs: int, cluster: int = 16, max_shots: int = 0):
+    """Hand shots about to start relay leg `legs` over to `cluster`-CTA
+    clusters (legs = 0: off); outputs unchanged bit for bit."""
+    _check(_lib.relaybp_set_tail_offload(h.ptr, legs, cluster, max_shots), "relaybp_set_tail_offload")
 
 
 def relaybp_set_learned_legs(h: Handle, legs: int):

@@ -1,0 +1,107 @@
+"""Tail offload: shots about to start relay leg `legs` leave the two-shot
+kernel and finish on thread-block clusters.  Both kernels evaluate the FP32
+Relay-BP iteration with the same operations in the same order, a new leg
+restarts the messages at zero, and the residual restarts consistent with
+e^ = 0, so every output -- corrections, predicted observables, per-shot
+statistics including the FP64 weight -- must equal a decode without offload
+bit for bit: with many shots handed over, with more shots than hand-over slots
+(the rest stay in the two-shot kernel), with every leg run, with learned
+legs before the hand-over leg, and through the host-buffer and allocation-free
+entry points."""
+import numpy as np
+import pytest
+import torch
+
+from workloads.dem import circuit_dem
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(gamma0=0.125, pre_iter=80, num_sets=1000, max_iterations=60, stop_nconv=5, gamma_min=-0.15,
+          gamma_max=0.61, seed=202)
+
+
+def _run(R, h, syn, shot0, entry="batch"):
+    n = syn.shape[0]
+    corr = torch.full((n, h.wv), -1, dtype=torch.int32, device="cuda")
+    pobs = torch.full((n, h.wk), -1, dtype=torch.int32, device="cuda")
+    stats = torch.full((n, 6), -1, dtype=torch.int32, device="cuda")
+    if entry == "batch":
+        R.relaybp_decode_batch(h, syn, shot0, n, corr, pobs, stats)
+    elif entry == "noalloc":
+        R.relaybp_decode_batch_noalloc(h, syn, shot0, n, corr, pobs, stats)
+    else:
+        hp = torch.full((n, h.wk), -1, dtype=torch.int32).pin_memory()
+        hs = torch.full((n, 6), -1, dtype=torch.int32).pin_memory()
+        R.relaybp_decode_host(h, syn.cpu().pin_memory(), shot0, n, hp, hs)
+        return None, hp.numpy(), hs.numpy()
+    torch.cuda.synchronize()
+    return corr.cpu().numpy(), pobs.cpu().numpy(), stats.cpu().numpy()
+
+
+def _equal(a, b):
+    for x, y in zip(a, b):
+        if x is not None and y is not None:
+            assert np.array_equal(x, y), int(np.sum(np.any(x != y, axis=1)))
+
+
+@pytest.fixture(scope="module")
+def dem4():
+    return circuit_dem("ZSZ-LP-160", 0.004, 10, "Z")
+
+
+@pytest.mark.parametrize("legs,cluster,cap,shots", [(3, 16, 1024, 1500), (2, 8, 16, 1200), (6, 4, 512, 600)])
+def test_offload_equals_plain(dem4, legs, cluster, cap, shots):
+    from paper_2607_27644_b300 import relaybp as R
+    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype="f32", **KW))
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 11, 40, shots, syn)
+    ref = _run(R, h, syn, 40)
+    st = ref[2]
+    assert (st[:, 2] > legs).sum() > 20                 # plenty of shots reach the hand-over leg
+    R.relaybp_set_tail_offload(h, legs, cluster, cap)
+    n0 = R.relaybp_launch_count(h)
+    got = _run(R, h, syn, 40)
+    assert R.relaybp_launch_count(h) - n0 == 2
+    _equal(got, ref)
+    if cap < 100:                                       # more long shots than slots: the rest stay put
+        assert (st[:, 2] > legs).sum() > cap
+    R.relaybp_set_tail_offload(h, 0)
+    _equal(_run(R, h, syn, 40), ref)
+    R.relaybp_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["stop_all", "learned", "host", "noalloc"])
+def test_offload_cases(dem4, case):
+    from paper_2607_27644_b300 import relaybp as R
+    kw = dict(KW)
+    if case == "stop_all":
+        kw.update(stop_all=True, num_sets=8)
+    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype="f32", **kw))
+    shots = 800
+    if case == "learned":
+        rng = np.random.default_rng(5)
+        wrow = torch.from_numpy(rng.uniform(0.7, 1.1, size=(6, dem4.n_det)).astype(np.float32)).cuda()
+        knots = torch.from_numpy(np.sort(rng.uniform(-0.2, 0.7, size=9)).astype(np.float32)).cuda()
+        R.relaybp_set_learned_rows(h, wrow, knots)
+        R.relaybp_set_learned_legs(h, 3)
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 12, 0, shots, syn)
+    entry = case if case in ("host", "noalloc") else "batch"
+    ref = _run(R, h, syn, 0, entry)
+    R.relaybp_set_tail_offload(h, 3, 16, 2048)
+    _equal(_run(R, h, syn, 0, entry), ref)
+    if case == "stop_all":
+        assert np.all(ref[2][:, 2] == 9)
+    R.relaybp_destroy(h)
+
+
+def test_offload_rejections(dem4):
+    from paper_2607_27644_b300 import relaybp as R
+    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype="f32", carry_messages=True, **KW))
+    with pytest.raises(R.RelayBPError, match="carry"):
+        R.relaybp_set_tail_offload(h, 3)
+    R.relaybp_destroy(h)
+    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype="f16", **KW))
+    with pytest.raises(R.RelayBPError):
+        R.relaybp_set_tail_offload(h, 3)
+    R.relaybp_destroy(h)
