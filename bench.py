@@ -58,6 +58,9 @@ def _args():
     ap.add_argument("--latency-max-shots", type=int, default=5,
                     help="latency: shots per code and basis timed with every relay leg run (max latency)")
     ap.add_argument("--cluster", type=int, default=16, help="latency: CTAs per thread-block cluster")
+    ap.add_argument("--tail-legs", type=int, default=50,
+                    help="zsz160: hand shots about to start this relay leg to cluster-kernel launches (0: off)")
+    ap.add_argument("--tail-cluster", type=int, default=8, help="zsz160: CTAs per cluster of the tail offload")
     ap.add_argument("--sweep-shots", type=int, default=200_000, help="gamma_sweep: shots per point and basis")
     ap.add_argument("--stream-batch", type=int, default=1 << 16, help="stream550: shots per graph batch")
     ap.add_argument("--train-steps", type=int, default=300, help="learned: Adam steps of 512 shots at p=0.2%%")
@@ -223,6 +226,10 @@ def run_ours(a):
     msg = a.msg or "f32"
     hs = [R.relaybp_build_dem(dem, R.Params(msg_dtype=msg, **DECODER)) for _ in range(NS)]
     h = hs[0]
+    tail = a.tail_legs if msg == "f32" else 0
+    for x in hs:
+        if tail:
+            R.relaybp_set_tail_offload(x, tail, a.tail_cluster, 256)
     B, K, W = a.batch, a.steps, a.warmup
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     st = streams[0]
@@ -354,6 +361,8 @@ def run_ours(a):
                 if kind == "learned":
                     R.relaybp_set_learned_rows(x, wrow, knots)
                     R.relaybp_set_learned_legs(x, 50)
+                if tail:                        # past the learned legs, both arms alike
+                    R.relaybp_set_tail_offload(x, max(tail, 50), a.tail_cluster, 256)
                 hk.append(x)
             cnt_k = torch.zeros(4, dtype=torch.int64, device=dev)
             it_k = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -454,7 +463,10 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": msg, "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEM (no dataset)",
-            "config": _config(dem, B, K, world, streams=NS), "clocks": clk.summary(), "gpu_launches": launches * world,
+            "config": _config(dem, B, K, world, streams=NS, extra={
+                "tail_offload": ({"legs": tail, "cluster_ctas": a.tail_cluster,
+                                  "note": "shots about to start this relay leg finish on thread-block clusters "
+                                          "(bit-identical outputs)"} if tail else None)}), "clocks": clk.summary(), "gpu_launches": launches * world,
             "roofline": roof, "e2e": e2e,
             "ler": {"shots": c[0], "failures": c[3], "nonconverged": c[1], "logical": c[2],
                     "block_ler": c[3] / max(1, c[0])},
