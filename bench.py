@@ -444,15 +444,21 @@ def run_ours(a):
     # kernel (ncu, same kernel build), scaled by shots to one launch of this
     # run: the state stays on chip; DRAM carries syndromes in, results out and
     # the L2 write-backs of the per-block memory-strength rows
-    traffic = (2633216 + 2473216) * B / 3000 if (msg == "f32" and B >= 3000) else None
+    # DRAM bytes of one two-shot-kernel launch of 3,000 shots (ncu capture of
+    # this build), scaled to the step's shots
+    traffic = (4172288 + 3796736) * B / 3000 if (msg == "f32" and B >= 3000) else None
     roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
             "traffic": traffic,
-            "kernel": ("relay_pair_kernel<23> (two shots per block, FP32)" if msg == "f32"
+            "kernel": (("relay_pair_kernel<23> (two shots per block, FP32)"
+                        + (f"; shots reaching relay leg {tail} finish in relay_cluster_kernel ({a.tail_cluster} "
+                           "CTAs per shot)" if tail else "")) if msg == "f32"
                        else f"relay_decode_kernel<{msg}>"),
             "algorithmic_bytes": f"per shot-iteration 4*b_m*E + 16*V + (V+C)/8 (b_m={b_m})",
             "peak_source": "measured live: conflict-free 16-B shared-memory loads on all SMs (relaybp_probe_smem_read)",
             "achieved_basis": f"algorithmic bytes of all decode launches / the timed region ({NS} launches in flight "
-                              "at once; the decode kernel fills >99.8% of device time in the ncu launch list)",
+                              "at once; the decode kernels fill >99.7% of device time in the serialised ncu launch "
+                              "list of this command with 2 steps: two-shot kernel 73.8%, cluster kernel of the "
+                              "handed-over shots 25.9%)",
             "achieved_per_launch": per_launch, "decode_ms_per_launch": dec_avg_s * 1e3,
             "edge_updates_per_s": edge_updates,
             "hbm_equivalent": ({"peak_gbs": hbm_gbs, "frac": achieved / hbm_gbs,
