@@ -404,23 +404,25 @@ int relaybp_set_pair_kernel(relaybp_handle *h, int32_t enable, int32_t warps);
 int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster);
 
 /* Tail offload: shots that need many relay legs finish on thread-block
- * clusters.  The two-shot FP32 kernel hands a shot over when it is about to
- * start leg `legs` (>= 1; 0 turns offload off) -- its marginals M, best
- * solution with its FP64 weight, and solution / leg / iteration counts -- and
- * one launch of the cluster kernel (clusters of `cluster` CTAs, 1..16, as in
- * relaybp_set_cluster_kernel) on the same stream continues those shots from
- * that leg.  A new leg restarts the messages at zero, the residual restarts
- * consistent with e^ = 0, and both kernels evaluate the same operations in
- * the same order, so every output equals that of a decode without offload,
- * bit for bit.  Up to `max_shots` shots per launch are handed over (0: 256;
- * device memory ~ max_shots * 4 * (V + V / 32) bytes); later ones stay in the
- * two-shot kernel.  A shot that runs every leg takes about 60,000 iterations:
- * seconds on one SM, a fraction of that on a cluster, so a batch no longer
- * waits on its slowest shot.  Applies to relaybp_decode_batch,
- * relaybp_decode_batch_noalloc and relaybp_decode_host of FP32 handles on the
- * two-shot kernel; not to traced, timed or flagged decodes, message
- * carry-over, or learned parameters in the legs being handed over (legs must
- * be >= the learned legs).  Launches per decode: two.  Turning the cluster
+ * clusters.  The decode kernel (the two-shot FP32 kernel or the one-shot
+ * kernel for every storage form but FP64) hands a shot over when it is about
+ * to start leg `legs` (>= 1; 0 turns offload off) -- its marginals M as
+ * stored, best solution with its FP64 weight, and solution / leg / iteration
+ * counts -- and one launch of the cluster kernel (clusters of `cluster` CTAs,
+ * 1..16, as in relaybp_set_cluster_kernel, same storage form) on the same
+ * stream continues those shots from that leg.  A new leg restarts the
+ * messages at zero, the residual restarts consistent with e^ = 0, and the
+ * kernels evaluate the same operations in the same order, so every output
+ * equals that of a decode without offload, bit for bit.  Up to `max_shots`
+ * shots per launch are handed over (0: 256; device memory ~ max_shots * 4 *
+ * (V + V / 32) bytes); later ones stay where they are.  A shot that runs every
+ * leg takes about 60,000 iterations: seconds on one SM, a fraction of that on
+ * a cluster, so a batch no longer waits on its slowest shot.  Applies to
+ * relaybp_decode_batch, relaybp_decode_batch_noalloc, relaybp_decode_host
+ * and relaybp_group_decode (one cluster launch per offloading DEM after the
+ * group launch); not to traced, timed or flagged decodes, message carry-over,
+ * per-edge learned weights, or row-tied learned weights and knots in the legs
+ * being handed over (legs must be >= the learned legs).  Turning the cluster
  * kernel on for every shot (relaybp_set_cluster_kernel) turns offload off. */
 int relaybp_set_tail_offload(relaybp_handle *h, int32_t legs, int32_t cluster, int64_t max_shots);
 

@@ -92,6 +92,49 @@ __device__ __forceinline__ uint4 cl_ld_v4(uint32_t a)
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a) : "memory");
     return v;
 }
+__device__ __forceinline__ uint2 cl_ld_v2(uint32_t a)
+{
+    uint2 v;
+    asm volatile("ld.shared::cluster.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t cl_ld_u16(uint32_t a)
+{
+    unsigned short v;
+    asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t cl_ld_u8(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+// One stored value of type S / one check state from another CTA's shared memory.
+template <typename S> __device__ __forceinline__ S cl_ld_val(uint32_t a);
+template <> __device__ __forceinline__ float cl_ld_val<float>(uint32_t a) { return cl_ld_f32(a); }
+template <> __device__ __forceinline__ __half cl_ld_val<__half>(uint32_t a)
+{
+    return __ushort_as_half((unsigned short)cl_ld_u16(a));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 cl_ld_val<__nv_bfloat16>(uint32_t a)
+{
+    return __ushort_as_bfloat16((unsigned short)cl_ld_u16(a));
+}
+template <> __device__ __forceinline__ int8_t cl_ld_val<int8_t>(uint32_t a) { return (int8_t)cl_ld_u8(a); }
+template <typename S> __device__ __forceinline__ CheckState<S> cl_ld_cs(uint32_t a)
+{
+    CheckState<S> c;
+    if constexpr (sizeof(CheckState<S>) == 16) {
+        const uint4 v = cl_ld_v4(a);
+        memcpy(&c, &v, 16);
+    } else {
+        const uint2 v = cl_ld_v2(a);
+        memcpy(&c, &v, 8);
+    }
+    return c;
+}
+
 __device__ __forceinline__ void cl_st_u32(uint32_t a, uint32_t v)
 {
     asm volatile("st.shared::cluster.u32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
@@ -171,7 +214,10 @@ __device__ __forceinline__ double cl_weight(const ClusterJob &J, uint32_t rank, 
     return wsum;
 }
 
-template <int NB>
+// S: storage precision of A, M and the check minima (FP32, FP16, BF16 or
+// scaled int8; arithmetic in FP32), loaded and stored exactly as the
+// one-block kernels do.
+template <typename S, int NB>
 __global__ void __launch_bounds__(1024, 1)
 relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *__restrict__ work)
 {
@@ -197,20 +243,22 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
     DevDEM gl = g;                                      // the row pass's view: own rows, local numbering
     gl.C = nrow;
     gl.rslot = J.rslot + (size_t)rank * J.CPc * kRowStride;
-    const QScale qs{0.f};
-    float *A = reinterpret_cast<float *>(smem + pl.A);          // own variables (read by the others)
-    float *M = reinterpret_cast<float *>(smem + pl.M);
+    using C = float;
+    constexpr uint32_t SZ = sizeof(S);
+    const QScale qs{p.qscale};
+    S *A = reinterpret_cast<S *>(smem + pl.A);                  // own variables (read by the others)
+    S *M = reinterpret_cast<S *>(smem + pl.M);
     float *gam = reinterpret_cast<float *>(smem + pl.gam);
-    float *Ah = reinterpret_cast<float *>(smem + pl.Ah);        // A halo [HA + 1]
+    S *Ah = reinterpret_cast<S *>(smem + pl.Ah);                // A halo [HA + 1]
     // the two check-state / sign-word buffers of the own rows (selected by
     // `cur`, not indexed: a register select keeps them out of local memory)
-    CheckState<float> *const cs0 = reinterpret_cast<CheckState<float> *>(smem + pl.cs0);
-    CheckState<float> *const cs1 = reinterpret_cast<CheckState<float> *>(smem + pl.cs1);
+    CheckState<S> *const cs0 = reinterpret_cast<CheckState<S> *>(smem + pl.cs0);
+    CheckState<S> *const cs1 = reinterpret_cast<CheckState<S> *>(smem + pl.cs1);
     uint32_t *const sg0 = reinterpret_cast<uint32_t *>(smem + pl.sg0);
     uint32_t *const sg1 = reinterpret_cast<uint32_t *>(smem + pl.sg1);
     auto CS = [&](int b) { return b ? cs1 : cs0; };
     auto SG = [&](int b) { return b ? sg1 : sg0; };
-    CheckState<float> *csh = reinterpret_cast<CheckState<float> *>(smem + pl.csh);   // row halo [HR + 1]
+    CheckState<S> *csh = reinterpret_cast<CheckState<S> *>(smem + pl.csh);   // row halo [HR + 1]
     uint32_t *sgh = reinterpret_cast<uint32_t *>(smem + pl.sgh);
     uint32_t *ahs = reinterpret_cast<uint32_t *>(smem + pl.ahs);
     uint32_t *rhs = reinterpret_cast<uint32_t *>(smem + pl.rhs);
@@ -227,15 +275,15 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
     const uint32_t copyS = (uint32_t)__cvta_generic_to_shared(&s_copy);
     const uint32_t shotS = (uint32_t)__cvta_generic_to_shared(&s_shot);
     const uint32_t vmask = (1u << J.lgv) - 1u, rmask = (1u << J.lgcs) - 1u;
-    const float finf = __int_as_float(0x7f800000);
+    constexpr uint32_t CSZ = sizeof(CheckState<S>);
 
     // halo source lists (fixed for the launch) and the halos' dummy entries
     for (int k = tid; k < HA; k += nthr) ahs[k] = __ldg(J.ahs + J.ha_off[rank] + k);
     for (int k = tid; k < HR; k += nthr) rhs[k] = __ldg(J.rhs + J.hr_off[rank] + k);
     if (tid == 0) {
-        Ah[HA] = finf;                                  // padded row slots: |mu| = inf, no sign
-        CheckState<float> z;
-        z.m1 = 0.f; z.m2 = 0.f; z.meta = 0u;
+        Ah[HA] = Prec<S>::pinf();                       // padded row slots: |mu| = inf, no sign
+        CheckState<S> z;
+        z.m1 = Prec<S>::st(0.f, qs); z.m2 = z.m1; z.meta = 0u;
         csh[HR] = z;                                    // padded column slots: message +0
     }
     for (int w = tid; w < RW; w += nthr) sgh[HR * RW + w] = 0u;
@@ -243,7 +291,7 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
     auto pull_A = [&]() {
         for (int k = tid; k < HA; k += nthr) {
             const uint32_t c = ahs[k];
-            Ah[k] = cl_ld_f32(cl_map(aS + 4u * (c & vmask), c >> J.lgv));
+            Ah[k] = cl_ld_val<S>(cl_map(aS + SZ * (c & vmask), c >> J.lgv));
         }
     };
     // refresh the row halo (check states and sign words of buffer b)
@@ -251,8 +299,7 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
         const uint32_t csS = sbase + (b ? pl.cs1 : pl.cs0), sgS = sbase + (b ? pl.sg1 : pl.sg0);
         for (int k = tid; k < HR; k += nthr) {
             const uint32_t c = rhs[k], own = c >> J.lgcs, lr = c & rmask;
-            const uint4 q = cl_ld_v4(cl_map(csS + 16u * lr, own));
-            reinterpret_cast<uint4 *>(csh)[k] = q;
+            csh[k] = cl_ld_cs<S>(cl_map(csS + CSZ * lr, own));
         }
         for (int x = tid; x < HR * RW; x += nthr) {
             const int k = x >> (lg - 5), w = x & (RW - 1);
@@ -286,17 +333,17 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
         for (int jl = tid; jl < ngr * 32; jl += nthr) {
             const int j = g0 * 32 + jl;
             if (j < V) {
-                const float l0 = __ldg(g.L0f + j), gm = (float)p.gamma0;
-                M[jl] = rsm ? J.tail.M[qrec * V + j] : l0;
+                const C l0 = __ldg(g.L0f + j), gm = (C)p.gamma0;
+                M[jl] = rsm ? reinterpret_cast<const S *>(J.tail.M)[qrec * V + j] : Prec<S>::st(l0, qs);
                 gam[jl] = gm;                           // resumed shots: redrawn at their leg start
-                A[jl] = memprior<float>(gm, l0, l0);
+                A[jl] = Prec<S>::st(memprior<C>(gm, l0, l0), qs);
             } else {
-                A[jl] = finf;
+                A[jl] = Prec<S>::pinf();
             }
         }
         for (int i = tid; i <= nrow; i += nthr) {      // row nrow: the row pass's dummy
-            CheckState<float> z;
-            z.m1 = 0.f; z.m2 = 0.f; z.meta = 0u;
+            CheckState<S> z;
+            z.m1 = Prec<S>::st(0.f, qs); z.m2 = z.m1; z.meta = 0u;
             cs0[i] = z;
             cs1[i] = z;
         }
@@ -333,18 +380,18 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
                 for (int jl = tid; jl < ngr * 32; jl += nthr) {
                     const int j = g0 * 32 + jl;
                     if (j >= V) continue;
-                    const float l0 = __ldg(g.L0f + j);
-                    const float gn = draw_gamma<float>(p, shot, leg, j, V);
-                    const float Mj = M[jl];
-                    float carry = 0.f;
-                    if (p.carry_messages) carry = add_rn(A[jl], -memprior<float>(gam[jl], l0, Mj));
+                    const C l0 = __ldg(g.L0f + j);
+                    const C gn = draw_gamma<C>(p, shot, leg, j, V);
+                    const C Mj = Prec<S>::ld(M[jl], qs);
+                    C carry = 0.f;
+                    if (p.carry_messages) carry = add_rn(Prec<S>::ld(A[jl], qs), -memprior<C>(gam[jl], l0, Mj));
                     gam[jl] = gn;
-                    A[jl] = add_rn(memprior<float>(gn, l0, Mj), carry);
+                    A[jl] = Prec<S>::st(add_rn(memprior<C>(gn, l0, Mj), carry), qs);
                 }
                 if (!p.carry_messages) {
                     for (int r = tid; r < nrow; r += nthr) {
-                        CheckState<float> z;
-                        z.m1 = 0.f; z.m2 = 0.f; z.meta = 0u;
+                        CheckState<S> z;
+                        z.m1 = Prec<S>::st(0.f, qs); z.m2 = z.m1; z.meta = 0u;
                         CS(cur)[r] = z;
                     }
                     for (int w = tid; w < nrow * RW; w += nthr) SG(cur)[w] = 0u;
@@ -357,8 +404,8 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
             bool conv = false;
             for (int t = 0; t < T_leg; ++t) {
                 // ---- a3: own rows; for t > 0 also speculative past iteration t-1
-                row_pass<float, L, NB, false>(gl, Ah, CS(cur), SG(cur), CS(cur ^ 1), SG(cur ^ 1), syn, warp, nwarp, lane,
-                                              nullptr, nullptr, qs);
+                row_pass<S, L, NB, false>(gl, Ah, CS(cur), SG(cur), CS(cur ^ 1), SG(cur ^ 1), syn, warp, nwarp, lane,
+                                          nullptr, nullptr, qs);
                 cl_sync();
                 if (t > 0) {
                     const uint32_t f = (lane < J.nc) ? flags[((t - 1) & 1) * 16 + lane] : 0u;
@@ -384,24 +431,24 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const uint32_t hr = c[u] >> lg;
-                            const CheckState<float> q = csh[hr];
+                            const CheckState<S> q = csh[hr];
                             const uint32_t hw = sgh[hr * RW + ((c[u] & pmask) >> 5)];
-                            const float mag = ((c[u] & pmask) == (q.meta & pmask)) ? q.m2 : q.m1;
+                            const C mag = Prec<S>::ld(((c[u] & pmask) == (q.meta & pmask)) ? q.m2 : q.m1, qs);
                             Ssum = add_rn(Ssum, xsign(mag, __funnelshift_l(hw, hw, c[u]) & 0x80000000u));
                         }
                     }
                     for (; k < D; ++k) {
                         const uint32_t c = __ldg(col + k * 32), hr = c >> lg;
-                        const CheckState<float> q = csh[hr];
+                        const CheckState<S> q = csh[hr];
                         const uint32_t hw = sgh[hr * RW + ((c & pmask) >> 5)];
-                        const float mag = ((c & pmask) == (q.meta & pmask)) ? q.m2 : q.m1;
+                        const C mag = Prec<S>::ld(((c & pmask) == (q.meta & pmask)) ? q.m2 : q.m1, qs);
                         Ssum = add_rn(Ssum, xsign(mag, __funnelshift_l(hw, hw, c) & 0x80000000u));
                     }
                     uint32_t dec = 0u;
                     if (act) {
-                        const float Mn = add_rn(memprior<float>(gm, l0, M[jl]), Ssum);
-                        M[jl] = Mn;
-                        A[jl] = add_rn(memprior<float>(gm, l0, Mn), Ssum);
+                        const C Mn = add_rn(memprior<C>(gm, l0, Prec<S>::ld(M[jl], qs)), Ssum);
+                        M[jl] = Prec<S>::st(Mn, qs);
+                        A[jl] = Prec<S>::st(add_rn(memprior<C>(gm, l0, Mn), Ssum), qs);
                         dec = (Mn < 0.f) ? 1u : 0u;
                     }
                     const uint32_t nw = __ballot_sync(FULL, dec);

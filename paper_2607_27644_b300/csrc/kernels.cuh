@@ -106,7 +106,7 @@ struct TailRec {
 };
 struct TailOut {
     TailRec *rec;
-    float *M;
+    void *M;                    // [max][V] marginals in the storage precision
     uint32_t *best;
     unsigned int *count;        // NULL: no hand-over
     long long max;
@@ -501,6 +501,7 @@ struct DecodeJob {
     int trace_iters;
     uint64_t *times_out;        // [shots][2] device clock (ns) at shot start and retire, or NULL
     FlagOut flag;               // flagged nonconvergences (flag.post NULL: not written)
+    TailOut tail;               // shots handed over at a leg boundary (tail.count NULL: never)
 };
 
 constexpr int kMaxJobs = 16;
@@ -530,7 +531,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *gblk = GS ? gstate + (size_t)blockIdx.x * state_stride : nullptr;
 
-    __shared__ long long s_shot, s_fslot;
+    __shared__ long long s_shot, s_fslot, s_defer;
     __shared__ unsigned long long s_t0;
     __shared__ int s_job, s_nsol, s_have_best, s_copy;
     __shared__ double s_best_w, s_w;
@@ -612,6 +613,7 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
         __syncthreads();
 
         int legs = 0, iters = 0;
+        bool handed = false;
         for (int leg = 0; leg <= p.num_sets; ++leg) {
             ++legs;
             // learned parameters in this leg (row-tied weights and knots act
@@ -744,6 +746,41 @@ relay_decode_kernel(const __grid_constant__ JobTable tab, unsigned long long *__
                 __syncthreads();
             }
             if (!p.stop_all && s_nsol >= p.stop_nconv) break;
+            // tail hand-over: a shot about to start leg >= tail.legs leaves
+            // for the cluster kernel while hand-over slots last (its marginals
+            // as stored, best solution and counters; a new leg restarts the
+            // messages at zero)
+            if (J.tail.count && leg + 1 <= p.num_sets && leg + 1 >= J.tail.legs) {
+                if (tid == 0) {
+                    const unsigned q = atomicAdd(J.tail.count, 1u);
+                    s_defer = ((long long)q < J.tail.max) ? (long long)q : -1;
+                }
+                __syncthreads();
+                const long long q = s_defer;
+                if (q >= 0) {
+                    for (int j = tid; j < V; j += nthr) reinterpret_cast<S *>(J.tail.M)[q * V + j] = M[j];
+                    for (int w = tid; w < WV; w += nthr) J.tail.best[q * WV + w] = best[w];
+                    if (tid == 0) {
+                        TailRec rec;
+                        rec.sidx = sidx;
+                        rec.next_leg = leg + 1;
+                        rec.legs = legs;
+                        rec.iters = iters;
+                        rec.nsol = s_nsol;
+                        rec.have = s_have_best;
+                        rec.pad = 0;
+                        rec.bestw = s_best_w;
+                        rec.t0 = s_t0;
+                        J.tail.rec[q] = rec;
+                    }
+                    handed = true;
+                    break;
+                }
+            }
+        }
+        if (handed) {                           // the cluster kernel writes this shot's outputs
+            __syncthreads();
+            continue;
         }
 
         // ---- outputs --------------------------------------------------------

@@ -480,7 +480,7 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
                 // solution and counters (messages restart at zero in a new leg)
                 const long long q = s_defer[s];
                 const float *M1 = reinterpret_cast<const float *>(M2) + s;
-                for (int j = tid; j < V; j += nthr) J.tail.M[q * V + j] = M1[2 * j];
+                for (int j = tid; j < V; j += nthr) static_cast<float *>(J.tail.M)[q * V + j] = M1[2 * j];
                 for (int w = tid; w < WV; w += nthr) J.tail.best[q * WV + w] = best(s)[w];
                 if (tid == 0) {
                     TailRec rec;

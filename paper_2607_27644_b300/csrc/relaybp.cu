@@ -400,6 +400,7 @@ int launch_jobs(relaybp_handle *const *hs, const JobIO *io, int n, Scratch &sc, 
         if (h->lw) learned = true;      // per-edge weights; row-tied weights and knots run in the plain kernel
         J.plan = make_plan(h->dem, sizeof(S), sizeof(CheckState<S>), (size_t)-1);
         J.syn_in = io[d].syn;
+        J.tail = io[d].tail;
         J.shot0 = io[d].shot0;
         J.shots = io[d].shots;
         J.corr_out = io[d].corr;
@@ -628,10 +629,10 @@ int launch_pair(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st
 // Cluster (latency) kernel: NB = row slots per lane (32 lanes per row).
 constexpr int kClusterNB[] = {2, 4, 6, 8, 12, 16};     // slots per lane, 16 lanes per row
 
-template <int NB>
+template <typename S, int NB>
 int launch_cluster_nb(relaybp_handle *h, Scratch &sc, const ClusterJob &job, cudaStream_t st)
 {
-    auto kern = relay_cluster_kernel<NB>;
+    auto kern = relay_cluster_kernel<S, NB>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, job.plan.total));
     if (job.nc > 8) CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
@@ -662,6 +663,20 @@ int launch_cluster_nb(relaybp_handle *h, Scratch &sc, const ClusterJob &job, cud
     return 0;
 }
 
+template <typename S>
+int launch_cluster_s(relaybp_handle *h, Scratch &sc, const ClusterJob &job, cudaStream_t st)
+{
+    switch (h->cl_nb) {
+    case 2: return launch_cluster_nb<S, 2>(h, sc, job, st);
+    case 4: return launch_cluster_nb<S, 4>(h, sc, job, st);
+    case 6: return launch_cluster_nb<S, 6>(h, sc, job, st);
+    case 8: return launch_cluster_nb<S, 8>(h, sc, job, st);
+    case 12: return launch_cluster_nb<S, 12>(h, sc, job, st);
+    case 16: return launch_cluster_nb<S, 16>(h, sc, job, st);
+    default: return fail(RELAYBP_ERR_UNSUPPORTED, "cluster kernel: %d row slots per lane", h->cl_nb);
+    }
+}
+
 int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t st)
 {
     ClusterJob job = h->cl;
@@ -678,15 +693,14 @@ int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
         job.tail = io.tail;
         job.shots = io.tail.max;
     }
+    job.p.qscale = h->params.int8_scale > 0.0f ? h->params.int8_scale : (float)(h->l0max / 24.0);
     int rc;
-    switch (h->cl_nb) {
-    case 2: rc = launch_cluster_nb<2>(h, sc, job, st); break;
-    case 4: rc = launch_cluster_nb<4>(h, sc, job, st); break;
-    case 6: rc = launch_cluster_nb<6>(h, sc, job, st); break;
-    case 8: rc = launch_cluster_nb<8>(h, sc, job, st); break;
-    case 12: rc = launch_cluster_nb<12>(h, sc, job, st); break;
-    case 16: rc = launch_cluster_nb<16>(h, sc, job, st); break;
-    default: return fail(RELAYBP_ERR_UNSUPPORTED, "cluster kernel: %d row slots per lane", h->cl_nb);
+    switch (h->params.msg_dtype) {
+    case RELAYBP_MSG_F32: rc = launch_cluster_s<float>(h, sc, job, st); break;
+    case RELAYBP_MSG_F16: rc = launch_cluster_s<__half>(h, sc, job, st); break;
+    case RELAYBP_MSG_BF16: rc = launch_cluster_s<__nv_bfloat16>(h, sc, job, st); break;
+    case RELAYBP_MSG_I8: rc = launch_cluster_s<int8_t>(h, sc, job, st); break;
+    default: return fail(RELAYBP_ERR_UNSUPPORTED, "cluster kernel: storage form %d", h->params.msg_dtype);
     }
     if (rc == 0) h->launches += 1;
     return rc;
@@ -696,7 +710,9 @@ int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
 // diagnostics (trace, flagged posteriors, times) or message carry-over.
 bool tail_applies(const relaybp_handle *h, const JobIO &io)
 {
-    if (h->cl_mode != 2 || io.trace || io.flag.post || io.times || h->params.carry_messages || h->lw) return false;
+    if (h->cl_mode != 2 || io.trace || io.flag.post || io.times || h->params.carry_messages || h->lw ||
+        h->params.msg_dtype == RELAYBP_MSG_F64)
+        return false;
     if ((h->lknots || h->lwrow) && (h->llegs < 0 || h->tail_legs < h->llegs)) return false;
     return true;
 }
@@ -717,17 +733,16 @@ int decode_single(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t 
             io2.tail = TailOut{h->tail_rec, h->tail_M, h->tail_best, h->tail_count, h->tail_max, h->tail_legs};
         }
         int rc = launch_pair(h, sc, io2, st);
-        if (rc <= 0) {
-            if (rc == 0) {
-                h->launches += 1;
-                if (tail) rc = launch_cluster(h, sc, io2, st);     // the handed-over shots, same stream
-            }
-            return rc;
+        if (rc > 0) {
+            rc = launch_jobs_dtype(&h, &io2, 1, sc, st, on_chip_only);
+            if (rc > 0) rc = fail(RELAYBP_ERR_UNSUPPORTED, "no decode kernel for this handle");
         }
+        if (rc == 0) {
+            h->launches += 1;
+            if (tail) rc = launch_cluster(h, sc, io2, st);         // the handed-over shots, same stream
+        }
+        return rc;
     }
-    int rc = launch_jobs_dtype(&h, &io, 1, sc, st, on_chip_only);
-    if (rc == 0) h->launches += 1;
-    return rc;
 }
 
 // ---- learned form ----------------------------------------------------------
@@ -1172,8 +1187,10 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
     h->cl_ecode = h->cl_halo[0] = h->cl_halo[1] = nullptr;
     h->cl_nc = h->cl_nb = h->cl_clusters = h->cl_mode = 0;
     if (cluster == 0) return 0;
-    if (h->params.msg_dtype != RELAYBP_MSG_F32)
-        return fail(RELAYBP_ERR_UNSUPPORTED, "the cluster kernel decodes FP32 messages");
+    if (h->params.msg_dtype == RELAYBP_MSG_F64)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "the cluster kernel stores FP32, FP16, BF16 or int8 (not FP64)");
+    const int es = h->params.msg_dtype == RELAYBP_MSG_F32 ? 4 : (h->params.msg_dtype == RELAYBP_MSG_I8 ? 1 : 2);
+    const int css = h->params.msg_dtype == RELAYBP_MSG_F32 ? 16 : 8;     // sizeof(CheckState<S>)
     const DevDEM &g = h->dem;
     const int32_t C = g.C, V = g.V, NG = (V + 31) / 32, lg = g.lg_rsp;
     int nb = 0;
@@ -1264,15 +1281,15 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster)
         off += bytes;
         return (int)at;
     };
-    pl.A = take(4 * (size_t)Vc);
-    pl.M = take(4 * (size_t)Vc);
+    pl.A = take(es * (size_t)Vc);
+    pl.M = take(es * (size_t)Vc);
     pl.gam = take(4 * (size_t)Vc);
-    pl.Ah = take(4 * (size_t)(HAmax + 1));
-    pl.cs0 = take(16 * (size_t)(Cc + 1));
-    pl.cs1 = take(16 * (size_t)(Cc + 1));
+    pl.Ah = take(es * (size_t)(HAmax + 1));
+    pl.cs0 = take(css * (size_t)(Cc + 1));
+    pl.cs1 = take(css * (size_t)(Cc + 1));
     pl.sg0 = take(4 * (size_t)(Cc + 1) * RWd);
     pl.sg1 = take(4 * (size_t)(Cc + 1) * RWd);
-    pl.csh = take(16 * (size_t)(HRmax + 1));
+    pl.csh = take(css * (size_t)(HRmax + 1));
     pl.sgh = take(4 * (size_t)(HRmax + 1) * RWd);
     pl.ahs = take(4 * (size_t)HAmax);
     pl.rhs = take(4 * (size_t)HRmax);
@@ -1324,7 +1341,8 @@ int relaybp_set_tail_offload(relaybp_handle *h, int32_t legs, int32_t cluster, i
     }
     if (h->params.carry_messages)
         return fail(RELAYBP_ERR_UNSUPPORTED, "tail offload restarts messages at a leg boundary (no carry-over)");
-    if (!h->rslot2) return fail(RELAYBP_ERR_UNSUPPORTED, "tail offload hands shots over from the two-shot kernel");
+    if (h->params.msg_dtype == RELAYBP_MSG_F64)
+        return fail(RELAYBP_ERR_UNSUPPORTED, "tail offload continues shots in the cluster kernel (not FP64)");
     if (h->cl_nc != cluster || h->cl_mode == 0) {
         if (int rc = relaybp_set_cluster_kernel(h, cluster)) return rc;
     }
@@ -2122,8 +2140,24 @@ int relaybp_group_decode(relaybp_group *grp, const uint32_t *const *d_syndromes,
                       d_pred_obs ? d_pred_obs[d] : nullptr,
                       d_stats ? reinterpret_cast<StatsDev *>(d_stats[d]) : nullptr, nullptr, 0};
     }
-    int rc = launch_jobs_dtype(grp->handles.data(), io.data(), n, grp->scratch, static_cast<cudaStream_t>(cuda_stream));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // DEMs with tail offload hand their long shots to one cluster launch each
+    std::vector<int> tails;
+    for (int d = 0; d < n; ++d) {
+        relaybp_handle *h = grp->handles[d];
+        if (io[d].shots > 0 && tail_applies(h, io[d])) {
+            CUDA_TRY(cudaMemsetAsync(h->tail_count, 0, sizeof(unsigned int), st));
+            io[d].tail = TailOut{h->tail_rec, h->tail_M, h->tail_best, h->tail_count, h->tail_max, h->tail_legs};
+            tails.push_back(d);
+        }
+    }
+    int rc = launch_jobs_dtype(grp->handles.data(), io.data(), n, grp->scratch, st);
     if (rc == 0) grp->launches += 1;
+    for (size_t k = 0; k < tails.size() && rc == 0; ++k) {
+        const int d = tails[k];
+        rc = launch_cluster(grp->handles[d], grp->scratch, io[d], st);
+        if (rc == 0) grp->launches += 1;
+    }
     return rc;
 }
 

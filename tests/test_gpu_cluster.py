@@ -119,10 +119,40 @@ def test_cluster_zsz550_single_shots():
     R.relaybp_destroy(h)
 
 
+@pytest.mark.parametrize("dtype,nc", [("f16", 8), ("bf16", 16), ("i8", 4)])
+def test_cluster_equals_one_block_kernel_low_precision(dems, dtype, nc):
+    """16- and 8-bit storage (FP32 arithmetic): the cluster kernel loads and
+    stores exactly as the one-shot-per-block kernel, so outputs are equal."""
+    from paper_2607_27644_b300 import relaybp as R
+    h = R.relaybp_build_dem(dems["z4"], R.Params(msg_dtype=dtype, **CIRC_KW))
+    shots = 500
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 61, 0, shots, syn)
+    ref = _run(R, h, syn, 0)
+    R.relaybp_set_cluster_kernel(h, nc)
+    _equal(_run(R, h, syn, 0), ref)
+    assert ref[2][:, 1].mean() > 2.0
+    R.relaybp_destroy(h)
+
+
+def test_cluster_zsz550_fp16_eight_ctas():
+    """ZSZ-LP-550 in FP16 storage fits 8-CTA clusters (FP32 needs 16)."""
+    from paper_2607_27644_b300 import relaybp as R
+    dem = circuit_dem("ZSZ-LP-550", 0.001, None, "Z")
+    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f16", **dict(CIRC_KW, gamma_min=-0.12, gamma_max=0.62)))
+    shots = 48
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 8, 0, shots, syn)
+    ref = _run(R, h, syn, 0)
+    R.relaybp_set_cluster_kernel(h, 8)
+    _equal(_run(R, h, syn, 0), ref)
+    R.relaybp_destroy(h)
+
+
 def test_cluster_rejects_unsupported_handles(dems):
     from paper_2607_27644_b300 import relaybp as R
-    h = R.relaybp_build_dem(dems["z1"], R.Params(msg_dtype="f16", **CIRC_KW))
-    with pytest.raises(R.RelayBPError, match="FP32"):
+    h = R.relaybp_build_dem(dems["z1"], R.Params(msg_dtype="f64", **CIRC_KW))
+    with pytest.raises(R.RelayBPError, match="FP64"):
         R.relaybp_set_cluster_kernel(h, 8)
     with pytest.raises(R.RelayBPError):
         R.relaybp_set_cluster_kernel(h, 17)

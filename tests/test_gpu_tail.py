@@ -101,7 +101,65 @@ def test_offload_rejections(dem4):
     with pytest.raises(R.RelayBPError, match="carry"):
         R.relaybp_set_tail_offload(h, 3)
     R.relaybp_destroy(h)
-    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype="f16", **KW))
-    with pytest.raises(R.RelayBPError):
+    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype="f64", **KW))
+    with pytest.raises(R.RelayBPError, match="FP64"):
         R.relaybp_set_tail_offload(h, 3)
     R.relaybp_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "i8", "f32_one_shot"])
+def test_offload_from_the_one_shot_kernel(dem4, dtype):
+    """FP16 / int8 storage and FP32 with the two-shot kernel off: the one-shot
+    kernel hands the shots over, the cluster kernel continues them in the same
+    storage form."""
+    from paper_2607_27644_b300 import relaybp as R
+    msg = "f32" if dtype == "f32_one_shot" else dtype
+    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype=msg, **KW))
+    if dtype == "f32_one_shot":
+        R.relaybp_set_pair_kernel(h, False)
+    shots = 900
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 13, 7, shots, syn)
+    ref = _run(R, h, syn, 7)
+    assert (ref[2][:, 2] > 3).sum() > 20
+    R.relaybp_set_tail_offload(h, 3, 8, 1024)
+    n0 = R.relaybp_launch_count(h)
+    _equal(_run(R, h, syn, 7), ref)
+    assert R.relaybp_launch_count(h) - n0 == 2
+    R.relaybp_destroy(h)
+
+
+def test_offload_in_a_group_launch():
+    """Two DEMs in one persistent launch, both with offload (one cluster launch
+    each after the group launch), against the group without offload."""
+    from paper_2607_27644_b300 import relaybp as R
+    dems = [circuit_dem("ZSZ-LP-160", 0.004, 10, "Z"), circuit_dem("ZSZ-LP-160", 0.003, 10, "X")]
+    hs = [R.relaybp_build_dem(d, R.Params(msg_dtype="f16", **KW)) for d in dems]
+    shots = [700, 500]
+    syns = []
+    for h, n in zip(hs, shots):
+        x = torch.zeros((n, h.wc), dtype=torch.int32, device="cuda")
+        R.relaybp_sample(h, 14, 0, n, x)
+        syns.append(x)
+
+    def run():
+        grp = R.relaybp_group_create(hs)
+        outs = [(torch.full((n, h.wv), -1, dtype=torch.int32, device="cuda"),
+                 torch.full((n, h.wk), -1, dtype=torch.int32, device="cuda"),
+                 torch.full((n, 6), -1, dtype=torch.int32, device="cuda")) for h, n in zip(hs, shots)]
+        R.relaybp_group_decode(grp, syns, [0, 0], shots, [o[0] for o in outs], [o[1] for o in outs],
+                               [o[2] for o in outs])
+        torch.cuda.synchronize()
+        n_l = R.relaybp_group_launch_count(grp)
+        R.relaybp_group_destroy(grp)
+        return [tuple(t.cpu().numpy() for t in o) for o in outs], n_l
+
+    ref, n_ref = run()
+    for h in hs:
+        R.relaybp_set_tail_offload(h, 3, 8, 1024)
+    got, n_got = run()
+    assert n_ref == 1 and n_got == 3
+    for a, b in zip(got, ref):
+        _equal(a, b)
+    for h in hs:
+        R.relaybp_destroy(h)
