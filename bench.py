@@ -499,6 +499,26 @@ MIXED_P = [0.001, 0.002, 0.003]
 MIXED_RATIO = [2, 5, 10]
 
 
+def _tail_offload(R, handles, a):
+    """Tail offload on every handle (--tail-legs, --tail-cluster; the next
+    larger cluster where a DEM's slice does not fit shared memory); the
+    setting reported in the JSON line, or None."""
+    if a.tail_legs <= 0:
+        return None
+    used = set()
+    for x in handles:
+        for nc in (a.tail_cluster, 16):
+            try:
+                R.relaybp_set_tail_offload(x, a.tail_legs, nc, 256)
+                used.add(nc)
+                break
+            except R.RelayBPError:
+                if nc == 16:
+                    raise
+    return {"legs": a.tail_legs, "cluster_ctas": sorted(used),
+            "note": "shots about to start this relay leg finish on thread-block clusters (bit-identical outputs)"}
+
+
 def run_mixed(a):
     import torch
     from paper_2607_27644_b300 import relaybp as R
@@ -518,6 +538,7 @@ def run_mixed(a):
     NS = max(1, a.streams)
     HS = [[R.relaybp_build_dem(d, R.Params(msg_dtype=mmsg, **pp)) for d, pp in zip(dems, params)] for _ in range(NS)]
     hs = HS[0]
+    tail = _tail_offload(R, [x for hh in HS for x in hh], a)
     grps = [R.relaybp_group_create(x) for x in HS]
     n = len(hs)
     shots = [MIXED_RATIO[i % 3] * a.mixed_base for i in range(n)]
@@ -574,7 +595,7 @@ def run_mixed(a):
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     # graph replays do not pass through the host counters: count what one step launches
-    per_step = 2 * n + 1
+    per_step = 2 * n + 1 + (n if tail else 0)       # samples, group launch, counts (+ one cluster launch per DEM)
     total = sum(shots) * K
     c = counters.cpu().numpy()
     from paper_2607_27644_b300.stats import per_qubit_round
@@ -590,6 +611,7 @@ def run_mixed(a):
             "config": {"workload": "ZSZ-LP-320/390/550 (d=14/16/18) x p in {0.001,0.002,0.003}, Z-memory, "
                                    f"one group launch per step, CUDA-graph replay, steps rotating over {NS} streams",
                        "shots_per_step": sum(shots), "mix": shots, "decoder": "paper settings, Table 9 gamma",
+                       "tail_offload": tail,
                        "l2": "flushed before every step (256 MiB write, inside the graph)"},
             "clocks": clk.summary(), "gpu_launches": per_step * K, "per_dem": per_dem}
     print(json.dumps(line), flush=True)
@@ -752,6 +774,7 @@ def run_stream550(a):
     hs = [R.relaybp_build_dem(dem, R.Params(msg_dtype=msg, **dict(DECODER, gamma_min=gmin, gamma_max=gmax)))
           for _ in range(NS)]
     h = hs[0]
+    tail = _tail_offload(R, hs, a)
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     bufs = [dict(syn=torch.empty((B, h.wc), dtype=torch.int32, device=dev),
                  obs=torch.empty((B, h.wk), dtype=torch.int32, device=dev),
@@ -825,8 +848,8 @@ def run_stream550(a):
                        "state": "per-block region of global memory (L2-resident): one shot's state exceeds shared "
                                 "memory even in int8",
                        "l2": "flushed before every batch (256 MiB write, inside the graph)",
-                       "dem_build_s": t_build},
-            "clocks": clk.summary(), "gpu_launches": 3 * K,
+                       "dem_build_s": t_build, "tail_offload": tail},
+            "clocks": clk.summary(), "gpu_launches": (4 if tail else 3) * K,
             "ler": {"shots": shots, "failures": fails, "nonconverged": int(c[1]), "logical": int(c[2]),
                     "block_ler": blk, "block_ler_95": [lo, hi],
                     "per_qubit_round": per_qubit_round(blk, rounds, kq),

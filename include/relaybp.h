@@ -420,7 +420,8 @@ int relaybp_set_cluster_kernel(relaybp_handle *h, int32_t cluster);
  * a cluster, so a batch no longer waits on its slowest shot.  Applies to
  * relaybp_decode_batch, relaybp_decode_batch_noalloc, relaybp_decode_host
  * and relaybp_group_decode (one cluster launch per offloading DEM after the
- * group launch); not to traced, timed or flagged decodes, message carry-over,
+ * group launch) and relaybp_decode_timed (a handed-over shot keeps its start
+ * time); not to traced or flagged decodes, message carry-over,
  * per-edge learned weights, or row-tied learned weights and knots in the legs
  * being handed over (legs must be >= the learned legs).  Turning the cluster
  * kernel on for every shot (relaybp_set_cluster_kernel) turns offload off. */

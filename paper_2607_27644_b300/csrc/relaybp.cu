@@ -706,11 +706,12 @@ int launch_cluster(relaybp_handle *h, Scratch &sc, const JobIO &io, cudaStream_t
     return rc;
 }
 
-// Tail offload applies to plain legs of plain decodes without per-shot
-// diagnostics (trace, flagged posteriors, times) or message carry-over.
+// Tail offload applies to plain legs of decodes without traces, flagged
+// posteriors or message carry-over (a handed-over shot keeps its start time:
+// the cluster kernel writes both times of a timed decode).
 bool tail_applies(const relaybp_handle *h, const JobIO &io)
 {
-    if (h->cl_mode != 2 || io.trace || io.flag.post || io.times || h->params.carry_messages || h->lw ||
+    if (h->cl_mode != 2 || io.trace || io.flag.post || h->params.carry_messages || h->lw ||
         h->params.msg_dtype == RELAYBP_MSG_F64)
         return false;
     if ((h->lknots || h->lwrow) && (h->llegs < 0 || h->tail_legs < h->llegs)) return false;

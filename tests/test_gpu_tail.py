@@ -107,6 +107,35 @@ def test_offload_rejections(dem4):
     R.relaybp_destroy(h)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_offload_timed_decode(dem4, dtype):
+    """relaybp_decode_timed with offload: outputs unchanged; a handed-over
+    shot keeps its start time and gets its retire time from the cluster
+    kernel, so every shot has start < retire."""
+    from paper_2607_27644_b300 import relaybp as R
+    h = R.relaybp_build_dem(dem4, R.Params(msg_dtype=dtype, **KW))
+    shots = 700
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    R.relaybp_sample(h, 15, 0, shots, syn)
+
+    def timed():
+        corr = torch.full((shots, h.wv), -1, dtype=torch.int32, device="cuda")
+        stats = torch.full((shots, 6), -1, dtype=torch.int32, device="cuda")
+        times = torch.zeros((shots, 2), dtype=torch.int64, device="cuda")
+        R.relaybp_decode_timed(h, syn, 0, shots, times, d_corrections=corr, d_stats=stats)
+        torch.cuda.synchronize()
+        return corr.cpu().numpy(), stats.cpu().numpy(), times.cpu().numpy()
+
+    c0, s0, _ = timed()
+    R.relaybp_set_tail_offload(h, 3, 8, 1024)
+    c1, s1, t1 = timed()
+    assert np.array_equal(c0, c1) and np.array_equal(s0, s1)
+    assert np.all(t1[:, 0] > 0) and np.all(t1[:, 1] > t1[:, 0])
+    long = s1[:, 2] > 3
+    assert long.sum() > 20
+    R.relaybp_destroy(h)
+
+
 @pytest.mark.parametrize("dtype", ["f16", "i8", "f32_one_shot"])
 def test_offload_from_the_one_shot_kernel(dem4, dtype):
     """FP16 / int8 storage and FP32 with the two-shot kernel off: the one-shot
