@@ -67,7 +67,14 @@ def _args():
     ap.add_argument("--learned-msg", default="bf16", choices=["bf16", "f16", "f32"], help="learned: message storage")
     ap.add_argument("--objective", type=int, default=1, choices=[0, 1],
                     help="learned: training loss, 0 cross-entropy against the sampled error, 1 soft syndrome")
-    ap.add_argument("--train-T", type=int, default=10, help="learned: unrolled iterations of training")
+    ap.add_argument("--train-T", type=int, default=20, help="learned: unrolled iterations of training")
+    ap.add_argument("--learned-legs", default="leg0", choices=["leg0", "legs50"],
+                    help="learned: weights in leg 0 trained at gamma0 with plain legs after (leg0), or weights and "
+                         "memory-strength knots in legs 0-49 (legs50)")
+    ap.add_argument("--warm-start", default="1,0.9,0.85,0.8,0.75,0.7",
+                    help="learned: candidate uniform weights for the warm start ('' for none)")
+    ap.add_argument("--learned-steps", type=int, default=16,
+                    help="default workload: timed steps of the learned arm and of its ablation")
     ap.add_argument("--train-lr", type=float, default=3e-3, help="learned: Adam learning rate")
     ap.add_argument("--no-learned", action="store_true", help="default workload: skip the learned and ablation arms")
     ap.add_argument("--learned-train-steps", type=int, default=300,
@@ -340,13 +347,15 @@ def run_ours(a):
                "sync_call": "relaybp_decode_host, one step, synchronous (copies and decode in one call)"}
 
     # ---- the metric's learned side: learned vs plain at equal LER ----------
-    # Row-tied weights and knots trained here (soft-syndrome objective, p =
-    # 0.2%, untimed), then the same K steps of fresh shots as the plain arm
-    # decoded by (i) the learned decoder -- learned legs 0..49 with plain legs
-    # after in the same launch, stop after the first solution -- and (ii) the
-    # ablation, plain Relay-BP with the same stop-after-first rule: learned vs
-    # ablation is what the trained parameters gain, learned vs plain also
-    # counts the stopping rule.  FP32, two-shot kernel, same streams.
+    # Row-tied weights trained here (soft-syndrome objective, p = 0.2%,
+    # untimed; by default leg 0's weights at gamma0 from a one-parameter warm
+    # start), then --learned-steps batches of fresh shots -- the plain arm's
+    # shots first -- decoded by (i) the learned decoder -- learned legs, then
+    # plain legs in the same launch, stop after the first solution -- and (ii)
+    # the ablation, plain Relay-BP with the same stop-after-first rule:
+    # learned vs ablation is what the trained parameters gain, learned vs
+    # plain also counts the stopping rule.  FP32, two-shot kernel, same
+    # streams.
     learned = None
     if not a.no_learned and world == 1:
         from paper_2607_27644_b300.stats import agree_within
@@ -354,13 +363,14 @@ def run_ours(a):
         d_train = circuit_dems(WORKLOAD["code"], [0.002], WORKLOAD["rounds"], WORKLOAD["basis"])[0]
         wrow, knots, info = train_learned(a, dev, dem, d_train, a.learned_train_steps)
         arm = {}
+        KL = max(1, a.learned_steps)
         for kind in ("learned", "ablation"):
             hk = []
             for q in range(NS):
                 x = R.relaybp_build_dem(dem, R.Params(msg_dtype="f32", **dict(DECODER, stop_nconv=1)))
                 if kind == "learned":
                     R.relaybp_set_learned_rows(x, wrow, knots)
-                    R.relaybp_set_learned_legs(x, 50)
+                    R.relaybp_set_learned_legs(x, info["learned_legs"])
                 if tail:                        # past the learned legs, both arms alike
                     R.relaybp_set_tail_offload(x, max(tail, 50), a.tail_cluster, 256)
                 hk.append(x)
@@ -370,7 +380,7 @@ def run_ours(a):
             def astep(k):
                 q = k % NS
                 s_, b_, h_ = streams[q], bufs[q], hk[q]
-                shot0, _ = shot_range(rank, world, K + W, B, k)
+                shot0, _ = shot_range(rank, world, KL + W, B, k)
                 with torch.cuda.stream(s_):
                     flush.fill_(k)
                     R.relaybp_sample(h_, SAMPLE_SEED, shot0, B, b_["syn"], b_["obs"], None, s_)
@@ -379,7 +389,7 @@ def run_ours(a):
                     it_k.add_(b_["stats"][:, 3].sum())
 
             for w_ in range(W):
-                astep(K + w_)
+                astep(KL + w_)
             torch.cuda.synchronize()
             cnt_k.zero_()
             it_k.zero_()
@@ -388,31 +398,33 @@ def run_ours(a):
                 e0.record(streams[0])
                 for s_ in streams[1:]:
                     s_.wait_stream(streams[0])
-                for k in range(K):
+                for k in range(KL):
                     astep(k)
                 join()
                 e1.record(streams[0])
                 torch.cuda.synchronize()
             ms_k = e0.elapsed_time(e1)
             ck = cnt_k.cpu().tolist()
-            arm[kind] = {"value": B * K / (ms_k / 1e3), "unit": "shots/s", "shots": ck[0], "failures": ck[3],
+            arm[kind] = {"value": B * KL / (ms_k / 1e3), "unit": "shots/s", "shots": ck[0], "failures": ck[3],
                          "nonconverged": ck[1], "logical": ck[2], "block_ler": ck[3] / max(1, ck[0]),
-                         "mean_iterations": float(it_k.item()) / (B * K), "clocks": clk_k.summary()}
+                         "mean_iterations": float(it_k.item()) / (B * KL), "clocks": clk_k.summary()}
             for x in hk:
                 R.relaybp_destroy(x)
         cp = cnt.cpu().tolist()
         lv, ab = arm["learned"], arm["ablation"]
         learned = dict(lv)
         learned.update({
-            "decoder": "FP32; learned row-tied weights (first T iterations of a leg, unit after) and memory-strength "
-                       "knots in legs 0-49, plain legs after in the same launch; stop after the first solution",
+            "decoder": ("FP32; learned row-tied weights in the first T iterations of leg 0 (unit after), plain legs "
+                        "after in the same launch" if info["learned_legs"] == 1 else
+                        "FP32; learned row-tied weights (first T iterations of a leg, unit after) and memory-strength "
+                        "knots in legs 0-49, plain legs after in the same launch") + "; stop after the first solution",
             "ablation": ab, "train": info,
             "speedup_vs_plain": lv["value"] / value, "speedup_vs_ablation": lv["value"] / ab["value"],
             "mean_iterations_vs_ablation": lv["mean_iterations"] / ab["mean_iterations"],
             "equal_ler_2sigma_vs_plain": bool(agree_within(lv["failures"], lv["shots"], cp[3], cp[0])),
             "equal_ler_2sigma_vs_ablation": bool(agree_within(lv["failures"], lv["shots"], ab["failures"],
                                                               ab["shots"])),
-            "note": "same shots as the plain arm; speedup_vs_plain mostly measures the stopping rule (first solution "
+            "note": f"{KL} batches of {B} shots, the plain arm's first; speedup_vs_plain mostly measures the stopping rule (first solution "
                     "vs five), speedup_vs_ablation and mean_iterations_vs_ablation what the trained parameters "
                     "gain at the same rule"})
 
@@ -626,8 +638,9 @@ def train_learned(a, dev, d_inf, d_train, steps):
     """The library's trainer (row-tied weights, checkpoint selection by
     held-out decoding iterations) with this benchmark's settings."""
     from paper_2607_27644_b300.learned import train_rows
+    warm = tuple(float(x) for x in a.warm_start.split(",") if x.strip()) or None
     return train_rows(d_inf, d_train, DECODER, steps, T=a.train_T, lr=a.train_lr, objective=a.objective,
-                      device=dev)
+                      device=dev, leg0=a.learned_legs == "leg0", warm_start=warm, select_shots=16384)
 
 
 def run_learned(a):
@@ -635,9 +648,9 @@ def run_learned(a):
     plain Relay-BP (paper settings, FP32) on the same fresh shots at p = 0.1%.
 
     Learned decoder: learned row-tied message weights for the first T
-    iterations of each learned leg (unit weights after them) and a learned
-    memory-strength distribution, in legs 0..49; plain legs after that in the
-    same launch (the fallback for shots the learned legs leave unconverged);
+    iterations of each learned leg (unit weights after them) -- leg 0 by
+    default, or legs 0..49 with a learned memory-strength distribution
+    (--learned-legs legs50); plain legs after that in the same launch (the fallback for shots the learned legs leave unconverged);
     stop after the first solution; FP32 messages (the two-shot kernel) and
     the --learned-msg storage.  Ablations run plain Relay-BP with the same
     stop-after-one rule at both precisions: what the learned parameters gain
@@ -656,10 +669,11 @@ def run_learned(a):
     E = d_inf.n_edges
     wrow, knots, train_info = train_learned(a, dev, d_inf, d_train, a.train_steps)
     # ---- decoders: one handle set per stream ------------------------------------
-    # learned parameters for legs 0..49, then plain legs (unit weights, uniform
+    # learned parameters for the learned legs (leg 0 by default, legs 0..49
+    # with --learned-legs legs50), then plain legs (unit weights, uniform
     # gamma) up to the paper's 1000 in the same launch: the plain fallback for
     # the shots the learned legs do not settle; stop after the first solution
-    NS, LEGS = 3, 50
+    NS, LEGS = 3, train_info["learned_legs"]
     learned_params = dict(DECODER, stop_nconv=1)
     B, K, W = a.batch, a.steps, a.warmup
     streams = [torch.cuda.Stream(device=dev) for _ in range(NS)]

@@ -59,7 +59,8 @@ class LearnedParams(torch.nn.Module):
     applies at no extra memory traffic (relaybp_set_learned_rows)."""
 
     def __init__(self, T: int, n_edges: int, gamma_min: float, gamma_max: float, K: int = 16,
-                 dtype=torch.float32, device="cuda", row_of_edge=None, n_rows: int = 0):
+                 dtype=torch.float32, device="cuda", row_of_edge=None, n_rows: int = 0,
+                 fixed_gamma: float | None = None):
         super().__init__()
         self.row_of_edge = None
         if row_of_edge is not None:
@@ -67,6 +68,12 @@ class LearnedParams(torch.nn.Module):
             self.w = torch.nn.Parameter(torch.ones((T, n_rows), dtype=dtype, device=device))
         else:
             self.w = torch.nn.Parameter(torch.ones((T, n_edges), dtype=dtype, device=device))
+        # fixed_gamma: every variable takes this strength (two equal knots, not
+        # trained) -- the unrolled leg is then leg 0, which runs at gamma0
+        self.theta = None
+        if fixed_gamma is not None:
+            self.register_buffer("fixed_knots", torch.full((2,), fixed_gamma, dtype=dtype, device=device))
+            return
         step = (gamma_max - gamma_min) / K
         inv_sp = float(torch.log(torch.expm1(torch.tensor(step, dtype=torch.float64))))
         theta = torch.full((K + 1,), inv_sp, dtype=dtype, device=device)
@@ -74,6 +81,8 @@ class LearnedParams(torch.nn.Module):
         self.theta = torch.nn.Parameter(theta)
 
     def knots(self):
+        if self.theta is None:
+            return self.fixed_knots
         return torch.cat([self.theta[:1], self.theta[:1] + torch.cumsum(torch.nn.functional.softplus(self.theta[1:]),
                                                                         0)])
 
@@ -87,17 +96,27 @@ class LearnedParams(torch.nn.Module):
 
 def train_rows(d_inf, d_train, decoder: dict, steps: int, T: int = 10, lr: float = 3e-3, objective: int = 1,
                device="cuda", batch: int = 512, select_shots: int = 8192, learned_legs: int = 50,
-               sample_seed: int = 4, select_seed: int = 5):
+               sample_seed: int = 4, select_seed: int = 5, leg0: bool = False,
+               warm_start: tuple | None = None):
     """Train row-tied message weights [T, C] and memory-strength knots on
     self-sampled shots of d_train (the training DEM: the same detectors and
     faults as d_inf at another noise strength) with the library's forward and
-    backward kernels and Adam; every 25 steps the current parameters decode
+    backward kernels and Adam.  leg0=True trains the weights of leg 0 alone:
+    the unrolled leg runs at the decoder's gamma0 for every variable, as leg 0
+    does, the knots stay at gamma0 (two equal knots, not trained) and
+    learned_legs is 1, so every later leg is the plain method.  warm_start, a
+    tuple of candidate values, starts the gradient steps from the uniform
+    weight among them (every row and iteration alike) that decodes the
+    held-out shots below in the fewest mean iterations -- a one-parameter fit
+    on the decoding objective, which the per-row gradient steps then refine.
+    Every 25 steps the current parameters decode
     select_shots held-out shots of d_inf (stop after the first solution,
     learned legs 0..learned_legs-1, plain legs after), and the checkpoint with
     the fewest mean iterations -- clipped at the learned legs' horizon, so a
-    shot left to the plain legs counts once -- is kept; step 0 (unit weights,
-    the uniform interval) is a candidate, so the result never decodes slower
-    than no training on that sample.  decoder: Relay-BP parameters (Params
+    shot left to the plain legs counts once -- is kept; step 0 (unit weights
+    and the uniform interval, or the warm start, whose candidates include 1)
+    is a candidate, so the result never decodes slower than no training on
+    that sample.  decoder: Relay-BP parameters (Params
     fields).  Returns (wrow, knots, info) with wrow and knots FP32 device
     tensors for relaybp_set_learned_rows."""
     import numpy as np
@@ -113,8 +132,10 @@ def train_rows(d_inf, d_train, decoder: dict, steps: int, T: int = 10, lr: float
     # ---- training (untimed) ---------------------------------------------------
     ht = R.relaybp_build_dem(d_train, R.Params(msg_dtype="f32", **DECODER))
     row_of = np.repeat(np.arange(d_inf.n_det), np.diff(d_inf.H_indptr))
+    if leg0:
+        learned_legs = 1
     model = LearnedParams(T, E, DECODER["gamma_min"], DECODER["gamma_max"], device=dev, row_of_edge=row_of,
-                          n_rows=d_inf.n_det)
+                          n_rows=d_inf.n_det, fixed_gamma=float(DECODER.get("gamma0", 0.125)) if leg0 else None)
     opt = torch.optim.Adam(model.parameters(), lr=lr)
     syn_t = torch.empty((BT, ht.wc), dtype=torch.int32, device=dev)
     err_t = torch.empty((BT, ht.wv), dtype=torch.int32, device=dev)
@@ -161,6 +182,16 @@ def train_rows(d_inf, d_train, decoder: dict, steps: int, T: int = 10, lr: float
             best, best_step = it, k
             best_state = {n: t.detach().clone() for n, t in model.state_dict().items()}
 
+    warm = None
+    if warm_start:
+        scores = {}
+        with torch.no_grad():
+            for v in warm_start:
+                model.w.fill_(float(v))
+                scores[float(v)] = round(held_out_iterations(), 3)
+            v_best = min(scores, key=scores.get)     # first of equal scores
+            model.w.fill_(v_best)
+        warm = {"candidates": scores, "chosen": v_best}
     checkpoint(0)
     for k in range(steps):
         R.relaybp_sample(ht, sample_seed, k * BT, BT, syn_t, None, err_t)
@@ -180,9 +211,13 @@ def train_rows(d_inf, d_train, decoder: dict, steps: int, T: int = 10, lr: float
     wrow = model.w.detach().float().contiguous()
     knots = model.knots().detach().float().contiguous()
     info = {"steps": steps, "batch": BT, "shots": steps * BT, "unrolled_iterations": T,
+            "learned_legs": learned_legs,
+            "memory_strength": (f"leg 0 only: gamma0 = {float(DECODER.get('gamma0', 0.125)):g} in training, plain "
+                                f"legs after" if leg0 else "learned knots in legs 1..learned_legs-1"),
             "objective": ["cross-entropy against the sampled error", "soft syndrome"][objective],
             "optimizer": f"Adam {lr:g}, grad-norm clip 1, weights in [0, 2]",
             "weights": "tied per check row and iteration; unit past the trained horizon", "seconds": train_s,
+            "warm_start": warm,
             "held_out_loss_every_25_steps": hist, "held_out_mean_iterations_every_25_steps": sel_hist,
             "selection": f"fewest held-out mean iterations, clipped at the learned legs' horizon ({NSEL} shots of "
                          f"the inference DEM, stop after the first solution); kept step {best_step}"}

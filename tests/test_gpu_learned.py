@@ -276,15 +276,16 @@ def test_learned_legs_cutoff_matches_oracle():
 
 
 def test_trained_parameters_lower_mean_iterations():
-    """What training gains, at the same stopping rule: row-tied weights and
-    memory-strength knots trained on self-sampled shots of the ZSZ-LP-160
-    circuit DEM at p = 0.2% (soft-syndrome objective, T = 10, 200 Adam steps of
-    512 shots, checkpoint selection on 8,192 held-out shots) decode 2^17 fresh
-    shots at p = 0.1% -- learned legs 0..49, plain legs after, stop after the
-    first solution -- in fewer mean iterations than the same decoder with unit
-    weights and the uniform interval (the ablation); failures agree within 2
-    sigma.  Iterations are clipped at the learned legs' horizon (80 + 50 x 60)
-    so a shot left to the plain legs counts once; both means are reported."""
+    """What training gains, at the same stopping rule: row-tied weights of leg
+    0 trained on self-sampled shots of the ZSZ-LP-160 circuit DEM at p = 0.2%
+    (soft-syndrome objective over T = 20 iterations at gamma0, from the
+    uniform weight that decodes held-out shots in the fewest iterations, 200
+    Adam steps of 512 shots, checkpoint selection on 16,384 held-out shots)
+    decode 2^17 fresh shots at p = 0.1% -- learned leg 0, plain legs after,
+    stop after the first solution -- in at least 5% fewer mean iterations than
+    the same decoder with unit weights (the ablation); failures agree within 2
+    sigma.  Iterations are clipped at the learned legs' horizon (80 + 60) so a
+    shot left to the plain legs counts once; both means are reported."""
     import warnings
     import torch
     from paper_2607_27644_b300 import relaybp as R
@@ -294,11 +295,14 @@ def test_trained_parameters_lower_mean_iterations():
     d_inf, d_train = circuit_dems("ZSZ-LP-160", [0.001, 0.002], 10, "Z")
     decoder = dict(gamma0=0.125, pre_iter=80, num_sets=1000, max_iterations=60, stop_nconv=5, gamma_min=-0.15,
                    gamma_max=0.61, seed=24301)
-    wrow, knots, info = train_rows(d_inf, d_train, decoder, 200)
+    wrow, knots, info = train_rows(d_inf, d_train, decoder, 200, T=20, leg0=True, select_shots=16384,
+                                   warm_start=(1.0, 0.9, 0.85, 0.8, 0.75, 0.7))
+    legs = info["learned_legs"]
+    horizon = decoder["pre_iter"] + legs * decoder["max_iterations"]
     p1 = R.Params(msg_dtype="f32", **dict(decoder, stop_nconv=1))
     hl, hu = R.relaybp_build_dem(d_inf, p1), R.relaybp_build_dem(d_inf, p1)
     R.relaybp_set_learned_rows(hl, wrow, knots)
-    R.relaybp_set_learned_legs(hl, 50)
+    R.relaybp_set_learned_legs(hl, legs)
     N, shot0 = 1 << 17, 3 * 10**9
     syn = torch.empty((N, hl.wc), dtype=torch.int32, device="cuda")
     obs = torch.empty((N, hl.wk), dtype=torch.int32, device="cuda")
@@ -311,12 +315,13 @@ def test_trained_parameters_lower_mean_iterations():
         R.relaybp_decode_batch(h, syn, shot0, N, None, pobs, st)
         R.relaybp_count_failures(h, pobs, obs, st, N, cnt)
         it = st[:, 3].double()
-        res[name] = (float(it.clamp(max=80 + 50 * 60).mean()), float(it.mean()), int(cnt[3]))
+        res[name] = (float(it.clamp(max=horizon).mean()), float(it.mean()), int(cnt[3]))
     warnings.warn(UserWarning(
         f"trained vs unit parameters, 2^17 shots, stop after the first solution: mean iterations (clipped) "
         f"{res['learned'][0]:.3f} vs {res['unit'][0]:.3f}, unclipped {res['learned'][1]:.2f} vs {res['unit'][1]:.2f}, "
-        f"failures {res['learned'][2]} vs {res['unit'][2]}; kept training step {info['selection'][-4:]}"))
-    assert res["learned"][0] < res["unit"][0]
+        f"failures {res['learned'][2]} vs {res['unit'][2]}; warm start {info['warm_start']}; "
+        f"kept training step {info['selection'].split()[-1]}"))
+    assert res["learned"][0] <= 0.95 * res["unit"][0]
     assert agree_within(res["learned"][2], N, res["unit"][2], N)
     R.relaybp_destroy(hl)
     R.relaybp_destroy(hu)
