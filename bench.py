@@ -246,7 +246,9 @@ def run_ours(a):
                  stats=torch.empty((B, 6), dtype=torch.int32, device=dev)) for _ in range(NS)]
     syn, obs, pobs, stats = bufs[0]["syn"], bufs[0]["obs"], bufs[0]["pobs"], bufs[0]["stats"]
     counters = torch.zeros(4, dtype=torch.int64, device=dev)
-    iters_total = torch.zeros(1, dtype=torch.int64, device=dev)
+    # per-stream iteration sums: an in-place add on one element from several
+    # streams at once would lose updates
+    iters_total = torch.zeros(NS, dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
     from paper_2607_27644_b300.replicas import shot_range, reduce_counters
 
@@ -263,7 +265,7 @@ def run_ours(a):
             if dec_events:
                 dec_events[1].record(s_)
             R.relaybp_count_failures(h_, b_["pobs"], b_["obs"], b_["stats"], B, counters, s_)
-            iters_total.add_(b_["stats"][:, 3].sum())
+            iters_total[q:q + 1].add_(b_["stats"][:, 3].sum())
 
     def join():
         for s_ in streams[1:]:
@@ -294,7 +296,7 @@ def run_ours(a):
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     dec_ms = [e0.elapsed_time(e1) for e0, e1 in dec_ev]
-    cnt, ms_max = reduce_counters(torch.cat([counters, iters_total]), ms)
+    cnt, ms_max = reduce_counters(torch.cat([counters, iters_total.sum().reshape(1)]), ms)
     cnt = cnt[:4]
     shots_total = B * K * world
     value = shots_total / (ms_max / 1e3)
@@ -375,7 +377,7 @@ def run_ours(a):
                     R.relaybp_set_tail_offload(x, max(tail, 50), a.tail_cluster, 256)
                 hk.append(x)
             cnt_k = torch.zeros(4, dtype=torch.int64, device=dev)
-            it_k = torch.zeros(1, dtype=torch.int64, device=dev)
+            it_k = torch.zeros(NS, dtype=torch.int64, device=dev)       # per stream
 
             def astep(k):
                 q = k % NS
@@ -386,7 +388,7 @@ def run_ours(a):
                     R.relaybp_sample(h_, SAMPLE_SEED, shot0, B, b_["syn"], b_["obs"], None, s_)
                     R.relaybp_decode_batch(h_, b_["syn"], shot0, B, None, b_["pobs"], b_["stats"], s_)
                     R.relaybp_count_failures(h_, b_["pobs"], b_["obs"], b_["stats"], B, cnt_k, s_)
-                    it_k.add_(b_["stats"][:, 3].sum())
+                    it_k[q:q + 1].add_(b_["stats"][:, 3].sum())
 
             for w_ in range(W):
                 astep(KL + w_)
@@ -407,7 +409,7 @@ def run_ours(a):
             ck = cnt_k.cpu().tolist()
             arm[kind] = {"value": B * KL / (ms_k / 1e3), "unit": "shots/s", "shots": ck[0], "failures": ck[3],
                          "nonconverged": ck[1], "logical": ck[2], "block_ler": ck[3] / max(1, ck[0]),
-                         "mean_iterations": float(it_k.item()) / (B * KL), "clocks": clk_k.summary()}
+                         "mean_iterations": float(it_k.sum().item()) / (B * KL), "clocks": clk_k.summary()}
             for x in hk:
                 R.relaybp_destroy(x)
         cp = cnt.cpu().tolist()
@@ -442,7 +444,7 @@ def run_ours(a):
         e1.record(st)
         torch.cuda.synchronize()
     smem_gbs = nb / (e0.elapsed_time(e1) / 1e3) / 1e9
-    iters_rank = int(iters_total.item())
+    iters_rank = int(iters_total.sum().item())
     wall_s = ms / 1e3
     E, V, C = dem.n_edges, dem.n_loc, dem.n_det
     b_m = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "i8": 1}[msg]
@@ -458,7 +460,7 @@ def run_ours(a):
     # the L2 write-backs of the per-block memory-strength rows
     # DRAM bytes of one two-shot-kernel launch of 3,000 shots (ncu capture of
     # this build), scaled to the step's shots
-    traffic = (4172288 + 3796736) * B / 3000 if (msg == "f32" and B >= 3000) else None
+    traffic = (4205056 + 4014080) * B / 3000 if (msg == "f32" and B >= 3000) else None
     roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
             "traffic": traffic,
             "kernel": (("relay_pair_kernel<23> (two shots per block, FP32)"
@@ -469,8 +471,8 @@ def run_ours(a):
             "peak_source": "measured live: conflict-free 16-B shared-memory loads on all SMs (relaybp_probe_smem_read)",
             "achieved_basis": f"algorithmic bytes of all decode launches / the timed region ({NS} launches in flight "
                               "at once; the decode kernels fill >99.7% of device time in the serialised ncu launch "
-                              "list of this command with 2 steps: two-shot kernel 73.8%, cluster kernel of the "
-                              "handed-over shots 25.9%)",
+                              "list of this command with 2 steps: two-shot kernel 73.2%, cluster kernel of the "
+                              "handed-over shots 26.6%)",
             "achieved_per_launch": per_launch, "decode_ms_per_launch": dec_avg_s * 1e3,
             "edge_updates_per_s": edge_updates,
             "hbm_equivalent": ({"peak_gbs": hbm_gbs, "frac": achieved / hbm_gbs,
@@ -703,13 +705,13 @@ def run_learned(a):
             R.relaybp_sample(h_["plain"], SAMPLE_SEED, s0, B, b_["syn"], b_["obs"], None, st_)
             R.relaybp_decode_batch(h_[kind], b_["syn"], s0, B, None, b_["pobs"], b_["stats"], st_)
             R.relaybp_count_failures(h_["plain"], b_["pobs"], b_["obs"], b_["stats"], B, cnt, st_)
-            it.add_(b_["stats"][:, 3].sum())
+            it[q:q + 1].add_(b_["stats"][:, 3].sum())     # per stream: no cross-stream update
 
     out = {}
     kinds = ["plain"] + [f"{x}_{m}" for m in dict.fromkeys(("f32", a.learned_msg)) for x in ("learned", "ablation")]
     for kind in kinds:
         cnt = torch.zeros(4, dtype=torch.int64, device=dev)
-        it = torch.zeros(1, dtype=torch.int64, device=dev)
+        it = torch.zeros(NS, dtype=torch.int64, device=dev)
         for w_ in range(W):
             step(kind, K + w_, cnt, it)
         torch.cuda.synchronize()
@@ -730,7 +732,7 @@ def run_learned(a):
         c = cnt.cpu().tolist()
         out[kind] = {"shots_per_s": B * K / (ms / 1e3), "ms_per_step": ms / K, "shots": c[0], "failures": c[3],
                      "nonconverged": c[1], "logical": c[2], "block_ler": c[3] / max(1, c[0]),
-                     "mean_iterations": float(it.item()) / (B * K), "clocks": clk.summary()}
+                     "mean_iterations": float(it.sum().item()) / (B * K), "clocks": clk.summary()}
     lp, lm = out["plain"], a.learned_msg
     arms = {}
     for m in dict.fromkeys(("f32", lm)):
@@ -796,7 +798,7 @@ def run_stream550(a):
                  stats=torch.empty((B, 6), dtype=torch.int32, device=dev)) for _ in range(NS)]
     times = [torch.zeros((B, 2), dtype=torch.int64, device=dev) for _ in range(K + W)]
     counters = torch.zeros(4, dtype=torch.int64, device=dev)
-    iters = torch.zeros(1, dtype=torch.int64, device=dev)
+    iters = torch.zeros(NS, dtype=torch.int64, device=dev)     # per stream: no cross-stream update
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
 
     def step(k):
@@ -807,7 +809,7 @@ def run_stream550(a):
         R.relaybp_sample(h_, SAMPLE_SEED, s0, B, b_["syn"], b_["obs"], None, streams[q])
         R.relaybp_decode_timed(h_, b_["syn"], s0, B, times[k], None, b_["pobs"], b_["stats"], streams[q])
         R.relaybp_count_failures(h_, b_["pobs"], b_["obs"], b_["stats"], B, counters, streams[q])
-        iters.add_(b_["stats"][:, 3].sum())
+        iters[q:q + 1].add_(b_["stats"][:, 3].sum())
 
     # one eager step per stream sizes every scratch buffer, then each step is
     # captured once on its stream and replayed
@@ -874,7 +876,7 @@ def run_stream550(a):
                            "in_batch_p50": pct(sojourn, 50), "in_batch_p99": pct(sojourn, 99),
                            "definition": "service = retire - start of the shot's thread block (device %globaltimer); "
                                          "in_batch = retire - first start in its batch"},
-            "mean_iterations_per_shot": float(iters.item()) / (B * K)}
+            "mean_iterations_per_shot": float(iters.sum().item()) / (B * K)}
     print(json.dumps(line), flush=True)
     for x in hs:
         R.relaybp_destroy(x)

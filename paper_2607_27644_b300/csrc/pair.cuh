@@ -398,17 +398,29 @@ relay_pair_kernel(const __grid_constant__ PairJob J, unsigned long long *__restr
             if (lane == 0) { e0[G] = nw0; e1[G] = nw1; }
             const uint32_t ch0 = o0 ^ nw0, ch1 = o1 ^ nw1;
             if (ch0 | ch1) {                    // warp-uniform: a decision changed (a5, incremental residual)
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    if (((s ? ch1 : ch0) >> lane) & 1u) {
-                        uint32_t *rs = res(s);
-                        const uint32_t r0 = (uint32_t)J.plan.MM >> 4;
-                        for (int kk = 0; kk < Dc; ++kk) {
-                            const uint32_t ri = (__ldg(col + kk * 32) >> 10) - r0;
-                            if (ri >= (uint32_t)Cn) break;     // padding (the dummy check)
-                            atomicXor(rs + (ri >> 5), 1u << (ri & 31));
+                // bit s: this lane's decision of shot s changed; its column's
+                // checks flip in that shot's residual.  The first eight codes
+                // load together (every group holds >= 8 slots), so one L2
+                // latency serves both shots; padding codes name the dummy
+                // check C and flip nothing.
+                const uint32_t mine = ((ch0 >> lane) & 1u) | (((ch1 >> lane) & 1u) << 1);
+                if (mine) {
+                    const uint32_t r0 = (uint32_t)J.plan.MM >> 4;
+                    uint32_t *rs0 = res(0), *rs1 = res(1);
+                    auto flip = [&](uint32_t code) {
+                        const uint32_t ri = (code >> 10) - r0;
+                        if (ri < (uint32_t)Cn) {
+                            if (mine & 1u) atomicXor(rs0 + (ri >> 5), 1u << (ri & 31));
+                            if (mine & 2u) atomicXor(rs1 + (ri >> 5), 1u << (ri & 31));
                         }
-                    }
+                    };
+                    uint32_t cc[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) cc[u] = __ldg(col + u * 32);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (u < Dc) flip(cc[u]);
+                    for (int kk = 8; kk < Dc; ++kk) flip(__ldg(col + kk * 32));
                 }
             }
         }
