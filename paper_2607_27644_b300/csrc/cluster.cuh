@@ -456,11 +456,24 @@ relay_cluster_kernel(const __grid_constant__ ClusterJob J, unsigned long long *_
                     __syncwarp();
                     if (lane == 0) ehat[G - g0] = nw;
                     if (((old ^ nw) >> lane) & 1u) {        // a5: flip this variable's checks at their owners
-                        for (int kk = 0; kk < D; ++kk) {
-                            const uint32_t hr = __ldg(col + kk * 32) >> lg;
-                            if (hr >= (uint32_t)HR) break;               // padding (the dummy row)
+                        // the first eight codes load together; padding codes
+                        // (the dummy row, at the end of a column) flip nothing
+                        auto flip = [&](uint32_t hr) {
                             const uint32_t c = rhs[hr], lr = c & rmask;
                             cl_xor(cl_map(resS + 4u * (lr >> 5), c >> J.lgcs), 1u << (lr & 31));
+                        };
+                        uint32_t cc[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) cc[u] = (u < D) ? __ldg(col + u * 32) : 0u;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const uint32_t hr = cc[u] >> lg;
+                            if (u < D && hr < (uint32_t)HR) flip(hr);
+                        }
+                        for (int kk = 8; kk < D; ++kk) {
+                            const uint32_t hr = __ldg(col + kk * 32) >> lg;
+                            if (hr >= (uint32_t)HR) break;               // padding (the dummy row)
+                            flip(hr);
                         }
                     }
                 }
