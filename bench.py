@@ -471,8 +471,8 @@ def run_ours(a):
             "peak_source": "measured live: conflict-free 16-B shared-memory loads on all SMs (relaybp_probe_smem_read)",
             "achieved_basis": f"algorithmic bytes of all decode launches / the timed region ({NS} launches in flight "
                               "at once; the decode kernels fill >99.7% of device time in the serialised ncu launch "
-                              "list of this command with 2 steps: two-shot kernel 73.2%, cluster kernel of the "
-                              "handed-over shots 26.6%)",
+                              "list of this command with 2 steps: two-shot kernel 73.4%, cluster kernel of the "
+                              "handed-over shots 26.3%)",
             "achieved_per_launch": per_launch, "decode_ms_per_launch": dec_avg_s * 1e3,
             "edge_updates_per_s": edge_updates,
             "hbm_equivalent": ({"peak_gbs": hbm_gbs, "frac": achieved / hbm_gbs,
