@@ -688,6 +688,9 @@ def run_learned(a):
             R.relaybp_set_learned_legs(hl, LEGS)
             hh["learned_" + msg] = hl
             hh["ablation_" + msg] = R.relaybp_build_dem(d_inf, R.Params(msg_dtype=msg, **learned_params))
+        if a.tail_legs > 0:                     # every arm alike: shots reaching that leg finish on clusters
+            for x in hh.values():
+                R.relaybp_set_tail_offload(x, max(a.tail_legs, LEGS), a.tail_cluster, 256)
         H.append(hh)
     hp = H[0]["plain"]
     bufs = [dict(syn=torch.empty((B, hp.wc), dtype=torch.int32, device=dev),
@@ -752,10 +755,14 @@ def run_learned(a):
             "data": "synthetic: Philox-sampled faults of the ZSZ-LP-160 circuit DEMs",
             "config": {"workload": "learned vs plain Relay-BP, ZSZ-LP-160 d=10, inference p=0.001, training p=0.002",
                        "train": train_info,
-                       "learned_decoder": "learned weights + knots in legs 0-49, plain legs after (in-kernel "
-                                          "fallback), stop_nconv=1; FP32 and " + lm + " message storage",
+                       "learned_decoder": ("learned row-tied weights in leg 0" if LEGS == 1 else
+                                           f"learned weights + knots in legs 0-{LEGS - 1}")
+                                          + ", plain legs after (in-kernel fallback), stop_nconv=1; FP32 and " + lm
+                                          + " message storage",
                        "ablation": "plain Relay-BP with the same stop_nconv=1 rule at the same storage precision",
                        "pipeline": "3 streams, steps rotate, L2 flushed before every step",
+                       "tail_offload": ({"legs": max(a.tail_legs, LEGS), "cluster_ctas": a.tail_cluster,
+                                         "arms": "all"} if a.tail_legs > 0 else None),
                        "plain_decoder": "FP32, paper settings (stop_nconv=5)", "shots_per_step": B},
             "plain": lp, "arms": arms,
             "note": "speedup_vs_plain mostly measures the stopping rule (stop after the first solution vs five); "
