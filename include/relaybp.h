@@ -361,6 +361,16 @@ int relaybp_learned_backward(relaybp_handle *h, int32_t precision, int32_t T, co
                              const void *d_tape, double scale, void *d_grad_w, void *d_grad_knots,
                              void *cuda_stream);
 
+/* Wait until the work queued on cuda_stream (NULL = the legacy default
+ * stream) has finished and report an asynchronous failure there: 0, or
+ * RELAYBP_ERR_CUDA with the CUDA error text in relaybp_last_error() (a launch
+ * that failed after its call returned, a kernel that faulted).  The handle's
+ * device must be current (RELAYBP_ERR_INVALID otherwise).  The paper has no
+ * counterpart: it is the boundary's synchronisation point.  No kernel of this
+ * library waits on a flag, a peer or a timeout, so CUDA's own status is the
+ * only device-side error there is to report. */
+int relaybp_sync(relaybp_handle *h, void *cuda_stream);
+
 /* Number of kernel launches this handle has issued since it was built. */
 int64_t relaybp_launch_count(const relaybp_handle *h);
 

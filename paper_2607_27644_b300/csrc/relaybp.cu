@@ -2179,6 +2179,16 @@ int64_t relaybp_group_launch_count(const relaybp_group *grp) { return grp ? grp-
 
 int64_t relaybp_launch_count(const relaybp_handle *h) { return h ? h->launches : -1; }
 
+int relaybp_sync(relaybp_handle *h, void *cuda_stream)
+{
+    g_err.clear();
+    if (!h) return fail(RELAYBP_ERR_INVALID, "handle is NULL");
+    if (int rc = check_device(h)) return rc;
+    CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 int relaybp_probe_smem_read(int32_t reps, float *d_sink, double *bytes_read, void *cuda_stream)
 {
     g_err.clear();

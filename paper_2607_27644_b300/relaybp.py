@@ -79,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "relaybp_set_tail_offload": ([P, I32, I32, I64], ctypes.c_int),
         "relaybp_count_failures": ([P, P, P, P, I64, P, P], ctypes.c_int),
         "relaybp_launch_count": ([P], I64),
+        "relaybp_sync": ([P, P], ctypes.c_int),
         "relaybp_learned_tape_bytes": ([P, I32, I32, I64], I64),
         "relaybp_learned_forward": ([P, I32, I32, P, I32, P, U64, I32, P, P, U64, I64, P, P, P], ctypes.c_int),
         "relaybp_learned_backward": ([P, I32, I32, P, I32, P, U64, I32, P, P, U64, I64, P, ctypes.c_double, P, P,
@@ -105,7 +106,7 @@ EXPORTED = ["relaybp_build", "relaybp_set_params", "relaybp_set_learned", "relay
             "relaybp_set_learned_legs", "relaybp_set_pair_kernel", "relaybp_set_cluster_kernel", "relaybp_set_tail_offload", "relaybp_sizes", "relaybp_sample", "relaybp_decode_batch",
             "relaybp_decode_timed", "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host", "relaybp_decode_flagged", "relaybp_osd", "relaybp_spa_create", "relaybp_spa_llr",
             "relaybp_spa_decode", "relaybp_spa_destroy", "relaybp_windows_create", "relaybp_windows_info",
-            "relaybp_windows_handle", "relaybp_windows_decode", "relaybp_windows_destroy", "relaybp_count_failures", "relaybp_launch_count",
+            "relaybp_windows_handle", "relaybp_windows_decode", "relaybp_windows_destroy", "relaybp_count_failures", "relaybp_launch_count", "relaybp_sync",
             "relaybp_probe_smem_read", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
             "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_create", "relaybp_group_decode", "relaybp_group_launch_count",
             "relaybp_group_destroy", "relaybp_destroy", "relaybp_last_error"]
@@ -453,6 +454,12 @@ def relaybp_count_failures(h: Handle, d_pred_obs, d_true_obs, d_stats, shots: in
 
 def relaybp_launch_count(h: Handle) -> int:
     return int(_lib.relaybp_launch_count(h.ptr))
+
+
+def relaybp_sync(h: Handle, stream=None):
+    """Wait for the work queued on the stream; raise on an asynchronous CUDA
+    failure there."""
+    _check(_lib.relaybp_sync(h.ptr, _stream(stream)), "relaybp_sync")
 
 
 def relaybp_probe_smem_read(reps: int, d_sink, stream=None) -> float:

@@ -92,7 +92,7 @@ _HANDLE_CALLS = ["relaybp_set_params", "relaybp_set_learned", "relaybp_set_learn
                  "relaybp_decode_trace", "relaybp_decode_batch_noalloc", "relaybp_decode_host",
                  "relaybp_count_failures", "relaybp_learned_tape_bytes", "relaybp_learned_forward",
                  "relaybp_learned_backward", "relaybp_autotune", "relaybp_group_decode", "relaybp_windows_info",
-                 "relaybp_set_tail_offload",
+                 "relaybp_set_tail_offload", "relaybp_sync",
                  "relaybp_windows_handle", "relaybp_windows_decode"]
 
 

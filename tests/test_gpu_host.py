@@ -44,3 +44,26 @@ def test_decode_host_equals_decode_batch(dem160, shots, cluster):
     R.relaybp_decode_host(h, syn.cpu().numpy(), 500, shots, h_pobs2, None)
     assert np.array_equal(h_pobs2, pobs.cpu().numpy())
     R.relaybp_destroy(h)
+
+
+def test_sync_waits_for_the_stream_and_reports_success():
+    """relaybp_sync on the stream a decode was queued on returns once the
+    decode has finished: every shot's statistics are written when it returns,
+    with no other synchronisation."""
+    from paper_2607_27644_b300 import relaybp as R
+    from workloads.dem import code_capacity_dem
+    dem = code_capacity_dem("ZSZ-LP-160", 0.05)
+    h = R.relaybp_build_dem(dem, R.Params(msg_dtype="f64", num_sets=50, seed=101))
+    shots = 4000
+    st = torch.cuda.Stream()
+    syn = torch.zeros((shots, h.wc), dtype=torch.int32, device="cuda")
+    stats = torch.full((shots, 6), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    R.relaybp_sample(h, 5, 0, shots, syn, None, None, st)
+    R.relaybp_decode_batch(h, syn, 0, shots, None, None, stats, st)
+    host = torch.empty((shots, 6), dtype=torch.int32).pin_memory()
+    with torch.cuda.stream(st):
+        host.copy_(stats, non_blocking=True)
+    R.relaybp_sync(h, st)
+    assert int(host[:, 3].min()) >= 1            # every shot ran at least one iteration
+    R.relaybp_destroy(h)
